@@ -1,0 +1,78 @@
+"""Plant plausible mistakes in a copy of the oracle (on the CPU) and check that the
+pins of ``test_oracle_pins.py`` catch every one of them."""
+import inspect
+import os
+import shutil
+import tempfile
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "spline_oracle.c")
+
+MUTANTS = [
+    ("diagonal loses its factor 2", "*b = 2.0 * (aj + cj);", "*b = (aj + cj);"),
+    ("sign of the slope difference", "*d = 6.0 * ((y[j + 1] - y[j]) / cj - (y[j] - y[j - 1]) / aj);",
+     "*d = 6.0 * ((y[j + 1] - y[j]) / cj + (y[j] - y[j - 1]) / aj);"),
+    ("sign of the start slope", "*d = 6.0 * ((y[1] - y[0]) / h - yp1);", "*d = 6.0 * ((y[1] - y[0]) / h + yp1);"),
+    ("last clamped row with a_n and b_n swapped as printed", "*a = h;\n    *b = 2.0 * h;", "*a = 2.0 * h;\n    *b = h;"),
+    ("elimination uses c instead of a", "double den = b - a * cp[i - 1];", "double den = b - c * cp[i - 1];"),
+    ("back substitution off by one", "ypp[i] = ypp[i] - cp[i] * ypp[i + 1];", "ypp[i] = ypp[i] - cp[i + 1] * ypp[i + 1];"),
+    ("transposed operand in the cubic term", "ppj * right * (right * right - w2)", "ppj * left * (right * right - w2)"),
+    ("dropped 1/6", "v / 6.0", "v"),
+    ("swapped node values", "yj * right + yj1 * left", "yj * left + yj1 * right"),
+    ("tie goes to the right interval", "x[i + 1] < xq[k]", "x[i + 1] <= xq[k]"),
+    ("natural sentinel not strict", "slope > 0.99e30", "slope >= 0.99e30"),
+    ("grid product and sum fused order", "double t = (double)k * step;\n    xq[k] = t + x[0];",
+     "xq[k] = x[0] + (double)k * (x[n - 1] - x[0]) / (double)(m - 1);"),
+]
+
+
+def _pin_functions():
+    out = []
+    for name, fn in inspect.getmembers(pins, inspect.isfunction):
+        if not name.startswith("test_"):
+            continue
+        params = inspect.signature(fn).parameters
+        marks = getattr(fn, "pytestmark", [])
+        grid = {}
+        for mk in marks:
+            if mk.name == "parametrize":
+                grid[mk.args[0]] = list(mk.args[1])
+        if not params:
+            out.append((name, fn, {}))
+        else:
+            import itertools
+            keys = list(params)
+            for combo in itertools.product(*[grid[k] for k in keys]):
+                out.append((name, fn, dict(zip(keys, combo))))
+    return out
+
+
+@pytest.fixture(scope="module")
+def workdir():
+    d = tempfile.mkdtemp(prefix="oracle_mut_")
+    yield d
+    shutil.rmtree(d, ignore_errors=True)
+
+
+@pytest.mark.parametrize("desc,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(desc, old, new, workdir):
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation anchor not unique: %r" % old
+    tag = str(abs(hash(desc)))
+    cpath = os.path.join(workdir, "mut_%s.c" % tag)
+    with open(cpath, "w") as f:
+        f.write(src.replace(old, new))
+    so = oracle.compile_source(cpath, os.path.join(workdir, "mut_%s.so" % tag))
+    caught = None
+    with oracle.swapped(so):
+        for name, fn, kw in _pin_functions():
+            try:
+                fn(**kw)
+            except (AssertionError, ValueError, FloatingPointError, ZeroDivisionError):
+                caught = name
+                break
+    assert caught is not None, "no pin caught: " + desc
