@@ -1,0 +1,199 @@
+/*
+ * spl.h - C ABI of the GB300 cubic-spline library (fit + uniform-grid evaluation).
+ *
+ * What it computes (Hornbeck, "Fast Cubic Spline Interpolation", arXiv 2001.09253):
+ *   fit   - the second derivatives y''[0..n-1] of the interpolating C2 cubic
+ *           spline through (x_j, y_j): the tridiagonal system of eq. (init_val),
+ *           section "Generating Second Derivatives", with the end rows of section
+ *           "Start and End Derivatives" (an end slope > 0.99e30 selects the
+ *           natural end y'' = 0, any other finite slope clamps S' there), solved
+ *           as Thomas' algorithm of section "Implementation" prescribes;
+ *   eval  - S(x_k) at M uniformly spaced queries x_k = x_0 + k*step,
+ *           step = (x_{n-1}-x_0)/(M-1), the last query forced to x_{n-1}
+ *           (section "Curve Interpolation", benchmark step 8), each query
+ *           bracketed to the interval j with x_j < x_k <= x_{j+1} (j = 0 for
+ *           x_k <= x_0; j <= n-2), and evaluated with the one-division form of
+ *           section "Fast Interpolation".
+ *   Bracket indices are bit-exact with a sequential FP64 reference; floating-point
+ *   outputs agree with it to a relative 1e-12 (SPL_PREC_F64) or 1e-5
+ *   (SPL_PREC_F32_REFINE), normwise.
+ *
+ * Conventions for every entry point:
+ *   - Return an spl_status; nothing is thrown across the ABI.  SPL_OK is 0,
+ *     errors are negative, SPL_PENDING is positive.
+ *   - Arrays are plain C arrays of float64 (double) or int32, contiguous,
+ *     0-based, structure-of-arrays.  "device" pointers are CUDA device (or
+ *     managed) addresses on the context's device; "host" pointers are CPU
+ *     addresses (pinned memory gives asynchronous copies).
+ *   - The caller owns every input and output array; the library owns its
+ *     scratch, which it carves from the arena given at creation.
+ *   - One context orders all of its GPU work on one CUDA stream.  Calls on a
+ *     context are serialised by an internal lock; distinct contexts are
+ *     independent.
+ *   - Nothing falls back to the CPU: without the CUDA device the calls fail
+ *     with SPL_ERR_CUDA.
+ */
+#ifndef SPL_H_
+#define SPL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum spl_status {
+  SPL_OK = 0,
+  SPL_PENDING = 1,                /* submitted, not finished yet */
+  SPL_ERR_INVALID_ARG = -1,       /* n < 3, M < 0, null pointer, NaN or -inf end slope, bad option */
+  SPL_ERR_NOT_INCREASING = -2,    /* knots not strictly increasing (found on the device) */
+  SPL_ERR_NONFINITE = -3,         /* a knot or value is NaN or infinite (found on the device) */
+  SPL_ERR_BUDGET = -4,            /* the request can never fit in the context's memory budget */
+  SPL_ERR_QUEUE_FULL = -5,        /* no free slot or memory right now; retry after a completion */
+  SPL_ERR_TIMEOUT = -6,           /* a bounded wait ran out (host wait, or a device-side wait) */
+  SPL_ERR_CUDA = -7,              /* a CUDA call failed; the context may be unusable */
+  SPL_ERR_UNKNOWN_TICKET = -8,    /* ticket never issued by this context, or already collected */
+  SPL_ERR_STATE = -9              /* call not valid in the context's current mode */
+} spl_status;
+
+/* Precision of the arithmetic on the hot path. */
+typedef enum spl_precision {
+  SPL_PREC_F64 = 0,         /* every step in binary64 on the GPU */
+  SPL_PREC_F32_REFINE = 1   /* knot/query differences exact, solve and cubic in binary32,
+                               optional refinement of y'' against an extended-precision residual */
+} spl_precision;
+
+typedef enum spl_mem {
+  SPL_MEM_DEVICE = 0,       /* request arrays are device pointers */
+  SPL_MEM_HOST = 1          /* request arrays are host pointers: the library stages them through
+                               its arena and copies results back before completion */
+} spl_mem;
+
+typedef struct spl_ctx spl_ctx;
+typedef struct spl_plan spl_plan;
+typedef struct spl_batch spl_batch;
+
+/* Context creation.
+ *   device       CUDA device ordinal.
+ *   stream       cudaStream_t (as void*) that orders the context's work; NULL means the
+ *                legacy default stream.  Caller-owned; must outlive the context.
+ *   arena        device memory the library sub-allocates all of its scratch and staging
+ *                from (caller-owned, e.g. a PyTorch tensor).  NULL: the library allocates
+ *                arena_bytes itself with cudaMalloc and frees it in spl_destroy.
+ *   arena_bytes  size of the arena.  It is also the memory budget: requests whose
+ *                footprint (inputs, outputs, scratch) cannot fit are refused with
+ *                SPL_ERR_BUDGET, requests that do not fit right now with SPL_ERR_QUEUE_FULL
+ *                (or wait in the serving queue, see spl_serve_start).
+ *   max_slots    requests that may be in flight at once (>= 1). */
+typedef struct spl_ctx_desc {
+  int32_t device;
+  int32_t max_slots;
+  void *stream;
+  void *arena;
+  uint64_t arena_bytes;
+} spl_ctx_desc;
+
+/* Plan: options shared by the requests submitted with it.
+ *   max_n         largest knot count a request may have (sizes the scratch).
+ *   precision     spl_precision.
+ *   refine_steps  SPL_PREC_F32_REFINE only: refinement sweeps of y'' (0..4).
+ *   tile_rows     knots per tile of the chunked solve; 0 picks it from the device and n.
+ *                 Exposed so tests can force many small tiles; values below 16 are refused. */
+typedef struct spl_plan_desc {
+  uint64_t max_n;
+  int32_t precision;
+  int32_t refine_steps;
+  int32_t tile_rows;
+  int32_t reserved;
+} spl_plan_desc;
+
+/* One instance.
+ *   n, x, y      knots (strictly increasing) and values, n >= 3.
+ *   yp1, ypn     end slopes S'(x_0), S'(x_{n-1}); a value > 0.99e30 (e.g. 1e32 or +inf)
+ *                selects the natural end.  NaN or -inf is SPL_ERR_INVALID_ARG.
+ *   m            number of uniform queries (0 = fit only; 1 = the single query x_0).
+ *   ypp_out      y''[n] output, or NULL if not wanted.
+ *   yq_out       S(x_k)[m] output (NULL allowed only when m == 0).
+ *   jq_out       optional int32 bracket index per query (j of the interval used), or NULL.
+ *   mem          spl_mem: where x, y and the outputs live. */
+typedef struct spl_request {
+  uint64_t n;
+  const double *x;
+  const double *y;
+  double yp1;
+  double ypn;
+  uint64_t m;
+  double *ypp_out;
+  double *yq_out;
+  int32_t *jq_out;
+  int32_t mem;
+  int32_t reserved;
+} spl_request;
+
+/* Completion record.
+ *   status      SPL_OK, SPL_PENDING or the request's error.
+ *   device_ms   GPU time of the launch that carried the request (0 if unknown).
+ *   latency_ms  host wall time from submission to the first poll that saw completion. */
+typedef struct spl_result {
+  int32_t status;
+  float device_ms;
+  double latency_ms;
+} spl_result;
+
+/* Library counters (monotonic over the context's life). */
+typedef struct spl_stats {
+  uint64_t kernel_launches;   /* kernels this library launched */
+  uint64_t graph_launches;    /* CUDA graph launches */
+  uint64_t requests_done;
+  uint64_t arena_high_water;  /* bytes */
+} spl_stats;
+
+const char *spl_status_str(int32_t status);
+
+spl_status spl_create(spl_ctx **out, const spl_ctx_desc *desc);
+void spl_destroy(spl_ctx *ctx);  /* waits for the context's work; NULL is a no-op */
+
+spl_status spl_plan_create(spl_ctx *ctx, const spl_plan_desc *desc, spl_plan **out);
+void spl_plan_destroy(spl_plan *plan);
+
+/* Validate and enqueue one instance on the context's stream.  On SPL_OK *ticket names it
+ * until spl_poll/spl_wait returns a final status.  Device-side validation errors
+ * (NOT_INCREASING, NONFINITE) are reported at completion. */
+spl_status spl_submit(spl_ctx *ctx, spl_plan *plan, const spl_request *req, uint64_t *ticket);
+
+/* Many instances in one launch; tickets[i] names req[i].  All requests must use the same
+ * memory kind. */
+spl_status spl_submit_batch(spl_ctx *ctx, spl_plan *plan, const spl_request *reqs, uint32_t count,
+                            uint64_t *tickets);
+
+/* Non-blocking.  Returns SPL_PENDING, or the final status (then the ticket is released). */
+spl_status spl_poll(spl_ctx *ctx, uint64_t ticket, spl_result *res);
+
+/* Blocks up to timeout_ns (bounded; never forever); SPL_ERR_TIMEOUT when it runs out. */
+spl_status spl_wait(spl_ctx *ctx, uint64_t ticket, uint64_t timeout_ns, spl_result *res);
+
+spl_status spl_get_stats(spl_ctx *ctx, spl_stats *out);
+
+/* Reusable batch: the descriptors of count device-memory requests are uploaded once and
+ * the launch is captured in a CUDA graph; every spl_batch_launch replays it on the
+ * context's stream (one persistent kernel over all tiles of all instances).  Statuses
+ * of the last launch are read with spl_batch_wait. */
+spl_status spl_batch_create(spl_ctx *ctx, spl_plan *plan, const spl_request *reqs, uint32_t count,
+                            spl_batch **out);
+spl_status spl_batch_launch(spl_batch *batch);
+spl_status spl_batch_wait(spl_batch *batch, uint64_t timeout_ns, int32_t *statuses /* count, or NULL */);
+void spl_batch_destroy(spl_batch *batch);
+
+/* Device generator of the benchmark curve (the same counter-based SplitMix64 draws and
+ * integer prefix sum as the host generator, bit for bit): x_0 = 0,
+ * x_i = x_{i-1} + (u_i + 1) 2^-27 with u_i the top 27 bits of draw i, y_i = (top 53 bits)
+ * 2^-53.  x, y are device arrays of n doubles; scratch needs spl_generate_scratch_bytes(n). */
+uint64_t spl_generate_scratch_bytes(uint64_t n);
+spl_status spl_generate_curve(uint64_t seed, uint64_t instance, uint64_t n, double *x, double *y,
+                              void *scratch, uint64_t scratch_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPL_H_ */

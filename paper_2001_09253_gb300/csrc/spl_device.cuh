@@ -1,0 +1,144 @@
+// Device-side pieces shared by the spline kernels: the instance descriptor, the tile
+// geometry, order-preserving keys for exact bracketing, the uniform query grid and a
+// reciprocal that keeps the FP64 pipe free of the full IEEE division.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace spl {
+
+// Status bits a tile ORs into its instance's status word (device memory).
+enum : unsigned { kStNonFinite = 1u, kStNotIncreasing = 2u };
+
+// One instance as the kernels see it (built by the host runtime, lives in device memory
+// or in the kernel parameter block).
+struct Inst {
+  const double *x;      // knots, n
+  const double *y;      // values, n
+  double *ypp;          // y'' out, n (may be null)
+  double *yq;           // S(x_k) out, m (null when m == 0)
+  int32_t *jq;          // bracket index out, m (may be null)
+  long long n, m;
+  double yp1, ypn;      // end slopes (natural when > 0.99e30)
+  long long tile_begin; // global index of this instance's first tile
+  long long ntiles;     // tiles of this instance
+  int tile_rows;        // knots per tile (the last tile of an instance is ragged)
+  int pad;
+  unsigned *status;     // device word, OR of kSt* bits
+};
+
+// Natural end condition: section "Start and End Derivatives" (slope > 0.99e30).
+__device__ __forceinline__ bool is_natural(double slope) { return slope > 0.99e30; }
+
+// Order-preserving signed key of a double (with -0 folded onto +0): for non-NaN a, b,
+// a < b exactly when key(a) < key(b).  Compares run on the integer pipe instead of the
+// (scarce) FP64 pipe and are exact, which keeps the bracket indices bit-identical to a
+// sequential FP64 sweep.
+__device__ __forceinline__ long long dkey(double v) {
+  long long b = __double_as_longlong(v);
+  b = (b == (long long)0x8000000000000000ULL) ? 0LL : b;
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+
+__device__ __forceinline__ bool finite64(double v) {
+  return ((unsigned long long)__double_as_longlong(v) & 0x7FF0000000000000ULL) != 0x7FF0000000000000ULL;
+}
+
+// 1/d: the MUFU seed (rcp.approx.ftz.f64, ~2^-22 relative) refined by one third-order
+// Newton-Raphson step, r' = r + r(e + e^2) with e = 1 - d r (error ~ e^3, i.e. below one
+// ulp before the final rounding).  Three DFMAs instead of a full IEEE division.
+__device__ __forceinline__ double rcp64(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  double e2 = fma(e, e, e);
+  return fma(r, e2, r);
+}
+
+// num/den from its reciprocal r ~ 1/den: q = num*r, then one Markstein correction
+// q + (num - den*q)*r with the remainder formed exactly by the FMA; this returns the
+// correctly rounded quotient whenever r is within an ulp of 1/den, so slopes s_j =
+// (y_{j+1}-y_j)/h_j agree bit for bit with an IEEE division (they feed the cancelling
+// difference s_j - s_{j-1}, where a one-ulp difference would be amplified).
+__device__ __forceinline__ double quot64(double num, double den, double r) {
+  double q = num * r;
+  double rem = fma(-den, q, num);
+  return fma(rem, r, q);
+}
+
+// Same seed and step for binary32 (MUFU rcp has ~1 ulp; one second-order step suffices).
+__device__ __forceinline__ float rcp32(float d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  float e = fmaf(-d, r, 1.0f);
+  return fmaf(r, e, r);
+}
+
+// Exact conversion of 0 <= k < 2^53 to double built with integer operations (the
+// hardware int->f64 conversion runs at the FP64-pipe rate on this part).
+__device__ __forceinline__ double i2d_exact(long long k) {
+  if (k == 0) return 0.0;
+  int lz = __clzll(k);                 // k has 64 - lz significant bits
+  int e = 63 - lz;                     // floor(log2 k)
+  unsigned long long mant = (((unsigned long long)k << lz) << 1) >> 12;  // drop the leading 1
+  unsigned long long bits = ((unsigned long long)(1023 + e) << 52) | mant;
+  return __longlong_as_double((long long)bits);
+}
+
+// Uniform query grid: x_k = x_0 + k*step with separately rounded product and sum, the
+// last point forced to x_{n-1}; m == 1 gives x_0 (numpy linspace semantics).
+struct Grid {
+  double x0, xl, step;
+  long long m;
+  __device__ __forceinline__ double at(long long k) const {
+    if (m == 1) return x0;
+    if (k == m - 1) return xl;
+    return __dadd_rn(__dmul_rn(i2d_exact(k), step), x0);
+  }
+};
+
+__device__ __forceinline__ Grid make_grid(const double *x, long long n, long long m) {
+  Grid g;
+  g.x0 = x[0];
+  g.xl = x[n - 1];
+  g.m = m;
+  g.step = (m >= 2) ? __ddiv_rn(__dsub_rn(g.xl, g.x0), (double)(m - 1)) : 0.0;
+  return g;
+}
+
+// First query whose bracket index is >= s: k = 0 for s == 0, else the least k with
+// x_k > x_s (queries are non-decreasing), found by bisection over [0, m].
+__device__ __forceinline__ long long first_query(const Grid &g, const double *x, long long s) {
+  if (s == 0 || g.m == 0) return 0;
+  const long long ks = dkey(x[s]);
+  long long lo = 0, hi = g.m;
+  while (lo < hi) {
+    long long mid = lo + ((hi - lo) >> 1);
+    if (dkey(g.at(mid)) > ks) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Instance owning global tile t (binary search over tile_begin).
+__device__ __forceinline__ int find_inst(const Inst *insts, int ninst, long long t) {
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (insts[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Validation of the rows a tile owns (section "Generating Second Derivatives" assumes
+// strictly increasing knots; finite inputs are required on top).
+__device__ __forceinline__ void validate_rows(const Inst &I, long long s, long long e) {
+  unsigned bad = 0;
+  for (long long j = s; j < e; ++j) {
+    double xj = I.x[j], yj = I.y[j];
+    if (!finite64(xj) || !finite64(yj)) bad |= kStNonFinite;
+    if (j + 1 < I.n && !(dkey(I.x[j + 1]) > dkey(xj))) bad |= kStNotIncreasing;
+  }
+  if (bad) atomicOr(I.status, bad);
+}
+
+}  // namespace spl

@@ -1,0 +1,29 @@
+// Host-side declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "spl_device.cuh"
+
+namespace spl {
+
+// FP64 fused fit + evaluation (spl_fused_f64.cu).  `threads` must be a multiple of 128;
+// `ring` must hold ring_bytes_f64(threads) bytes.
+size_t ring_bytes_f64(long long threads);
+long long threads_f64(int sm_count, long long total_tiles);
+int halo_rows_f64();
+cudaError_t launch_fused_f64(const Inst *d_insts, int ninst, long long total_tiles, double *ring,
+                             long long threads, cudaStream_t stream);
+
+// Mixed-precision fused fit + evaluation (spl_fused_mixed.cu).
+long long threads_mixed(int sm_count, long long total_tiles);
+cudaError_t launch_fused_mixed(const Inst *d_insts, int ninst, long long total_tiles, long long threads,
+                               cudaStream_t stream);
+
+// Device curve generator (spl_synth.cu).
+size_t generate_scratch_bytes(long long n);
+cudaError_t launch_generate_curve(uint64_t seed, uint64_t instance, long long n, double *x, double *y,
+                                  void *scratch, cudaStream_t stream, int *launches);
+
+}  // namespace spl

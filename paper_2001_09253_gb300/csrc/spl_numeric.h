@@ -1,0 +1,151 @@
+// Integer-pipe numerics shared by the kernels (and compiled on the host by the tests).
+//
+// On GB300 every FP64 instruction, and every conversion to or from binary64, issues at about
+// 1.7 lanes/clk/SM, against ~128 for the FP32 and integer pipes.  The mixed-precision path
+// therefore forms the differences of binary64 knots, values and query positions with integer
+// arithmetic on their encodings, and converts between binary32 and binary64 the same way.
+#pragma once
+#include <cstdint>
+#include <cstring>
+
+#ifdef __CUDACC__
+#define SPL_HD __host__ __device__ __forceinline__
+#else
+#define SPL_HD inline
+#endif
+
+namespace spl {
+
+SPL_HD uint64_t bits64(double v) {
+#ifdef __CUDA_ARCH__
+  return (uint64_t)__double_as_longlong(v);
+#else
+  uint64_t u;
+  std::memcpy(&u, &v, 8);
+  return u;
+#endif
+}
+
+SPL_HD double from_bits64(uint64_t u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)u);
+#else
+  double v;
+  std::memcpy(&v, &u, 8);
+  return v;
+#endif
+}
+
+SPL_HD uint32_t bits32(float v) {
+#ifdef __CUDA_ARCH__
+  return (uint32_t)__float_as_uint(v);
+#else
+  uint32_t u;
+  std::memcpy(&u, &v, 4);
+  return u;
+#endif
+}
+
+SPL_HD float from_bits32(uint32_t u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float v;
+  std::memcpy(&v, &u, 4);
+  return v;
+#endif
+}
+
+SPL_HD int clz64(uint64_t v) {  // v != 0
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)v);
+#else
+  return __builtin_clzll(v);
+#endif
+}
+
+// b - a rounded to nearest-even binary32, from the encodings of two binary64 numbers with
+// normal exponents.  The significands are aligned on the larger exponent with 9 guard bits
+// in a signed 64-bit integer, so the difference is exact whenever the exponents differ by at
+// most 9 (always the case for neighbouring knots, a query and its bracketing knots, or two
+// values of similar size); for wider gaps the smaller operand loses bits below 2^-53 of the
+// larger one, far under binary32 resolution.  Returns false (and leaves *out unset) for zero,
+// subnormal, infinite or NaN inputs and for results outside binary32's normal range: the
+// caller then takes the (rare) FP64 route.
+SPL_HD bool diff_f32(double b, double a, float *out) {
+  const uint64_t ub = bits64(b), ua = bits64(a);
+  const int eb = (int)((ub >> 52) & 0x7FF), ea = (int)((ua >> 52) & 0x7FF);
+  if (eb == 0 || ea == 0 || eb == 0x7FF || ea == 0x7FF) return false;
+  int64_t mb = (int64_t)((ub & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+  int64_t ma = (int64_t)((ua & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+  if (ub >> 63) mb = -mb;
+  if (ua >> 63) ma = -ma;
+  int E;
+  int64_t D;
+  if (eb >= ea) {
+    const int d = eb - ea;
+    E = eb;
+    const int64_t MA = (d <= 9) ? ma * ((int64_t)1 << (9 - d)) : (d >= 72 ? (ma < 0 ? -1 : 0) : (ma >> (d - 9)));
+    D = mb * 512 - MA;
+  } else {
+    const int d = ea - eb;
+    E = ea;
+    const int64_t MB = (d <= 9) ? mb * ((int64_t)1 << (9 - d)) : (d >= 72 ? (mb < 0 ? -1 : 0) : (mb >> (d - 9)));
+    D = MB - ma * 512;
+  }
+  if (D == 0) {
+    *out = 0.0f;
+    return true;
+  }
+  const uint32_t sign = D < 0 ? 1u : 0u;
+  uint64_t u = D < 0 ? (uint64_t)(-D) : (uint64_t)D;  // |D| < 2^63
+  int msb = 63 - clz64(u);
+  int sh = msb - 23;
+  uint64_t q;
+  if (sh > 0) {
+    q = u >> sh;
+    const uint64_t rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (q & 1))) ++q;
+    if (q == (1ull << 24)) {
+      q >>= 1;
+      ++msb;
+    }
+  } else {
+    q = u << (-sh);
+  }
+  // value = (q / 2^23) * 2^(msb + E - 1084)
+  const int biased = msb + E - 1084 + 127;
+  if (biased < 1 || biased > 254) return false;
+  *out = from_bits32((sign << 31) | ((uint32_t)biased << 23) | ((uint32_t)q & 0x7FFFFFu));
+  return true;
+}
+
+// Exact binary32 -> binary64 conversion on the integer pipe (normal numbers and zero;
+// subnormal, infinite and NaN inputs go through the hardware conversion).
+SPL_HD double f32_to_f64(float f) {
+  const uint32_t u = bits32(f);
+  const uint32_t e = (u >> 23) & 0xFF;
+  if (e == 0 || e == 0xFF) {
+    if ((u & 0x7FFFFFFFu) == 0) return from_bits64((uint64_t)(u >> 31) << 63);
+    return (double)f;
+  }
+  const uint64_t s = (uint64_t)(u >> 31) << 63;
+  return from_bits64(s | ((uint64_t)(e + 896) << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29));
+}
+
+// binary64 -> binary32 rounded to nearest-even on the integer pipe, for values in binary32's
+// normal range; others go through the hardware conversion.
+SPL_HD float f64_to_f32(double d) {
+  const uint64_t u = bits64(d);
+  const int e = (int)((u >> 52) & 0x7FF) - 1023 + 127;
+  if (e < 1 || e > 254) return (float)d;
+  uint64_t m = (u & 0xFFFFFFFFFFFFFull);
+  uint64_t q = m >> 29;
+  const uint64_t rem = m & ((1ull << 29) - 1), half = 1ull << 28;
+  if (rem > half || (rem == half && (q & 1))) ++q;
+  uint32_t bits = ((uint32_t)(u >> 63) << 31) | (uint32_t)((((uint64_t)e) << 23) + q);  // carry ripples into the exponent
+  if (((bits >> 23) & 0xFF) == 0xFF) return (float)d;
+  return from_bits32(bits);
+}
+
+}  // namespace spl

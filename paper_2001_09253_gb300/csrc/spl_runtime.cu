@@ -1,0 +1,666 @@
+// Host runtime behind include/spl.h: contexts, plans, the arena sub-allocator, request
+// submission / completion tracking and reusable graph-captured batches.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/spl.h"
+#include "spl_internal.h"
+
+using spl::Inst;
+
+namespace {
+
+constexpr uint64_t kAlign = 256;
+
+uint64_t round_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit free-list allocator over [0, cap) with coalescing; offsets are kAlign-aligned.
+class Pool {
+ public:
+  void init(uint64_t cap) {
+    free_.clear();
+    cap_ = cap / kAlign * kAlign;
+    if (cap_) free_[0] = cap_;
+    used_ = high_ = 0;
+  }
+  uint64_t capacity() const { return cap_; }
+  uint64_t high_water() const { return high_; }
+  bool alloc(uint64_t size, uint64_t *off) {
+    size = round_up(std::max<uint64_t>(size, 1), kAlign);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= size) {
+        *off = it->first;
+        uint64_t rest = it->second - size;
+        uint64_t at = it->first + size;
+        free_.erase(it);
+        if (rest) free_[at] = rest;
+        used_ += size;
+        high_ = std::max(high_, used_);
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(uint64_t off, uint64_t size) {
+    size = round_up(std::max<uint64_t>(size, 1), kAlign);
+    used_ -= size;
+    auto it = free_.emplace(off, size).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+
+ private:
+  std::map<uint64_t, uint64_t> free_;
+  uint64_t cap_ = 0, used_ = 0, high_ = 0;
+};
+
+struct Block {
+  uint64_t off = 0, size = 0;
+};
+
+}  // namespace
+
+struct spl_plan {
+  spl_ctx *ctx;
+  uint64_t max_n;
+  int precision;
+  int refine_steps;
+  int tile_rows;
+};
+
+struct Job;
+
+struct Ticket {
+  Job *job;
+  int index;
+  double t_submit;
+};
+
+struct Job {
+  cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+  std::vector<Block> dev_blocks;   // arena blocks, released once the GPU is done
+  Block pin_block;                 // pinned staging block
+  int count = 0;
+  int slots_base = -1;
+  int remaining = 0;               // tickets not collected yet
+  bool done = false;
+  float ms = 0.f;
+  unsigned *h_status = nullptr;    // pinned, count words
+};
+
+struct spl_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  char *arena = nullptr;
+  bool own_arena = false;
+  int max_slots = 1;
+  int sm_count = 0;
+  std::mutex mu;
+  Pool dev;
+  Pool pin;
+  char *pinned = nullptr;          // pinned staging (descriptors, statuses)
+  uint64_t pinned_bytes = 0;
+  int slots_used = 0;
+  uint64_t next_ticket = 1;
+  std::unordered_map<uint64_t, Ticket> tickets;
+  spl_stats stats{};
+};
+
+struct spl_batch {
+  spl_ctx *ctx = nullptr;
+  int count = 0;
+  std::vector<Block> dev_blocks;
+  Block pin_block;
+  unsigned *h_status = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev_done = nullptr;
+  bool launched = false;
+  int launches_per_replay = 0;
+};
+
+namespace {
+
+spl_status cuda_fail(cudaError_t e) { return e == cudaSuccess ? SPL_OK : SPL_ERR_CUDA; }
+
+spl_status map_status_bits(unsigned bits) {
+  if (bits & spl::kStNonFinite) return SPL_ERR_NONFINITE;
+  if (bits & spl::kStNotIncreasing) return SPL_ERR_NOT_INCREASING;
+  return SPL_OK;
+}
+
+bool slope_ok(double s) { return !std::isnan(s) && !(std::isinf(s) && s < 0); }
+
+spl_status check_request(const spl_plan *plan, const spl_request *r) {
+  if (!r) return SPL_ERR_INVALID_ARG;
+  if (r->n < 3 || r->n > plan->max_n) return SPL_ERR_INVALID_ARG;
+  if (r->n > (1ull << 40) || r->m > (1ull << 40)) return SPL_ERR_INVALID_ARG;
+  if (!r->x || !r->y) return SPL_ERR_INVALID_ARG;
+  if (r->m > 0 && !r->yq_out) return SPL_ERR_INVALID_ARG;
+  if (!slope_ok(r->yp1) || !slope_ok(r->ypn)) return SPL_ERR_INVALID_ARG;
+  if (r->mem != SPL_MEM_DEVICE && r->mem != SPL_MEM_HOST) return SPL_ERR_INVALID_ARG;
+  return SPL_OK;
+}
+
+// Launch geometry of the FP64 kernel: one thread per tile up to four warps per SM (the
+// FP64 pipe is full at one warp per SM sub-partition); more tiles are strided over them.
+// The mixed-precision kernel runs two warps per sub-partition (its binary32 and integer work
+// needs the latency hiding; its ring is half the size).
+long long threads_for(const spl_ctx *c, int precision, long long total_tiles) {
+  return precision == SPL_PREC_F64 ? spl::threads_f64(c->sm_count, total_tiles)
+                                   : spl::threads_mixed(c->sm_count, total_tiles);
+}
+
+// Tile length so that one instance of total_points fills every thread of one wave; never
+// shorter than a few halos.
+int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points) {
+  const long long per_sm = precision == SPL_PREC_F64 ? 128 : 256;
+  long long target = (long long)c->sm_count * per_sm;
+  long long L = (long long)((total_points + target - 1) / target);
+  L = std::max<long long>(L, precision == SPL_PREC_F64 ? 256 : 128);
+  L = std::min<long long>(L, 1 << 20);
+  return (int)L;
+}
+
+struct Staged {
+  std::vector<Block> dev;
+  Block pin;
+  bool ok = true;
+};
+
+// Everything one launch needs, carved from the arena and the pinned pool.
+struct LaunchPlan {
+  int precision = SPL_PREC_F64;
+  std::vector<Inst> insts;
+  long long total_tiles = 0;
+  long long threads = 0;
+  uint64_t ring_bytes = 0;
+  // host-memory staging: device copies of inputs/outputs
+  struct HostIO {
+    const double *hx, *hy;
+    double *hypp, *hyq;
+    int32_t *hjq;
+    uint64_t n, m;
+    uint64_t off_x, off_y, off_ypp, off_yq, off_jq;
+  };
+  std::vector<HostIO> hio;
+};
+
+void release_blocks(spl_ctx *c, std::vector<Block> &blocks) {
+  for (auto &b : blocks) c->dev.release(b.off, b.size);
+  blocks.clear();
+}
+
+bool dev_alloc(spl_ctx *c, uint64_t size, std::vector<Block> &blocks, uint64_t *off) {
+  uint64_t o;
+  if (!c->dev.alloc(size, &o)) return false;
+  blocks.push_back({o, round_up(std::max<uint64_t>(size, 1), kAlign)});
+  *off = o;
+  return true;
+}
+
+// Build descriptors, allocate the arena blocks and pinned staging for `count` requests.
+// Returns SPL_OK, SPL_ERR_BUDGET (can never fit) or SPL_ERR_QUEUE_FULL (not now).
+spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t count, LaunchPlan &lp,
+                   std::vector<Block> &dev_blocks, Block &pin_block, uint64_t *d_insts_off,
+                   uint64_t *d_status_off, uint64_t *d_ring_off) {
+  uint64_t total_points = 0;
+  for (uint32_t i = 0; i < count; ++i) total_points += reqs[i].n;
+  const int L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points);
+  lp.precision = p->precision;
+  lp.insts.resize(count);
+  long long tiles = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    const spl_request &r = reqs[i];
+    Inst &I = lp.insts[i];
+    std::memset(&I, 0, sizeof(I));
+    I.x = r.x; I.y = r.y; I.ypp = r.ypp_out; I.yq = r.yq_out; I.jq = r.jq_out;
+    I.n = (long long)r.n; I.m = (long long)r.m;
+    I.yp1 = r.yp1; I.ypn = r.ypn;
+    I.tile_rows = L;
+    I.ntiles = ((long long)r.n + L - 1) / L;
+    I.tile_begin = tiles;
+    tiles += I.ntiles;
+  }
+  lp.total_tiles = tiles;
+  lp.threads = threads_for(c, p->precision, tiles);
+  lp.ring_bytes = p->precision == SPL_PREC_F64 ? spl::ring_bytes_f64(lp.threads) : 0;
+
+  // footprint check against the whole budget first
+  uint64_t need = round_up(sizeof(Inst) * count, kAlign) + round_up(4ull * count, kAlign) +
+                  round_up(lp.ring_bytes, kAlign);
+  for (uint32_t i = 0; i < count; ++i) {
+    if (reqs[i].mem == SPL_MEM_HOST) {
+      need += round_up(8 * reqs[i].n, kAlign) * 2;
+      if (reqs[i].ypp_out) need += round_up(8 * reqs[i].n, kAlign);
+      if (reqs[i].m) need += round_up(8 * reqs[i].m, kAlign);
+      if (reqs[i].jq_out && reqs[i].m) need += round_up(4 * reqs[i].m, kAlign);
+    }
+  }
+  if (need > c->dev.capacity()) return SPL_ERR_BUDGET;
+  uint64_t pin_need = sizeof(Inst) * count + 4ull * count + 64;
+  if (pin_need > c->pin.capacity()) return SPL_ERR_BUDGET;
+
+  bool ok = dev_alloc(c, sizeof(Inst) * count, dev_blocks, d_insts_off) &&
+            dev_alloc(c, 4ull * count, dev_blocks, d_status_off) &&
+            dev_alloc(c, lp.ring_bytes, dev_blocks, d_ring_off);
+  for (uint32_t i = 0; ok && i < count; ++i) {
+    const spl_request &r = reqs[i];
+    if (r.mem != SPL_MEM_HOST) continue;
+    LaunchPlan::HostIO h{};
+    h.hx = r.x; h.hy = r.y; h.hypp = r.ypp_out; h.hyq = r.yq_out; h.hjq = r.jq_out;
+    h.n = r.n; h.m = r.m;
+    ok = dev_alloc(c, 8 * r.n, dev_blocks, &h.off_x) && dev_alloc(c, 8 * r.n, dev_blocks, &h.off_y);
+    if (ok && r.ypp_out) ok = dev_alloc(c, 8 * r.n, dev_blocks, &h.off_ypp);
+    if (ok && r.m) ok = dev_alloc(c, 8 * r.m, dev_blocks, &h.off_yq);
+    if (ok && r.jq_out && r.m) ok = dev_alloc(c, 4 * r.m, dev_blocks, &h.off_jq);
+    if (ok) {
+      Inst &I = lp.insts[i];
+      I.x = reinterpret_cast<const double *>(c->arena + h.off_x);
+      I.y = reinterpret_cast<const double *>(c->arena + h.off_y);
+      I.ypp = r.ypp_out ? reinterpret_cast<double *>(c->arena + h.off_ypp) : nullptr;
+      I.yq = r.m ? reinterpret_cast<double *>(c->arena + h.off_yq) : nullptr;
+      I.jq = (r.jq_out && r.m) ? reinterpret_cast<int32_t *>(c->arena + h.off_jq) : nullptr;
+      lp.hio.push_back(h);
+    }
+  }
+  uint64_t poff = 0;
+  if (ok) ok = c->pin.alloc(pin_need, &poff);
+  if (!ok) {
+    release_blocks(c, dev_blocks);
+    return SPL_ERR_QUEUE_FULL;
+  }
+  pin_block = {poff, round_up(pin_need, kAlign)};
+  for (uint32_t i = 0; i < count; ++i)
+    lp.insts[i].status = reinterpret_cast<unsigned *>(c->arena + *d_status_off) + i;
+  return SPL_OK;
+}
+
+// The kernel(s) of the hot path for the plan's precision.
+cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, uint64_t d_ring_off, cudaStream_t st,
+                        int *launches) {
+  const Inst *insts = reinterpret_cast<const Inst *>(c->arena + d_insts_off);
+  const int count = (int)lp.insts.size();
+  cudaError_t e;
+  if (lp.precision == SPL_PREC_F64) {
+    e = spl::launch_fused_f64(insts, count, lp.total_tiles, reinterpret_cast<double *>(c->arena + d_ring_off),
+                              lp.threads, st);
+  } else {
+    e = spl::launch_fused_mixed(insts, count, lp.total_tiles, lp.threads, st);
+  }
+  if (launches) *launches += 1;
+  return e;
+}
+
+// Enqueue the launch described by lp: statuses cleared, descriptors uploaded, host inputs
+// copied in, the fused kernel, outputs and statuses copied back.
+cudaError_t enqueue(spl_ctx *c, const LaunchPlan &lp, char *pin_base, unsigned *h_status, uint64_t d_insts_off,
+                    uint64_t d_status_off, uint64_t d_ring_off, cudaStream_t st, int *launches) {
+  const int count = (int)lp.insts.size();
+  std::memcpy(pin_base, lp.insts.data(), sizeof(Inst) * count);
+  cudaError_t e = cudaMemsetAsync(c->arena + d_status_off, 0, 4ull * count, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->arena + d_insts_off, pin_base, sizeof(Inst) * count, cudaMemcpyHostToDevice, st);
+  for (const auto &h : lp.hio) {
+    if (e != cudaSuccess) break;
+    e = cudaMemcpyAsync(c->arena + h.off_x, h.hx, 8 * h.n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->arena + h.off_y, h.hy, 8 * h.n, cudaMemcpyHostToDevice, st);
+  }
+  if (e == cudaSuccess) e = launch_path(c, lp, d_insts_off, d_ring_off, st, launches);
+  for (const auto &h : lp.hio) {
+    if (e != cudaSuccess) break;
+    if (h.hypp) e = cudaMemcpyAsync(h.hypp, c->arena + h.off_ypp, 8 * h.n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && h.m)
+      e = cudaMemcpyAsync(h.hyq, c->arena + h.off_yq, 8 * h.m, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && h.hjq && h.m)
+      e = cudaMemcpyAsync(h.hjq, c->arena + h.off_jq, 4 * h.m, cudaMemcpyDeviceToHost, st);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h_status, c->arena + d_status_off, 4ull * count, cudaMemcpyDeviceToHost, st);
+  return e;
+}
+
+void finish_job(spl_ctx *c, Job *j) {
+  // the GPU is done with everything the job used
+  release_blocks(c, j->dev_blocks);
+  cudaEventElapsedTime(&j->ms, j->ev_start, j->ev_done);
+  j->done = true;
+}
+
+void free_job(spl_ctx *c, Job *j) {
+  if (!j->done) release_blocks(c, j->dev_blocks);
+  c->pin.release(j->pin_block.off, j->pin_block.size);
+  c->slots_used -= j->count;
+  if (j->ev_start) cudaEventDestroy(j->ev_start);
+  if (j->ev_done) cudaEventDestroy(j->ev_done);
+  delete j;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *spl_status_str(int32_t s) {
+  switch (s) {
+    case SPL_OK: return "ok";
+    case SPL_PENDING: return "pending";
+    case SPL_ERR_INVALID_ARG: return "invalid argument";
+    case SPL_ERR_NOT_INCREASING: return "knots not strictly increasing";
+    case SPL_ERR_NONFINITE: return "non-finite knot or value";
+    case SPL_ERR_BUDGET: return "request exceeds the memory budget";
+    case SPL_ERR_QUEUE_FULL: return "no free slot or memory now";
+    case SPL_ERR_TIMEOUT: return "timed out";
+    case SPL_ERR_CUDA: return "CUDA error";
+    case SPL_ERR_UNKNOWN_TICKET: return "unknown ticket";
+    case SPL_ERR_STATE: return "invalid in the current state";
+    default: return "unknown status";
+  }
+}
+
+spl_status spl_create(spl_ctx **out, const spl_ctx_desc *d) {
+  if (!out || !d || d->max_slots < 1 || d->arena_bytes < (1u << 20)) return SPL_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || d->device < 0 || d->device >= ndev) return SPL_ERR_CUDA;
+  if (cudaSetDevice(d->device) != cudaSuccess) return SPL_ERR_CUDA;
+  std::unique_ptr<spl_ctx> c(new (std::nothrow) spl_ctx());
+  if (!c) return SPL_ERR_CUDA;
+  c->device = d->device;
+  c->stream = static_cast<cudaStream_t>(d->stream);
+  c->max_slots = d->max_slots;
+  if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, d->device) != cudaSuccess)
+    return SPL_ERR_CUDA;
+  if (d->arena) {
+    c->arena = static_cast<char *>(d->arena);
+    if (reinterpret_cast<uintptr_t>(c->arena) % kAlign) return SPL_ERR_INVALID_ARG;
+  } else {
+    if (cudaMalloc(&c->arena, d->arena_bytes) != cudaSuccess) return SPL_ERR_CUDA;
+    c->own_arena = true;
+  }
+  c->dev.init(d->arena_bytes);
+  c->pinned_bytes = round_up((uint64_t)d->max_slots * (sizeof(Inst) + 8) + 4096, kAlign) * 2;
+  if (cudaHostAlloc(&c->pinned, c->pinned_bytes, cudaHostAllocDefault) != cudaSuccess) {
+    if (c->own_arena) cudaFree(c->arena);
+    return SPL_ERR_CUDA;
+  }
+  c->pin.init(c->pinned_bytes);
+  *out = c.release();
+  return SPL_OK;
+}
+
+void spl_destroy(spl_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  std::vector<Job *> jobs;
+  for (auto &kv : c->tickets) jobs.push_back(kv.second.job);
+  std::sort(jobs.begin(), jobs.end());
+  jobs.erase(std::unique(jobs.begin(), jobs.end()), jobs.end());
+  for (Job *j : jobs) {
+    if (!j->done) finish_job(c, j);
+    free_job(c, j);
+  }
+  if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->own_arena) cudaFree(c->arena);
+  delete c;
+}
+
+spl_status spl_plan_create(spl_ctx *c, const spl_plan_desc *d, spl_plan **out) {
+  if (!c || !d || !out) return SPL_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (d->max_n < 3) return SPL_ERR_INVALID_ARG;
+  if (d->precision != SPL_PREC_F64 && d->precision != SPL_PREC_F32_REFINE) return SPL_ERR_INVALID_ARG;
+  if (d->refine_steps < 0 || d->refine_steps > 4) return SPL_ERR_INVALID_ARG;
+  if (d->precision == SPL_PREC_F64 && d->refine_steps != 0) return SPL_ERR_INVALID_ARG;
+  if (d->tile_rows != 0 && d->tile_rows < 16) return SPL_ERR_INVALID_ARG;
+  spl_plan *p = new (std::nothrow) spl_plan();
+  if (!p) return SPL_ERR_CUDA;
+  p->ctx = c;
+  p->max_n = d->max_n;
+  p->precision = d->precision;
+  p->refine_steps = d->refine_steps;
+  p->tile_rows = d->tile_rows;
+  *out = p;
+  return SPL_OK;
+}
+
+void spl_plan_destroy(spl_plan *p) { delete p; }
+
+spl_status spl_submit_batch(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t count, uint64_t *tickets) {
+  if (!c || !p || !reqs || !tickets || count == 0 || p->ctx != c) return SPL_ERR_INVALID_ARG;
+  for (uint32_t i = 0; i < count; ++i) {
+    spl_status s = check_request(p, &reqs[i]);
+    if (s != SPL_OK) return s;
+    if (reqs[i].mem != reqs[0].mem) return SPL_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  if ((int)count > c->max_slots) return SPL_ERR_BUDGET;
+  if (c->slots_used + (int)count > c->max_slots) return SPL_ERR_QUEUE_FULL;
+  if (cudaSetDevice(c->device) != cudaSuccess) return SPL_ERR_CUDA;
+  LaunchPlan lp;
+  std::vector<Block> blocks;
+  Block pb;
+  uint64_t oi = 0, os = 0, orr = 0;
+  spl_status s = prepare(c, p, reqs, count, lp, blocks, pb, &oi, &os, &orr);
+  if (s != SPL_OK) return s;
+  Job *j = new (std::nothrow) Job();
+  if (!j) {
+    release_blocks(c, blocks);
+    c->pin.release(pb.off, pb.size);
+    return SPL_ERR_CUDA;
+  }
+  j->dev_blocks = std::move(blocks);
+  j->pin_block = pb;
+  j->count = (int)count;
+  j->remaining = (int)count;
+  c->slots_used += (int)count;
+  char *pin_base = c->pinned + pb.off;
+  j->h_status = reinterpret_cast<unsigned *>(pin_base + round_up(sizeof(Inst) * count, 64));
+  cudaError_t e = cudaEventCreate(&j->ev_start);
+  if (e == cudaSuccess) e = cudaEventCreate(&j->ev_done);
+  if (e == cudaSuccess) e = cudaEventRecord(j->ev_start, c->stream);
+  int launches = 0;
+  if (e == cudaSuccess) e = enqueue(c, lp, pin_base, j->h_status, oi, os, orr, c->stream, &launches);
+  if (e == cudaSuccess) e = cudaEventRecord(j->ev_done, c->stream);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(c->stream);
+    free_job(c, j);
+    return SPL_ERR_CUDA;
+  }
+  c->stats.kernel_launches += launches;
+  const double t = now_ms();
+  for (uint32_t i = 0; i < count; ++i) {
+    uint64_t tk = c->next_ticket++;
+    c->tickets[tk] = Ticket{j, (int)i, t};
+    tickets[i] = tk;
+  }
+  return SPL_OK;
+}
+
+spl_status spl_submit(spl_ctx *c, spl_plan *p, const spl_request *r, uint64_t *ticket) {
+  return spl_submit_batch(c, p, r, 1, ticket);
+}
+
+spl_status spl_poll(spl_ctx *c, uint64_t ticket, spl_result *res) {
+  if (!c) return SPL_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->tickets.find(ticket);
+  if (it == c->tickets.end()) return SPL_ERR_UNKNOWN_TICKET;
+  Ticket &t = it->second;
+  Job *j = t.job;
+  if (!j->done) {
+    cudaError_t q = cudaEventQuery(j->ev_done);
+    if (q == cudaErrorNotReady) {
+      if (res) { res->status = SPL_PENDING; res->device_ms = 0; res->latency_ms = now_ms() - t.t_submit; }
+      return SPL_PENDING;
+    }
+    if (q != cudaSuccess) return SPL_ERR_CUDA;
+    finish_job(c, j);
+  }
+  spl_status st = map_status_bits(j->h_status[t.index]);
+  if (res) { res->status = st; res->device_ms = j->ms; res->latency_ms = now_ms() - t.t_submit; }
+  c->tickets.erase(it);
+  c->stats.requests_done++;
+  if (--j->remaining == 0) free_job(c, j);
+  return st;
+}
+
+spl_status spl_wait(spl_ctx *c, uint64_t ticket, uint64_t timeout_ns, spl_result *res) {
+  const double t0 = now_ms();
+  const double limit = (double)timeout_ns * 1e-6;
+  int spins = 0;
+  for (;;) {
+    spl_status s = spl_poll(c, ticket, res);
+    if (s != SPL_PENDING) return s;
+    if (now_ms() - t0 >= limit) return SPL_ERR_TIMEOUT;
+    if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    else std::this_thread::yield();
+  }
+}
+
+spl_status spl_get_stats(spl_ctx *c, spl_stats *out) {
+  if (!c || !out) return SPL_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->stats.arena_high_water = c->dev.high_water();
+  *out = c->stats;
+  return SPL_OK;
+}
+
+spl_status spl_batch_create(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t count, spl_batch **out) {
+  if (!c || !p || !reqs || !out || count == 0 || p->ctx != c) return SPL_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (uint32_t i = 0; i < count; ++i) {
+    spl_status s = check_request(p, &reqs[i]);
+    if (s != SPL_OK) return s;
+    if (reqs[i].mem != SPL_MEM_DEVICE) return SPL_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (cudaSetDevice(c->device) != cudaSuccess) return SPL_ERR_CUDA;
+  std::unique_ptr<spl_batch> b(new (std::nothrow) spl_batch());
+  if (!b) return SPL_ERR_CUDA;
+  b->ctx = c;
+  b->count = (int)count;
+  LaunchPlan lp;
+  uint64_t oi = 0, os = 0, orr = 0;
+  spl_status s = prepare(c, p, reqs, count, lp, b->dev_blocks, b->pin_block, &oi, &os, &orr);
+  if (s != SPL_OK) return s;
+  char *pin_base = c->pinned + b->pin_block.off;
+  b->h_status = reinterpret_cast<unsigned *>(pin_base + round_up(sizeof(Inst) * count, 64));
+  // descriptors are uploaded once, outside the graph
+  std::memcpy(pin_base, lp.insts.data(), sizeof(Inst) * count);
+  cudaError_t e = cudaMemcpyAsync(c->arena + oi, pin_base, sizeof(Inst) * count, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaStream_t cap = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e1 = cudaMemsetAsync(c->arena + os, 0, 4ull * count, cap);
+    int nl = 0;
+    if (e1 == cudaSuccess) e1 = launch_path(c, lp, oi, orr, cap, &nl);
+    b->launches_per_replay = nl;
+    if (e1 == cudaSuccess)
+      e1 = cudaMemcpyAsync(b->h_status, c->arena + os, 4ull * count, cudaMemcpyDeviceToHost, cap);
+    cudaError_t e2 = cudaStreamEndCapture(cap, &b->graph);
+    e = (e1 != cudaSuccess) ? e1 : e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev_done);
+  if (cap) cudaStreamDestroy(cap);
+  if (e != cudaSuccess) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->ev_done) cudaEventDestroy(b->ev_done);
+    release_blocks(c, b->dev_blocks);
+    c->pin.release(b->pin_block.off, b->pin_block.size);
+    return SPL_ERR_CUDA;
+  }
+  *out = b.release();
+  return SPL_OK;
+}
+
+spl_status spl_batch_launch(spl_batch *b) {
+  if (!b) return SPL_ERR_INVALID_ARG;
+  spl_ctx *c = b->ctx;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaError_t e = cudaGraphLaunch(b->exec, c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev_done, c->stream);
+  if (e != cudaSuccess) return SPL_ERR_CUDA;
+  b->launched = true;
+  c->stats.graph_launches++;
+  c->stats.kernel_launches += b->launches_per_replay;
+  return SPL_OK;
+}
+
+spl_status spl_batch_wait(spl_batch *b, uint64_t timeout_ns, int32_t *statuses) {
+  if (!b) return SPL_ERR_INVALID_ARG;
+  if (!b->launched) return SPL_ERR_STATE;
+  const double t0 = now_ms();
+  const double limit = (double)timeout_ns * 1e-6;
+  int spins = 0;
+  for (;;) {
+    cudaError_t q = cudaEventQuery(b->ev_done);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) return SPL_ERR_CUDA;
+    if (now_ms() - t0 >= limit) return SPL_ERR_TIMEOUT;
+    if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    else std::this_thread::yield();
+  }
+  spl_status worst = SPL_OK;
+  for (int i = 0; i < b->count; ++i) {
+    spl_status s = map_status_bits(b->h_status[i]);
+    if (statuses) statuses[i] = s;
+    if (s != SPL_OK) worst = s;
+  }
+  return worst;
+}
+
+void spl_batch_destroy(spl_batch *b) {
+  if (!b) return;
+  spl_ctx *c = b->ctx;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->ev_done) cudaEventDestroy(b->ev_done);
+  release_blocks(c, b->dev_blocks);
+  c->pin.release(b->pin_block.off, b->pin_block.size);
+  delete b;
+}
+
+uint64_t spl_generate_scratch_bytes(uint64_t n) { return spl::generate_scratch_bytes((long long)n); }
+
+spl_status spl_generate_curve(uint64_t seed, uint64_t instance, uint64_t n, double *x, double *y, void *scratch,
+                              uint64_t scratch_bytes, void *stream) {
+  if (n == 0) return SPL_OK;
+  if (!x || !y || !scratch || n > (1ull << 26)) return SPL_ERR_INVALID_ARG;
+  if (scratch_bytes < spl::generate_scratch_bytes((long long)n)) return SPL_ERR_INVALID_ARG;
+  return cuda_fail(spl::launch_generate_curve(seed, instance, (long long)n, x, y, scratch,
+                                              static_cast<cudaStream_t>(stream), nullptr));
+}
+
+}  // extern "C"

@@ -1,0 +1,291 @@
+"""Thin ctypes binding of libspl.so (include/spl.h): argument marshalling only.
+
+Every step of the spline path runs in the CUDA library; this module converts
+torch tensors / numpy arrays to pointers and back.  PyTorch supplies the device
+memory (the arena handed to the library, the output tensors) and the stream.
+There is no CPU fallback: if the library is missing or cannot load, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+# spl_status
+OK, PENDING = 0, 1
+ERR_INVALID_ARG, ERR_NOT_INCREASING, ERR_NONFINITE, ERR_BUDGET = -1, -2, -3, -4
+ERR_QUEUE_FULL, ERR_TIMEOUT, ERR_CUDA, ERR_UNKNOWN_TICKET, ERR_STATE = -5, -6, -7, -8, -9
+PREC_F64, PREC_F32_REFINE = 0, 1
+MEM_DEVICE, MEM_HOST = 0, 1
+NATURAL = 1e32
+
+EXPORTS = [
+    "spl_status_str", "spl_create", "spl_destroy", "spl_plan_create", "spl_plan_destroy", "spl_submit",
+    "spl_submit_batch", "spl_poll", "spl_wait", "spl_get_stats", "spl_batch_create", "spl_batch_launch",
+    "spl_batch_wait", "spl_batch_destroy", "spl_generate_scratch_bytes", "spl_generate_curve",
+]
+
+
+class CtxDesc(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_slots", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_uint64)]
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("max_n", ctypes.c_uint64), ("precision", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
+                ("tile_rows", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("yp1", ctypes.c_double), ("ypn", ctypes.c_double), ("m", ctypes.c_uint64),
+                ("ypp_out", ctypes.c_void_p), ("yq_out", ctypes.c_void_p), ("jq_out", ctypes.c_void_p),
+                ("mem", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("device_ms", ctypes.c_float), ("latency_ms", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_uint64), ("graph_launches", ctypes.c_uint64),
+                ("requests_done", ctypes.c_uint64), ("arena_high_water", ctypes.c_uint64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libspl.so (building it first if it is absent).  Raises on failure."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or _build.LIB
+        if not os.path.exists(path):
+            _build.build()
+        L = ctypes.CDLL(path)
+        vp, u64, i32, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint32
+        L.spl_status_str.argtypes = [i32]
+        L.spl_status_str.restype = ctypes.c_char_p
+        L.spl_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(CtxDesc)]
+        L.spl_destroy.argtypes = [vp]
+        L.spl_destroy.restype = None
+        L.spl_plan_create.argtypes = [vp, ctypes.POINTER(PlanDesc), ctypes.POINTER(vp)]
+        L.spl_plan_destroy.argtypes = [vp]
+        L.spl_plan_destroy.restype = None
+        L.spl_submit.argtypes = [vp, vp, ctypes.POINTER(Request), ctypes.POINTER(u64)]
+        L.spl_submit_batch.argtypes = [vp, vp, ctypes.POINTER(Request), u32, ctypes.POINTER(u64)]
+        L.spl_poll.argtypes = [vp, u64, ctypes.POINTER(Result)]
+        L.spl_wait.argtypes = [vp, u64, u64, ctypes.POINTER(Result)]
+        L.spl_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        L.spl_batch_create.argtypes = [vp, vp, ctypes.POINTER(Request), u32, ctypes.POINTER(vp)]
+        L.spl_batch_launch.argtypes = [vp]
+        L.spl_batch_wait.argtypes = [vp, u64, ctypes.POINTER(i32)]
+        L.spl_batch_destroy.argtypes = [vp]
+        L.spl_batch_destroy.restype = None
+        L.spl_generate_scratch_bytes.argtypes = [u64]
+        L.spl_generate_scratch_bytes.restype = u64
+        L.spl_generate_curve.argtypes = [u64, u64, u64, vp, vp, vp, u64, vp]
+        for name in ["spl_create", "spl_plan_create", "spl_submit", "spl_submit_batch", "spl_poll", "spl_wait",
+                     "spl_get_stats", "spl_batch_create", "spl_batch_launch", "spl_batch_wait",
+                     "spl_generate_curve"]:
+            getattr(L, name).restype = i32
+        _lib = L
+        return L
+
+
+def status_str(s: int) -> str:
+    return load().spl_status_str(int(s)).decode()
+
+
+class SplError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        super().__init__("%s: %s (%d)" % (what, status_str(status), status))
+
+
+def _check(s: int, what: str):
+    if s < 0:
+        raise SplError(s, what)
+    return s
+
+
+def _ptr(a):
+    """Address of a torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _is_host(a) -> bool:
+    if isinstance(a, np.ndarray):
+        return True
+    return a.device.type == "cpu"
+
+
+def make_request(x, y, yp1=NATURAL, ypn=NATURAL, m=None, ypp_out=None, yq_out=None, jq_out=None) -> Request:
+    n = int(x.shape[0])
+    m = n if m is None else int(m)
+    r = Request()
+    r.n, r.x, r.y = n, _ptr(x), _ptr(y)
+    r.yp1, r.ypn, r.m = float(yp1), float(ypn), m
+    r.ypp_out, r.yq_out, r.jq_out = _ptr(ypp_out), _ptr(yq_out), _ptr(jq_out)
+    r.mem = MEM_HOST if _is_host(x) else MEM_DEVICE
+    return r
+
+
+class Plan:
+    def __init__(self, ctx: "Context", max_n: int, precision: int = PREC_F64, refine_steps: int = 0,
+                 tile_rows: int = 0):
+        self.ctx = ctx
+        d = PlanDesc(max_n=int(max_n), precision=int(precision), refine_steps=int(refine_steps),
+                     tile_rows=int(tile_rows), reserved=0)
+        h = ctypes.c_void_p()
+        _check(ctx.lib.spl_plan_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)), "spl_plan_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            self.ctx.lib.spl_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    def __init__(self, ctx: "Context", plan: Plan, requests, keep=()):
+        self.ctx, self.plan, self.count = ctx, plan, len(requests)
+        self._keep = keep
+        arr = (Request * len(requests))(*requests)
+        h = ctypes.c_void_p()
+        _check(ctx.lib.spl_batch_create(ctx.handle, plan.handle, arr, len(requests), ctypes.byref(h)),
+               "spl_batch_create")
+        self.handle = h
+
+    def launch(self):
+        _check(self.ctx.lib.spl_batch_launch(self.handle), "spl_batch_launch")
+
+    def wait(self, timeout_s: float = 60.0):
+        st = (ctypes.c_int32 * self.count)()
+        s = self.ctx.lib.spl_batch_wait(self.handle, int(timeout_s * 1e9), st)
+        if s == ERR_TIMEOUT or s == ERR_CUDA or s == ERR_STATE:
+            raise SplError(s, "spl_batch_wait")
+        return np.frombuffer(st, dtype=np.int32).copy()
+
+    def close(self):
+        if self.handle:
+            self.ctx.lib.spl_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """One library context on one device and one stream, with a torch-allocated arena."""
+
+    def __init__(self, device: int = 0, stream=None, arena_bytes: int = 1 << 30, max_slots: int = 1024,
+                 arena=None):
+        import torch
+        self.lib = load()
+        self.torch = torch
+        self.device = int(device)
+        dev = torch.device("cuda", self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        if arena is None:
+            arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=dev)
+        self.arena = arena
+        d = CtxDesc(device=self.device, max_slots=int(max_slots), stream=self.stream.cuda_stream,
+                    arena=arena.data_ptr(), arena_bytes=arena.numel() * arena.element_size())
+        h = ctypes.c_void_p()
+        _check(self.lib.spl_create(ctypes.byref(h), ctypes.byref(d)), "spl_create")
+        self.handle = h
+        self._keep = {}
+
+    def plan(self, max_n: int, precision: int = PREC_F64, refine_steps: int = 0, tile_rows: int = 0) -> Plan:
+        return Plan(self, max_n, precision, refine_steps, tile_rows)
+
+    def submit(self, plan: Plan, x, y, yp1=NATURAL, ypn=NATURAL, m=None, ypp_out=None, yq_out=None,
+               jq_out=None) -> int:
+        r = make_request(x, y, yp1, ypn, m, ypp_out, yq_out, jq_out)
+        t = ctypes.c_uint64()
+        _check(self.lib.spl_submit(self.handle, plan.handle, ctypes.byref(r), ctypes.byref(t)), "spl_submit")
+        self._keep[t.value] = (x, y, ypp_out, yq_out, jq_out)
+        return t.value
+
+    def submit_batch(self, plan: Plan, requests, keep=()):
+        arr = (Request * len(requests))(*requests)
+        ts = (ctypes.c_uint64 * len(requests))()
+        _check(self.lib.spl_submit_batch(self.handle, plan.handle, arr, len(requests), ts), "spl_submit_batch")
+        out = list(ts)
+        for t in out:
+            self._keep[t] = keep
+        return out
+
+    def poll(self, ticket: int):
+        res = Result()
+        s = self.lib.spl_poll(self.handle, int(ticket), ctypes.byref(res))
+        if s != PENDING:
+            self._keep.pop(int(ticket), None)
+        return s, res
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        res = Result()
+        s = self.lib.spl_wait(self.handle, int(ticket), int(timeout_s * 1e9), ctypes.byref(res))
+        if s not in (PENDING, ERR_TIMEOUT):
+            self._keep.pop(int(ticket), None)
+        return s, res
+
+    def batch(self, plan: Plan, requests, keep=()) -> Batch:
+        return Batch(self, plan, requests, keep)
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(self.lib.spl_get_stats(self.handle, ctypes.byref(st)), "spl_get_stats")
+        return {k: getattr(st, k) for k, _ in Stats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.spl_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def generate_curve(seed: int, n: int, instance: int = 0, device: int = 0, stream=None):
+    """Benchmark curve generated on the device (bit-identical to synth.curve)."""
+    import torch
+    L = load()
+    dev = torch.device("cuda", device)
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    y = torch.empty(n, dtype=torch.float64, device=dev)
+    nbytes = int(L.spl_generate_scratch_bytes(n))
+    scratch = torch.empty(max(nbytes, 8), dtype=torch.uint8, device=dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    _check(L.spl_generate_curve(seed, instance, n, x.data_ptr(), y.data_ptr(), scratch.data_ptr(), nbytes,
+                                st.cuda_stream), "spl_generate_curve")
+    return x, y

@@ -1,0 +1,139 @@
+"""The integer-pipe numerics of the mixed-precision kernels, compiled for the host from the
+same header and checked against exact rational arithmetic (no GPU needed)."""
+import ctypes
+import math
+import os
+import subprocess
+import tempfile
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2001_09253_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    d = tempfile.mkdtemp(prefix="splnum_")
+    so = os.path.join(d, "libnum.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I", CSRC, "-o", so,
+                    os.path.join(HERE, "numeric_driver.cpp")], check=True)
+    L = ctypes.CDLL(so)
+    L.t_diff_f32.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_float)]
+    L.t_diff_f32.restype = ctypes.c_int
+    L.t_f32_to_f64.argtypes = [ctypes.c_float]
+    L.t_f32_to_f64.restype = ctypes.c_double
+    L.t_f64_to_f32.argtypes = [ctypes.c_double]
+    L.t_f64_to_f32.restype = ctypes.c_float
+    return L
+
+
+def rn32(v: Fraction) -> float:
+    """Exact round-to-nearest-even of a rational to binary32 (normal range)."""
+    if v == 0:
+        return 0.0
+    s = -1 if v < 0 else 1
+    a = abs(v)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= a:
+        e += 1
+    scaled = a / Fraction(2) ** (e - 23)  # in [2^23, 2^24)
+    q, r = divmod(scaled.numerator, scaled.denominator)
+    rem = Fraction(r, scaled.denominator)
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and q % 2 == 1):
+        q += 1
+    return float(np.float32(s * q * 2.0 ** (e - 23)))
+
+
+def diff(L, b, a):
+    out = ctypes.c_float()
+    ok = L.t_diff_f32(b, a, ctypes.byref(out))
+    return bool(ok), out.value
+
+
+def _exp(v):
+    return math.frexp(v)[1]
+
+
+def test_diff_exact_on_close_operands(lib):
+    rng = np.random.default_rng(0)
+    cases = []
+    for _ in range(4000):
+        a = rng.normal() * 10.0 ** rng.integers(-6, 8)
+        kind = rng.integers(0, 5)
+        if kind == 0:
+            b = np.nextafter(a, np.inf) if rng.random() < 0.5 else a + abs(a) * 1e-12 * rng.random()
+        elif kind == 1:
+            b = a * (1 + rng.random())
+        elif kind == 2:
+            b = a + rng.normal() * abs(a) * 10.0 ** rng.integers(-15, 1)
+        elif kind == 3:
+            b = -a * rng.random()
+        else:
+            b = a * 2.0 ** rng.integers(-9, 10) * rng.random()
+        cases.append((float(b), float(a)))
+    # knots of the benchmark curve and crossings of powers of two
+    for v in [1.0, 2.0, 1024.0, 4194304.0]:
+        cases += [(v, float(np.nextafter(v, 0))), (float(np.nextafter(v, np.inf)), float(np.nextafter(v, 0)))]
+    for b, a in cases:
+        if b == 0 or a == 0:
+            continue
+        ok, got = diff(lib, b, a)
+        exact = Fraction(b) - Fraction(a)
+        if exact != 0 and not (2.0 ** -126 <= abs(float(exact)) < 2.0 ** 127):
+            assert not ok
+            continue
+        assert ok, (b, a)
+        ref = rn32(exact)
+        if abs(_exp(b) - _exp(a)) <= 9:
+            assert got == ref, (b, a, got, ref)
+        else:
+            ulp = abs(float(np.spacing(np.float32(ref))))
+            assert abs(got - float(exact)) <= ulp, (b, a, got, float(exact))
+
+
+def test_diff_far_apart_and_signs(lib):
+    rng = np.random.default_rng(1)
+    for _ in range(2000):
+        b = rng.normal() * 10.0 ** rng.integers(-10, 10)
+        a = rng.normal() * 10.0 ** rng.integers(-30, 30)
+        ok, got = diff(lib, b, a)
+        exact = Fraction(float(b)) - Fraction(float(a))
+        if exact == 0 or not (2.0 ** -126 <= abs(float(exact)) < 2.0 ** 127):
+            continue
+        assert ok
+        ref = rn32(exact)
+        ulp = abs(float(np.spacing(np.float32(ref))))
+        assert abs(got - float(exact)) <= ulp
+
+
+def test_diff_special_inputs_refused(lib):
+    for b, a in [(0.0, 1.0), (1.0, 0.0), (5e-324, 1.0), (np.inf, 1.0), (1.0, np.nan), (1e300, -1e300),
+                 (1.0 + 2 ** -52, 1.0 + 2 ** -51 - 2 ** -52 * 0)]:
+        ok, got = diff(lib, b, a)
+        exact = Fraction(float(b)) - Fraction(float(a)) if np.isfinite(b) and np.isfinite(a) else None
+        if b == 0 or a == 0 or not np.isfinite(b) or not np.isfinite(a) or abs(b) < 2.2250738585072014e-308:
+            assert not ok
+        elif exact is not None and abs(float(exact)) >= 2.0 ** 128:
+            assert not ok
+    ok, got = diff(lib, 3.0, 3.0)
+    assert ok and got == 0.0
+
+
+def test_float_double_conversions(lib):
+    rng = np.random.default_rng(2)
+    vals = np.concatenate([rng.normal(size=3000) * 10.0 ** rng.integers(-37, 38, size=3000),
+                           [0.0, -0.0, 1.0, -1.0, 3.4e38, 1.2e-38]])
+    for v in vals.astype(np.float32):
+        assert lib.t_f32_to_f64(float(v)) == float(v)
+        assert math.copysign(1, lib.t_f32_to_f64(float(v))) == math.copysign(1, float(v))
+    for v in rng.normal(size=5000) * 10.0 ** rng.integers(-37, 38, size=5000):
+        assert lib.t_f64_to_f32(float(v)) == float(np.float32(v))
+    # ties round to even
+    for base in [1.0, 1.5, 3.0]:
+        tie = base + 2.0 ** -24 * (1 if base < 2 else 2)
+        assert lib.t_f64_to_f32(tie) == float(np.float32(tie))

@@ -1,0 +1,96 @@
+"""GPU parity of the mixed-precision path (binary32 solve and cubic, exact binary64
+differences and query positions) against the FP64 oracle, through the C ABI.
+Tolerance 1e-5 (normwise for y'', per query for S(x_k)); bracket indices bit-exact."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2001_09253_gb300 import spl, synth
+from parity_util import TOL_MIXED, check_instance, run_gpu, ypp_error, yq_error
+
+pytestmark = pytest.mark.gpu
+
+NAT = oracle.NATURAL
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = spl.Context(device=0, arena_bytes=2 << 30, max_slots=8192)
+    yield c
+    c.close()
+
+
+def _plan(ctx, tile_rows=0, refine=0, max_n=1 << 26):
+    return ctx.plan(max_n=max_n, precision=spl.PREC_F32_REFINE, refine_steps=refine, tile_rows=tile_rows)
+
+
+@pytest.mark.parametrize("bc", [(NAT, NAT), (-1.0, 1.0), (0.0, 0.0), (NAT, 2.0)])
+def test_smallest_config_n1000(ctx, bc):
+    x, y = synth.curve(0, 1000)
+    for L in (0, 16, 37, 150):
+        check_instance(ctx, _plan(ctx, L), x, y, bc[0], bc[1], 1000, tol=TOL_MIXED)
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 9, 31, 32, 33, 40, 64, 65, 129, 257])
+@pytest.mark.parametrize("L", [16, 40])
+def test_sizes_and_tiles(ctx, n, L):
+    x, y = synth.curve(2000 + n, n)
+    for m in sorted({0, 1, 2, 3, n, 2 * n + 1, max(2, n // 3)}):
+        check_instance(ctx, _plan(ctx, L), x, y, -1.0, 1.0, m, tol=TOL_MIXED)
+        check_instance(ctx, _plan(ctx, L), x, y, NAT, NAT, m, tol=TOL_MIXED)
+
+
+def test_knots_far_from_zero_with_tiny_gaps(ctx):
+    """Knots near 5e6 with gaps down to 2^-27: binary32 cannot hold the knots, the exact
+    integer differences must carry the gaps."""
+    x, y = synth.curve(11, 20000)
+    x = x + 5.0e6
+    check_instance(ctx, _plan(ctx), x, y, NAT, NAT, 20000, tol=TOL_MIXED)
+    check_instance(ctx, _plan(ctx, 100), x, y, -1.0, 1.0, 33333, tol=TOL_MIXED)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_adversarial_gap_ratios(ctx, seed):
+    x, y = synth.curve_adversarial(seed, 5000, decades=6)
+    for L in (16, 300, 0):
+        check_instance(ctx, _plan(ctx, L), x, y, NAT, NAT, 7001, tol=TOL_MIXED)
+
+
+def test_negative_and_mixed_sign_knots(ctx):
+    x, y = synth.curve(12, 3000)
+    x = x - x[1500]
+    check_instance(ctx, _plan(ctx, 64), x, y, NAT, NAT, 4000, tol=TOL_MIXED)
+    check_instance(ctx, _plan(ctx, 64), x, 1000.0 + y, 0.25, -0.25, 4000, tol=TOL_MIXED)
+
+
+def test_validation_errors_reported(ctx):
+    x, y = synth.curve(6, 3000)
+    p = _plan(ctx, 64)
+    bad = x.copy()
+    bad[1700] = bad[1699]
+    st, *_ = run_gpu(ctx, p, bad, y, NAT, NAT, 100)
+    assert st == spl.ERR_NOT_INCREASING
+    bad = y.copy()
+    bad[5] = np.nan
+    st, *_ = run_gpu(ctx, p, x, bad, NAT, NAT, 100)
+    assert st == spl.ERR_NONFINITE
+
+
+def test_full_size_n1e7(ctx):
+    """n = M = 10^7, seed 1, in the benchmark's launch configuration; all outputs compared."""
+    import torch
+    n = 10_000_000
+    x, y = spl.generate_curve(1, n)
+    hx, hy = synth.curve(1, n)
+    ypp = torch.empty(n, dtype=torch.float64, device="cuda")
+    yq = torch.empty(n, dtype=torch.float64, device="cuda")
+    jq = torch.empty(n, dtype=torch.int32, device="cuda")
+    t = ctx.submit(_plan(ctx), x, y, NAT, NAT, n, ypp, yq, jq)
+    st, _ = ctx.wait(t, 300)
+    assert st == 0
+    ref = oracle.fit_eval(hx, hy, NAT, NAT, n)
+    e1 = ypp_error(ypp.cpu().numpy(), ref["ypp"])
+    assert np.array_equal(jq.cpu().numpy().astype(np.int64), ref["jq"])
+    e2 = yq_error(hx, hy, ref["ypp"], ref["jq"], yq.cpu().numpy(), ref["yq"])
+    print("mixed n=1e7: y'' err %.3e  S err %.3e" % (e1, e2))
+    assert e1 <= TOL_MIXED and e2 <= TOL_MIXED
