@@ -1,10 +1,14 @@
 #!/usr/bin/env python3
 """Benchmark of the spline hot path on GB300: fit + uniform-grid evaluation.
 
-Workload (one step): one instance of n = M = 10^7 knots/queries, the benchmark curve of
+Main line (one step): one instance of n = M = 10^7 knots/queries, the benchmark curve of
 arXiv 2001.09253 section "Curve Interpolation" (seed 1; see paper_2001_09253_gb300/synth.py),
-natural ends, FP64 on the GPU.  Inputs and outputs (320 MB) exceed the 129 MB L2, so no
-explicit flush is needed between steps.
+natural ends, plain FP64 on the GPU.  Inputs and outputs (320 MB) exceed the 129 MB L2, so no
+explicit flush is needed between steps.  The same JSON line also carries, under
+"other_configs", the mixed-precision path on the same instance (binary32 solve and cubic,
+without and with one refinement step) and the batched workload (4096 instances, sizes
+log-uniform in [1e2, 1e5], seed 2, one persistent launch replayed from a CUDA graph), and,
+in the CPU-baseline leg, the error of every GPU result against the FP64 oracle.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -45,8 +49,13 @@ BYTES_PER_POINT = 32
 # 2 x 152 x 2.07e9 = 0.629e12 op/s (an FMA-counted peak would cap this algorithm near 55%).
 PEAK_FP64_OPS_T = 2 * 152 * 2.07e9 / 1e12
 PEAK_FP64_TFLOPS = 1.25
-KERNEL_SRC = os.path.join(ROOT, "paper_2001_09253_gb300", "csrc", "spl_fused_f64.cu")
-PROFILE = os.path.join(ROOT, "profiles", "fused_f64_n1e7.md")
+TOL = {"f64": 1e-12, "mixed": 1e-5}
+CSRC = os.path.join(ROOT, "paper_2001_09253_gb300", "csrc")
+PROFILES = {
+    "f64": (os.path.join(ROOT, "profiles", "fused_f64_n1e7.md"), ["spl_fused_f64.cu", "spl_device.cuh"]),
+    "mixed": (os.path.join(ROOT, "profiles", "fused_mixed_n1e7.md"),
+              ["spl_fused_mixed.cu", "spl_device.cuh", "spl_numeric.h"]),
+}
 
 
 def parse():
@@ -57,6 +66,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--only", default="", choices=["", "f64", "mixed", "mixed-refine", "batched"],
+                    help="time one path only and print a short line (profiling runs)")
     ap.add_argument("--n", type=int, default=N_POINTS, help="knots = queries per instance (profiling runs)")
     return ap.parse_args()
 
@@ -69,24 +80,25 @@ def measured_peaks():
         return {}
 
 
-def kernel_hash() -> str:
-    with open(KERNEL_SRC, "rb") as f:
-        h = hashlib.sha256(f.read())
-    with open(os.path.join(ROOT, "paper_2001_09253_gb300", "csrc", "spl_device.cuh"), "rb") as f:
-        h.update(f.read())
+def kernel_hash(files) -> str:
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, or None
-    when the summary is absent or was taken on a different version of the kernel source."""
+def profiled_traffic(which: str):
+    """DRAM bytes per launch of the kernel from its committed ncu summary, or None when the
+    summary is absent or was taken on a different version of the kernel sources."""
+    path, files = PROFILES[which]
     try:
-        text = open(PROFILE).read()
+        text = open(path).read()
     except OSError:
         return None
     mh = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
     mb = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
-    if not mh or not mb or mh.group(1) != kernel_hash():
+    if not mh or not mb or mh.group(1) != kernel_hash(files):
         return None
     return float(mb.group(1))
 
@@ -175,22 +187,12 @@ def reduce_max(world, v: float) -> float:
     return float(t.item())
 
 
-def cpu_oracle_rate(min_seconds=10.0, max_reps=30):
-    """The FP64 oracle, as it stands, single-threaded on this host, on the same instance."""
-    import oracle
-    from paper_2001_09253_gb300 import synth
-    x, y = synth.curve(SEED, N_POINTS)
-    oracle.fit_eval(x[:1000], y[:1000])  # build/load outside the timing
-    reps, t0 = 0, time.perf_counter()
-    while True:
-        r = oracle.fit_eval(x, y, oracle.NATURAL, oracle.NATURAL, N_POINTS)
-        assert r["status"] == oracle.OK
-        reps += 1
-        el = time.perf_counter() - t0
-        if el >= min_seconds or reps >= max_reps:
-            break
-    return reps / el, reps, el
+def pct(vals, q):
+    s = sorted(vals)
+    return s[min(len(s) - 1, int(q * len(s)))] if s else None
 
+
+# ------------------------------------------------------------------ reference arm (oracle)
 
 def run_reference(args, world, rank):
     if rank != 0:
@@ -201,8 +203,7 @@ def run_reference(args, world, rank):
     x, y = synth.curve(SEED, N_POINTS)
     for _ in range(min(warm, 1)):
         oracle.fit_eval(x, y, oracle.NATURAL, oracle.NATURAL, N_POINTS)
-    # each step is one full instance; capped so the run stays within a few minutes
-    steps = min(steps, 60)
+    steps = min(steps, 60)  # each step is one full instance; keeps the run within a few minutes
     t0 = time.perf_counter()
     for _ in range(steps):
         r = oracle.fit_eval(x, y, oracle.NATURAL, oracle.NATURAL, N_POINTS)
@@ -223,130 +224,303 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args, world, rank, local):
-    import torch
-    from paper_2001_09253_gb300 import spl
-    assert torch.cuda.is_available(), "the benchmark needs a CUDA device"
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.Stream(dev)
-    K, W = max(args.steps, 1), max(args.warmup, 3)
-    n = m = int(args.n)
-    window = 64
-    ring = 160 << 20  # per-launch scratch bound (the FP64 ring is ~80 MB on 152 SMs)
-    arena = (min(window, K) + 2) * ring
-    if not args.no_e2e:
-        arena += 10 * (32 * n + ring)  # host-buffer leg: staged inputs/outputs, 8 in flight
-    ctx = spl.Context(device=local, stream=stream, arena_bytes=int(arena), max_slots=4096)
-    plan = ctx.plan(max_n=n, precision=spl.PREC_F64)
-    with torch.cuda.stream(stream):
-        x, y = spl.generate_curve(SEED, n, instance=rank, device=local, stream=stream)
-        ypp = torch.empty(n, dtype=torch.float64, device=dev)
-        yq = torch.empty(m, dtype=torch.float64, device=dev)
-    stream.synchronize()
+# ------------------------------------------------------------------ GPU arm
 
-    def step():
-        return ctx.submit(plan, x, y, spl.NATURAL, spl.NATURAL, m, ypp, yq)
+class Runner:
+    def __init__(self, args, world, rank, local):
+        import torch
+        from paper_2001_09253_gb300 import spl
+        assert torch.cuda.is_available(), "the benchmark needs a CUDA device"
+        self.torch, self.spl = torch, spl
+        self.args, self.world, self.rank, self.local = args, world, rank, local
+        torch.cuda.set_device(local)
+        self.dev = torch.device("cuda", local)
+        self.stream = torch.cuda.Stream(self.dev)
+        self.K, self.W = max(args.steps, 1), max(args.warmup, 3)
+        self.n = int(args.n)
+        self.window = 64
+        ring = 160 << 20  # per-launch scratch bound (FP64 ring or binary32 y'' of a refined launch)
+        arena = (min(self.window, self.K) + 2) * (ring + 4 * self.n)
+        if not args.no_e2e:
+            arena += 10 * (32 * self.n + ring)  # host-buffer leg: staged inputs/outputs, 8 in flight
+        if not args.only or args.only == "batched":
+            arena += 2 << 30  # batched workload scratch
+        self.ctx = spl.Context(device=local, stream=self.stream, arena_bytes=int(arena), max_slots=8192)
+        with torch.cuda.stream(self.stream):
+            self.x, self.y = spl.generate_curve(SEED, self.n, instance=rank, device=local, stream=self.stream)
+        self.stream.synchronize()
 
-    for _ in range(W):
-        s, _ = ctx.wait(step(), 120.0)
-        assert s == spl.OK, spl.status_str(s)
-    clocks = Clocks(local)
-    st0 = ctx.stats()
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    pending, dev_ms = [], []
-    for _ in range(K):
-        pending.append(step())
-        if len(pending) >= window:
-            s, r = ctx.wait(pending.pop(0), 120.0)
+    def plan(self, precision, refine=0, max_n=None):
+        return self.ctx.plan(max_n=max_n or self.n, precision=precision, refine_steps=refine)
+
+    def time_single(self, plan, with_clocks=False):
+        """K steps of one instance on the device, W untimed warm-ups; events on the launch stream."""
+        torch, spl = self.torch, self.spl
+        n = m = self.n
+        ypp = torch.empty(n, dtype=torch.float64, device=self.dev)
+        yq = torch.empty(m, dtype=torch.float64, device=self.dev)
+
+        def step():
+            return self.ctx.submit(plan, self.x, self.y, spl.NATURAL, spl.NATURAL, m, ypp, yq)
+
+        for _ in range(self.W):
+            s, _ = self.ctx.wait(step(), 120.0)
+            assert s == spl.OK, spl.status_str(s)
+        clocks = Clocks(self.local) if with_clocks else None
+        st0 = self.ctx.stats()
+        barrier(self.world)
+        torch.cuda.synchronize(self.dev)
+        if clocks:
+            clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        pending, dev_ms = [], []
+        for _ in range(self.K):
+            pending.append(step())
+            if len(pending) >= self.window:
+                s, r = self.ctx.wait(pending.pop(0), 120.0)
+                assert s == spl.OK
+                dev_ms.append(r.device_ms)
+        e1.record(self.stream)
+        for t in pending:
+            s, r = self.ctx.wait(t, 120.0)
             assert s == spl.OK
             dev_ms.append(r.device_ms)
-    e1.record(stream)
-    for t in pending:
-        s, r = ctx.wait(t, 120.0)
-        assert s == spl.OK
-        dev_ms.append(r.device_ms)
-    torch.cuda.synchronize(dev)
-    ck = clocks.stop()
-    st1 = ctx.stats()
-    barrier(world)
-    t_ms = reduce_max(world, e0.elapsed_time(e1))
-    launches = st1["kernel_launches"] - st0["kernel_launches"]
-    value = world * K / (t_ms / 1e3)
-    ms_step = t_ms / K
-    achieved_tflops = FLOPS_PER_POINT * n / (ms_step * 1e-3) / 1e12
-    gbs = BYTES_PER_POINT * n / (ms_step * 1e-3) / 1e9
+        torch.cuda.synchronize(self.dev)
+        ck = clocks.stop() if clocks else None
+        st1 = self.ctx.stats()
+        barrier(self.world)
+        t_ms = reduce_max(self.world, e0.elapsed_time(e1))
+        return {"ms_per_step": t_ms / self.K, "value": self.world * self.K / (t_ms / 1e3),
+                "launches": st1["kernel_launches"] - st0["kernel_launches"],
+                "p50_ms": pct(dev_ms, 0.5), "p99_ms": pct(dev_ms, 0.99), "clocks": ck,
+                "ypp": ypp, "yq": yq}
 
-    if args.no_e2e:
-        if rank == 0:
-            print(json.dumps({"profile_run": True, "n": n, "steps": K, "ms_per_step": ms_step,
-                              "roofline_frac": achieved_tflops / PEAK_FP64_OPS_T, "gpu_launches": int(launches)}))
-        ctx.close()
-        return
-    # end to end through the C ABI with pinned host buffers: H2D of x, y and D2H of y'', S(x_k)
-    hx = x.cpu().pin_memory()
-    hy = y.cpu().pin_memory()
-    hypp = torch.empty(n, dtype=torch.float64).pin_memory()
-    hyq = torch.empty(m, dtype=torch.float64).pin_memory()
-    Ke = min(K, 100)
-    for _ in range(2):
-        s, _ = ctx.wait(ctx.submit(plan, hx, hy, spl.NATURAL, spl.NATURAL, m, hypp, hyq), 120.0)
-        assert s == spl.OK
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    pend = []
-    for _ in range(Ke):
-        pend.append(ctx.submit(plan, hx, hy, spl.NATURAL, spl.NATURAL, m, hypp, hyq))
-        if len(pend) >= 8:
-            s, _ = ctx.wait(pend.pop(0), 120.0)
+    def time_e2e(self, plan):
+        """Same metric through the C ABI with pinned host buffers (H2D of x, y and D2H of
+        y'' and S(x_k) inside the timed region), host wall clock."""
+        torch, spl = self.torch, self.spl
+        n = m = self.n
+        hx = self.x.cpu().pin_memory()
+        hy = self.y.cpu().pin_memory()
+        hypp = torch.empty(n, dtype=torch.float64).pin_memory()
+        hyq = torch.empty(m, dtype=torch.float64).pin_memory()
+        Ke = min(self.K, 100)
+        for _ in range(2):
+            s, _ = self.ctx.wait(self.ctx.submit(plan, hx, hy, spl.NATURAL, spl.NATURAL, m, hypp, hyq), 120.0)
             assert s == spl.OK
-    for t in pend:
-        s, _ = ctx.wait(t, 120.0)
-        assert s == spl.OK
-    torch.cuda.synchronize(dev)
-    te = reduce_max(world, time.perf_counter() - t0)
-    e2e_value = world * Ke / te
+        barrier(self.world)
+        torch.cuda.synchronize(self.dev)
+        t0 = time.perf_counter()
+        pend = []
+        for _ in range(Ke):
+            pend.append(self.ctx.submit(plan, hx, hy, spl.NATURAL, spl.NATURAL, m, hypp, hyq))
+            if len(pend) >= 8:
+                s, _ = self.ctx.wait(pend.pop(0), 120.0)
+                assert s == spl.OK
+        for t in pend:
+            s, _ = self.ctx.wait(t, 120.0)
+            assert s == spl.OK
+        torch.cuda.synchronize(self.dev)
+        te = reduce_max(self.world, time.perf_counter() - t0)
+        return {"value": self.world * Ke / te, "unit": "instances/s", "h2d_bytes_per_step": 16 * n,
+                "d2h_bytes_per_step": 16 * n + 4, "steps": Ke}
 
-    if rank != 0:
-        ctx.close()
+    def batched(self, count=4096, lo=1e2, hi=1e5, seed=2, steps=None):
+        """4096 independent instances, one persistent launch per step replayed from a CUDA graph."""
+        torch, spl = self.torch, self.spl
+        from paper_2001_09253_gb300 import synth
+        sizes = synth.sizes_loguniform(seed, count, lo, hi)
+        total = int(sizes.sum())
+        off = np.concatenate([[0], np.cumsum(sizes)])
+        X = torch.empty(total, dtype=torch.float64, device=self.dev)
+        Y = torch.empty(total, dtype=torch.float64, device=self.dev)
+        P = torch.empty(total, dtype=torch.float64, device=self.dev)
+        Q = torch.empty(total, dtype=torch.float64, device=self.dev)
+        nbytes = int(self.ctx.lib.spl_generate_scratch_bytes(int(sizes.max())))
+        scratch = torch.empty(max(nbytes, 8), dtype=torch.uint8, device=self.dev)
+        for i, nn in enumerate(sizes):
+            s = self.ctx.lib.spl_generate_curve(seed, self.rank * count + i, int(nn), X[off[i]:].data_ptr(),
+                                                Y[off[i]:].data_ptr(), scratch.data_ptr(), nbytes,
+                                                self.stream.cuda_stream)
+            assert s == 0
+        self.stream.synchronize()
+        plan = self.plan(spl.PREC_F32_REFINE, 1, max_n=int(sizes.max()))
+        reqs = []
+        for i, nn in enumerate(sizes):
+            o = int(off[i])
+            reqs.append(spl.make_request(X[o:o + nn], Y[o:o + nn], spl.NATURAL, spl.NATURAL, int(nn), P[o:o + nn],
+                                         Q[o:o + nn]))
+        b = self.ctx.batch(plan, reqs, keep=(X, Y, P, Q))
+        K = steps or max(10, min(self.K, 100))
+        for _ in range(3):
+            b.launch()
+            assert (b.wait() == 0).all()
+        st0 = self.ctx.stats()
+        barrier(self.world)
+        torch.cuda.synchronize(self.dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        for _ in range(K):
+            b.launch()
+        e1.record(self.stream)
+        st = b.wait()
+        torch.cuda.synchronize(self.dev)
+        assert (st == 0).all()
+        st1 = self.ctx.stats()
+        t_ms = reduce_max(self.world, e0.elapsed_time(e1))
+        res = {"workload": "4096 instances, n log-uniform in [1e2, 1e5], seed 2, natural ends, M = n, "
+                           "binary32 + 1 refinement step, one persistent launch pair per step from a CUDA graph",
+               "instances_per_step": count, "points_per_step": total, "steps": K,
+               "ms_per_step": t_ms / K, "value": self.world * count * K / (t_ms / 1e3), "unit": "instances/s",
+               "gb_per_s": BYTES_PER_POINT * total / (t_ms / K * 1e-3) / 1e9,
+               "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
+               "graph_launches": st1["graph_launches"] - st0["graph_launches"]}
+        b.close()
+        return res, (sizes, off, X, Y, P, Q)
+
+
+def short_line(r, which, res):
+    print(json.dumps({"profile_run": True, "path": which, "n": r.n, "steps": r.K,
+                      "ms_per_step": res["ms_per_step"], "gpu_launches": res.get("launches", res.get("gpu_launches"))}))
+
+
+def run_ours(args, world, rank, local):
+    r = Runner(args, world, rank, local)
+    spl = r.spl
+    if args.only:
+        if args.only == "batched":
+            res, _ = r.batched(steps=max(args.steps, 1))
+        else:
+            prec = spl.PREC_F64 if args.only == "f64" else spl.PREC_F32_REFINE
+            res = r.time_single(r.plan(prec, 1 if args.only == "mixed-refine" else 0))
+        if rank == 0:
+            short_line(r, args.only, res)
+        r.ctx.close()
         return
+    n = r.n
+    plan64 = r.plan(spl.PREC_F64)
+    main = r.time_single(plan64, with_clocks=True)
+    e2e = None if args.no_e2e else r.time_e2e(plan64)
+    mixed0 = r.time_single(r.plan(spl.PREC_F32_REFINE, 0))
+    mixed1 = r.time_single(r.plan(spl.PREC_F32_REFINE, 1))
+    batched, bdata = r.batched()
+    if rank != 0:
+        r.ctx.close()
+        return
+
+    ms = main["ms_per_step"]
+    achieved = FLOPS_PER_POINT * n / (ms * 1e-3) / 1e12
+    gbs = BYTES_PER_POINT * n / (ms * 1e-3) / 1e9
+    pk = measured_peaks()
+    hbm = pk.get("hbm_gbs")
+
+    def path_entry(res, name, tol, dtype):
+        msx = res["ms_per_step"]
+        g = BYTES_PER_POINT * n / (msx * 1e-3) / 1e9
+        return {"workload": name, "value": res["value"], "unit": "instances/s", "ms_per_step": msx,
+                "points_per_s": res["value"] * n, "gb_per_s": g, "hbm_frac_of_measured": g / hbm if hbm else None,
+                "latency_ms": {"p50": res["p50_ms"], "p99": res["p99_ms"]}, "gpu_launches": res["launches"],
+                "dtype": dtype, "tolerance": tol}
+
+    others = {
+        "mixed_f32": path_entry(mixed0, "n=M=1e7 seed 1, binary32 solve + cubic, exact binary64 differences "
+                                        "and query positions, no refinement", TOL["mixed"], "f32"),
+        "mixed_f32_refine1": path_entry(mixed1, "same, plus one refinement step of y'' against a double-float "
+                                                "residual (two launches)", TOL["mixed"], "f32+df"),
+        "batched": batched,
+    }
+    others["mixed_f32"]["roofline"] = {"bound": "hbm", "traffic": profiled_traffic("mixed"),
+                                       "achieved": others["mixed_f32"]["gb_per_s"], "peak": hbm, "unit": "GB/s",
+                                       "frac": others["mixed_f32"]["hbm_frac_of_measured"]}
+
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        rate, reps, el = cpu_oracle_rate()
-        cpu = {"value": rate, "unit": "instances/s", "cores": 1, "kind": "oracle",
-               "sample": "%d full n=1e7 instances (%.1f s), single thread" % (reps, el)}
-    pk = measured_peaks()
-    lat = sorted(dev_ms)
+        cpu, errs = cpu_baseline_and_errors(r, main, mixed0, mixed1, bdata)
+        others["mixed_f32"]["error_vs_oracle"] = errs["mixed0"]
+        others["mixed_f32_refine1"]["error_vs_oracle"] = errs["mixed1"]
+        others["batched"]["error_vs_oracle"] = errs["batched"]
+        main_err = errs["f64"]
+    else:
+        main_err = None
+
     line = {
-        "metric": METRIC, "value": value, "unit": "instances/s", "n_gpus": world, "steps": K, "warmup": W,
-        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": main["value"], "unit": "instances/s", "n_gpus": world, "steps": r.K,
+        "warmup": r.W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "fit+eval, n=M=1e7, seed 1, natural ends, plain FP64", "n": n, "m": m,
+        "config": {"workload": "fit+eval, n=M=1e7, seed 1, natural ends, plain FP64", "n": n, "m": n,
                    "instances_per_step": 1, "l2": "inputs+outputs 320 MB > 129 MB L2, no flush",
                    "parallelism": "one instance per GPU"},
-        "points_per_s": value * n, "gb_per_s": gbs,
-        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                       "what": "device time per step (events around each launch, %d in flight)" % window},
-        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": PEAK_FP64_OPS_T, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / PEAK_FP64_OPS_T, "traffic": profiled_traffic(),
+        "points_per_s": main["value"] * n, "gb_per_s": gbs,
+        "latency_ms": {"p50": main["p50_ms"], "p99": main["p99_ms"],
+                       "what": "device time per step (events around each launch, %d in flight)" % r.window},
+        "error_vs_oracle": main_err,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP64_OPS_T, "unit": "TFLOP/s",
+                     "frac": achieved / PEAK_FP64_OPS_T, "traffic": profiled_traffic("f64"),
                      "what": ("FP64 pipe: %d algorithmic FP64 ops/point (paper's counts, a division = 1) per second; "
                               "peak = 2 FP64 ops/clk/SM x 152 SMs x 2.07 GHz (one op per lane per clock)"
                               % FLOPS_PER_POINT),
-                     "frac_of_fma_counted_peak": achieved_tflops / PEAK_FP64_TFLOPS,
-                     "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / pk["hbm_gbs"] if pk.get("hbm_gbs") else None},
+                     "frac_of_fma_counted_peak": achieved / PEAK_FP64_TFLOPS,
+                     "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / hbm if hbm else None},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": "instances/s", "h2d_bytes_per_step": 16 * n,
-                "d2h_bytes_per_step": 16 * n + 4},
-        "gpu_launches": int(launches),
-        "clocks": ck,
+        "e2e": e2e,
+        "gpu_launches": int(main["launches"]),
+        "clocks": main["clocks"],
+        "other_configs": others,
     }
     print(json.dumps(line), flush=True)
-    ctx.close()
+    r.ctx.close()
+
+
+def cpu_baseline_and_errors(r, main, mixed0, mixed1, bdata):
+    """The FP64 oracle, as it stands, single-threaded on the host cores: its rate on the main
+    workload (repeated for ~10 s) and the error of every GPU result against its outputs."""
+    import oracle
+    from paper_2001_09253_gb300 import synth
+    n = r.n
+    x, y = synth.curve(SEED, n)
+    oracle.fit_eval(x[:1000], y[:1000])
+    reps, t0 = 0, time.perf_counter()
+    ref = None
+    while True:
+        ref = oracle.fit_eval(x, y, oracle.NATURAL, oracle.NATURAL, n)
+        assert ref["status"] == oracle.OK
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= 10.0 or reps >= 30:
+            break
+    cpu = {"value": reps / el, "unit": "instances/s", "cores": 1, "kind": "oracle",
+           "sample": "%d full n=1e7 instances (%.1f s), single thread" % (reps, el)}
+
+    def errs(res):
+        ypp = res["ypp"].cpu().numpy()
+        yq = res["yq"].cpu().numpy()
+        return error_pair(x, y, ref, ypp, yq)
+
+    out = {"f64": errs(main), "mixed0": errs(mixed0), "mixed1": errs(mixed1)}
+    sizes, off, X, Y, P, Q = bdata
+    rng = np.random.default_rng(0)
+    pick = rng.choice(len(sizes), size=64, replace=False)
+    worst = [0.0, 0.0]
+    Pc, Qc = P.cpu().numpy(), Q.cpu().numpy()
+    for i in pick:
+        nn, o = int(sizes[i]), int(off[i])
+        xi, yi = synth.curve(2, nn, instance=i)
+        rf = oracle.fit_eval(xi, yi, oracle.NATURAL, oracle.NATURAL, nn)
+        e = error_pair(xi, yi, rf, Pc[o:o + nn], Qc[o:o + nn])
+        worst = [max(worst[0], e["ypp"]), max(worst[1], e["yq"])]
+    out["batched"] = {"ypp": worst[0], "yq": worst[1], "sample": "64 of 4096 instances"}
+    return cpu, out
+
+
+def error_pair(x, y, ref, ypp, yq):
+    e1 = float(np.max(np.abs(ypp - ref["ypp"])) / max(np.max(np.abs(ref["ypp"])), 1e-300))
+    j = ref["jq"]
+    h = x[j + 1] - x[j]
+    curv = h * h * np.maximum(np.abs(ref["ypp"][j]), np.abs(ref["ypp"][j + 1])) / 6.0
+    scale = np.maximum.reduce([np.abs(y[j]), np.abs(y[j + 1]), np.abs(ref["yq"]), curv])
+    e2 = float(np.max(np.abs(yq - ref["yq"]) / np.maximum(scale, 1e-300)))
+    return {"ypp": e1, "yq": e2}
 
 
 def main():

@@ -97,7 +97,10 @@ typedef struct spl_ctx_desc {
 /* Plan: options shared by the requests submitted with it.
  *   max_n         largest knot count a request may have (sizes the scratch).
  *   precision     spl_precision.
- *   refine_steps  SPL_PREC_F32_REFINE only: refinement sweeps of y'' (0..4).
+ *   refine_steps  SPL_PREC_F32_REFINE only: 0 (one fused binary32 pass) or 1 (binary32 fit,
+ *                 then one step of iterative refinement of y'' against the residual of the
+ *                 system formed in double-float arithmetic, then the evaluation).  Other
+ *                 values are SPL_ERR_INVALID_ARG.
  *   tile_rows     knots per tile of the chunked solve; 0 picks it from the device and n.
  *                 Exposed so tests can force many small tiles; values below 16 are refused. */
 typedef struct spl_plan_desc {

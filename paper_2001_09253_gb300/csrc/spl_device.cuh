@@ -25,6 +25,7 @@ struct Inst {
   int tile_rows;        // knots per tile (the last tile of an instance is ragged)
   int pad;
   unsigned *status;     // device word, OR of kSt* bits
+  float *z;             // mixed path with refinement: binary32 y'' of the first pass (n), scratch
 };
 
 // Natural end condition: section "Start and End Derivatives" (slope > 0.99e30).

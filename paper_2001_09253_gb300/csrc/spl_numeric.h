@@ -5,6 +5,7 @@
 // therefore forms the differences of binary64 knots, values and query positions with integer
 // arithmetic on their encodings, and converts between binary32 and binary64 the same way.
 #pragma once
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 
@@ -117,6 +118,143 @@ SPL_HD bool diff_f32(double b, double a, float *out) {
   const int biased = msb + E - 1084 + 127;
   if (biased < 1 || biased > 254) return false;
   *out = from_bits32((sign << 31) | ((uint32_t)biased << 23) | ((uint32_t)q & 0x7FFFFFu));
+  return true;
+}
+
+// ---- double-float ("float-float") arithmetic: value = hi + lo, |lo| <= ulp(hi)/2 ----
+// Error-free transformations: Knuth's TwoSum, Dekker's Fast2Sum, and the FMA form of
+// TwoProduct; relative accuracy of the compound operations about 2^-46.
+struct F2 {
+  float hi, lo;
+};
+
+SPL_HD F2 two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return F2{s, e};
+}
+
+SPL_HD F2 fast_two_sum(float a, float b) {  // |a| >= |b| or a == 0
+  const float s = a + b;
+  return F2{s, b - (s - a)};
+}
+
+SPL_HD F2 two_prod(float a, float b) {
+  const float p = a * b;
+#ifdef __CUDA_ARCH__
+  return F2{p, __fmaf_rn(a, b, -p)};
+#else
+  return F2{p, std::fmaf(a, b, -p)};
+#endif
+}
+
+SPL_HD float fma32(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+  return __fmaf_rn(a, b, c);
+#else
+  return std::fmaf(a, b, c);
+#endif
+}
+
+SPL_HD F2 df_add(F2 a, F2 b) {
+  F2 s = two_sum(a.hi, b.hi);
+  const float e = s.lo + (a.lo + b.lo);
+  return fast_two_sum(s.hi, e);
+}
+
+SPL_HD F2 df_neg(F2 a) { return F2{-a.hi, -a.lo}; }
+
+SPL_HD F2 df_mul_f(F2 a, float b) {
+  F2 p = two_prod(a.hi, b);
+  return fast_two_sum(p.hi, fma32(a.lo, b, p.lo));
+}
+
+SPL_HD F2 df_mul(F2 a, F2 b) {
+  F2 p = two_prod(a.hi, b.hi);
+  const float e = fma32(a.hi, b.lo, fma32(a.lo, b.hi, p.lo));
+  return fast_two_sum(p.hi, e);
+}
+
+// a / b with the binary32 reciprocal r ~ 1/b.hi: q1 = a.hi r, one correction from the
+// double-float remainder a - q1 b.
+SPL_HD F2 df_div(F2 a, F2 b, float r) {
+  const float q1 = a.hi * r;
+  F2 rem = df_add(a, df_neg(df_mul_f(b, q1)));
+  const float q2 = rem.hi * r;
+  return fast_two_sum(q1, q2);
+}
+
+// b - a as a double-float (hi = the binary32 rounding of the difference, lo = the rounding
+// of what is left), from the same exact integer difference as diff_f32; about 48 correct
+// bits.  Same applicability as diff_f32.
+SPL_HD bool diff_f2(double b, double a, F2 *out) {
+  const uint64_t ub = bits64(b), ua = bits64(a);
+  const int eb = (int)((ub >> 52) & 0x7FF), ea = (int)((ua >> 52) & 0x7FF);
+  if (eb == 0 || ea == 0 || eb == 0x7FF || ea == 0x7FF) return false;
+  int64_t mb = (int64_t)((ub & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+  int64_t ma = (int64_t)((ua & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+  if (ub >> 63) mb = -mb;
+  if (ua >> 63) ma = -ma;
+  int E;
+  int64_t D;
+  if (eb >= ea) {
+    const int d = eb - ea;
+    E = eb;
+    const int64_t MA = (d <= 9) ? ma * ((int64_t)1 << (9 - d)) : (d >= 72 ? (ma < 0 ? -1 : 0) : (ma >> (d - 9)));
+    D = mb * 512 - MA;
+  } else {
+    const int d = ea - eb;
+    E = ea;
+    const int64_t MB = (d <= 9) ? mb * ((int64_t)1 << (9 - d)) : (d >= 72 ? (mb < 0 ? -1 : 0) : (mb >> (d - 9)));
+    D = MB - ma * 512;
+  }
+  if (D == 0) {
+    *out = F2{0.0f, 0.0f};
+    return true;
+  }
+  // hi: D rounded to 24 significant bits (as an integer), lo: the exact remainder rounded
+  const uint64_t u = D < 0 ? (uint64_t)(-D) : (uint64_t)D;
+  const int msb = 63 - clz64(u);
+  const int sh = msb - 23;
+  int64_t Dhi = D;
+  if (sh > 0) {
+    uint64_t q = u >> sh;
+    const uint64_t rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (q & 1))) ++q;
+    Dhi = (D < 0 ? -(int64_t)(q << sh) : (int64_t)(q << sh));
+  }
+  const int64_t Dlo = D - Dhi;  // exact, |Dlo| <= 2^(sh-1)
+  // scale 2^(E - 1084) applied through binary32 arithmetic on exact integers
+  auto to_f32 = [&](int64_t v, float *f) -> bool {
+    if (v == 0) {
+      *f = 0.0f;
+      return true;
+    }
+    const uint64_t w = v < 0 ? (uint64_t)(-v) : (uint64_t)v;
+    int hb = 63 - clz64(w);
+    int s2 = hb - 23;
+    uint64_t mq;
+    if (s2 > 0) {
+      mq = w >> s2;
+      const uint64_t rm = w & ((1ull << s2) - 1), hf = 1ull << (s2 - 1);
+      if (rm > hf || (rm == hf && (mq & 1))) ++mq;
+      if (mq == (1ull << 24)) {
+        mq >>= 1;
+        ++hb;
+      }
+    } else {
+      mq = w << (-s2);
+    }
+    const int biased = hb + E - 1084 + 127;
+    if (biased < 1 || biased > 254) return false;
+    *f = from_bits32(((v < 0 ? 1u : 0u) << 31) | ((uint32_t)biased << 23) | ((uint32_t)mq & 0x7FFFFFu));
+    return true;
+  };
+  F2 r;
+  if (!to_f32(Dhi, &r.hi)) return false;
+  if (!to_f32(Dlo, &r.lo)) r.lo = 0.0f;  // below binary32's range: negligible
+  *out = r;
   return true;
 }
 

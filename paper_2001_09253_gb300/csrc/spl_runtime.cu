@@ -195,6 +195,7 @@ struct Staged {
 // Everything one launch needs, carved from the arena and the pinned pool.
 struct LaunchPlan {
   int precision = SPL_PREC_F64;
+  int refine_steps = 0;
   std::vector<Inst> insts;
   long long total_tiles = 0;
   long long threads = 0;
@@ -232,6 +233,7 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
   for (uint32_t i = 0; i < count; ++i) total_points += reqs[i].n;
   const int L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points);
   lp.precision = p->precision;
+  lp.refine_steps = p->precision == SPL_PREC_F64 ? 0 : p->refine_steps;
   lp.insts.resize(count);
   long long tiles = 0;
   for (uint32_t i = 0; i < count; ++i) {
@@ -261,6 +263,9 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
       if (reqs[i].jq_out && reqs[i].m) need += round_up(4 * reqs[i].m, kAlign);
     }
   }
+  // refined mixed path: binary32 y'' of the first pass, one float per knot (scratch)
+  const uint64_t z_bytes = lp.refine_steps > 0 ? 4 * total_points : 0;
+  need += round_up(z_bytes, kAlign);
   if (need > c->dev.capacity()) return SPL_ERR_BUDGET;
   uint64_t pin_need = sizeof(Inst) * count + 4ull * count + 64;
   if (pin_need > c->pin.capacity()) return SPL_ERR_BUDGET;
@@ -268,6 +273,15 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
   bool ok = dev_alloc(c, sizeof(Inst) * count, dev_blocks, d_insts_off) &&
             dev_alloc(c, 4ull * count, dev_blocks, d_status_off) &&
             dev_alloc(c, lp.ring_bytes, dev_blocks, d_ring_off);
+  if (ok && z_bytes) {
+    uint64_t zoff = 0;
+    ok = dev_alloc(c, z_bytes, dev_blocks, &zoff);
+    uint64_t acc = 0;
+    for (uint32_t i = 0; ok && i < count; ++i) {
+      lp.insts[i].z = reinterpret_cast<float *>(c->arena + zoff) + acc;
+      acc += reqs[i].n;
+    }
+  }
   for (uint32_t i = 0; ok && i < count; ++i) {
     const spl_request &r = reqs[i];
     if (r.mem != SPL_MEM_HOST) continue;
@@ -309,8 +323,12 @@ cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, 
   if (lp.precision == SPL_PREC_F64) {
     e = spl::launch_fused_f64(insts, count, lp.total_tiles, reinterpret_cast<double *>(c->arena + d_ring_off),
                               lp.threads, st);
+  } else if (lp.refine_steps == 0) {
+    e = spl::launch_fused_mixed(insts, count, lp.total_tiles, lp.threads, st, false);
   } else {
-    e = spl::launch_fused_mixed(insts, count, lp.total_tiles, lp.threads, st);
+    e = spl::launch_fused_mixed(insts, count, lp.total_tiles, lp.threads, st, true);
+    if (launches) *launches += 1;
+    if (e == cudaSuccess) e = spl::launch_refine_mixed(insts, count, lp.total_tiles, lp.threads, st);
   }
   if (launches) *launches += 1;
   return e;
@@ -434,7 +452,7 @@ spl_status spl_plan_create(spl_ctx *c, const spl_plan_desc *d, spl_plan **out) {
   *out = nullptr;
   if (d->max_n < 3) return SPL_ERR_INVALID_ARG;
   if (d->precision != SPL_PREC_F64 && d->precision != SPL_PREC_F32_REFINE) return SPL_ERR_INVALID_ARG;
-  if (d->refine_steps < 0 || d->refine_steps > 4) return SPL_ERR_INVALID_ARG;
+  if (d->refine_steps < 0 || d->refine_steps > 1) return SPL_ERR_INVALID_ARG;
   if (d->precision == SPL_PREC_F64 && d->refine_steps != 0) return SPL_ERR_INVALID_ARG;
   if (d->tile_rows != 0 && d->tile_rows < 16) return SPL_ERR_INVALID_ARG;
   spl_plan *p = new (std::nothrow) spl_plan();

@@ -6,3 +6,29 @@ int t_diff_f32(double b, double a, float *out) { return spl::diff_f32(b, a, out)
 double t_f32_to_f64(float f) { return spl::f32_to_f64(f); }
 float t_f64_to_f32(double d) { return spl::f64_to_f32(d); }
 }
+
+extern "C" {
+int t_diff_f2(double b, double a, float *hi, float *lo) {
+  spl::F2 r;
+  if (!spl::diff_f2(b, a, &r)) return 0;
+  *hi = r.hi;
+  *lo = r.lo;
+  return 1;
+}
+void t_df_div(float ah, float al, float bh, float bl, float *qh, float *ql) {
+  float r = 1.0f / bh;
+  spl::F2 q = spl::df_div(spl::F2{ah, al}, spl::F2{bh, bl}, r);
+  *qh = q.hi;
+  *ql = q.lo;
+}
+void t_df_add(float ah, float al, float bh, float bl, float *sh, float *sl) {
+  spl::F2 q = spl::df_add(spl::F2{ah, al}, spl::F2{bh, bl});
+  *sh = q.hi;
+  *sl = q.lo;
+}
+void t_df_mul_f(float ah, float al, float b, float *ph, float *pl) {
+  spl::F2 q = spl::df_mul_f(spl::F2{ah, al}, b);
+  *ph = q.hi;
+  *pl = q.lo;
+}
+}

@@ -124,6 +124,59 @@ def test_diff_special_inputs_refused(lib):
     assert ok and got == 0.0
 
 
+def _f2(L, name, *args):
+    a = ctypes.c_float()
+    b = ctypes.c_float()
+    getattr(L, name)(*args, ctypes.byref(a), ctypes.byref(b))
+    return Fraction(a.value) + Fraction(b.value)
+
+
+def _setup_df(L):
+    f, pf = ctypes.c_float, ctypes.POINTER(ctypes.c_float)
+    L.t_diff_f2.argtypes = [ctypes.c_double, ctypes.c_double, pf, pf]
+    L.t_diff_f2.restype = ctypes.c_int
+    L.t_df_div.argtypes = [f, f, f, f, pf, pf]
+    L.t_df_add.argtypes = [f, f, f, f, pf, pf]
+    L.t_df_mul_f.argtypes = [f, f, f, pf, pf]
+    for nm in ("t_df_div", "t_df_add", "t_df_mul_f"):
+        getattr(L, nm).restype = None
+
+
+def _rand_f2(rng):
+    hi = np.float32(rng.normal() * 10.0 ** rng.integers(-8, 8))
+    lo = np.float32(float(hi) * rng.normal() * 2.0 ** -25)
+    return float(hi), float(lo)
+
+
+def test_double_float_difference_and_arithmetic(lib):
+    _setup_df(lib)
+    rng = np.random.default_rng(3)
+    for _ in range(3000):
+        a = rng.normal() * 10.0 ** rng.integers(-6, 7)
+        b = a + rng.normal() * abs(a) * 10.0 ** rng.integers(-14, 1)
+        hi, lo = ctypes.c_float(), ctypes.c_float()
+        if not lib.t_diff_f2(b, a, ctypes.byref(hi), ctypes.byref(lo)):
+            continue
+        exact = Fraction(float(b)) - Fraction(float(a))
+        got = Fraction(hi.value) + Fraction(lo.value)
+        if exact == 0:
+            assert got == 0
+        else:
+            assert abs(got - exact) <= abs(exact) * Fraction(1, 2 ** 47), (a, b)
+            assert hi.value == rn32(exact)
+    for _ in range(3000):
+        ah, al = _rand_f2(rng)
+        bh, bl = _rand_f2(rng)
+        A, B = Fraction(ah) + Fraction(al), Fraction(bh) + Fraction(bl)
+        q = _f2(lib, "t_df_div", ah, al, bh, bl)
+        assert abs(q - A / B) <= abs(A / B) * Fraction(1, 2 ** 44)
+        s = _f2(lib, "t_df_add", ah, al, bh, bl)
+        assert abs(s - (A + B)) <= (abs(A) + abs(B)) * Fraction(1, 2 ** 46)
+        c = float(np.float32(rng.normal()))
+        p = _f2(lib, "t_df_mul_f", ah, al, c)
+        assert abs(p - A * Fraction(c)) <= abs(A * Fraction(c)) * Fraction(1, 2 ** 46)
+
+
 def test_float_double_conversions(lib):
     rng = np.random.default_rng(2)
     vals = np.concatenate([rng.normal(size=3000) * 10.0 ** rng.integers(-37, 38, size=3000),

@@ -76,6 +76,62 @@ def test_validation_errors_reported(ctx):
     assert st == spl.ERR_NONFINITE
 
 
+@pytest.mark.parametrize("bc", [(NAT, NAT), (-1.0, 1.0), (NAT, 0.5)])
+def test_refinement_step(ctx, bc):
+    """One refinement step against the double-float residual: parity at the mixed tolerance
+    and a y'' error well below the unrefined one."""
+    x, y = synth.curve(21, 50000)
+    ref = oracle.fit_eval(x, y, bc[0], bc[1], 50000)
+    errs = {}
+    for refine in (0, 1):
+        for L in (16, 0):
+            st, ypp, yq, jq = run_gpu(ctx, _plan(ctx, L, refine), x, y, bc[0], bc[1], 50000)
+            assert st == 0
+            assert np.array_equal(jq.astype(np.int64), ref["jq"])
+            e1 = ypp_error(ypp, ref["ypp"])
+            e2 = yq_error(x, y, ref["ypp"], ref["jq"], yq, ref["yq"])
+            assert e1 <= TOL_MIXED and e2 <= TOL_MIXED
+            errs[(refine, L)] = e1
+    assert errs[(1, 0)] < 0.1 * errs[(0, 0)], errs
+    assert errs[(1, 16)] < 0.1 * errs[(0, 16)], errs
+    assert errs[(1, 0)] < 1e-9, errs
+
+
+def test_refinement_rescues_ill_conditioned_smooth_data(ctx):
+    """Geometric gaps with smooth data: the binary32 slopes cancel in d_j; the refined path
+    recovers the tolerance from the double-float residual."""
+    g = np.concatenate([0.7 ** np.arange(40), 0.7 ** np.arange(40)[::-1]] * 25)
+    x = np.concatenate([[1.0], 1.0 + np.cumsum(g)])
+    y = np.sin(3 * x)
+    ref = oracle.fit_eval(x, y, NAT, NAT, 3 * len(x))
+    st, ypp, yq, jq = run_gpu(ctx, _plan(ctx, 0, 1), x, y, NAT, NAT, 3 * len(x))
+    assert st == 0
+    assert ypp_error(ypp, ref["ypp"]) <= TOL_MIXED
+    assert yq_error(x, y, ref["ypp"], ref["jq"], yq, ref["yq"]) <= TOL_MIXED
+
+
+def test_refined_batch(ctx):
+    import torch
+    plan = _plan(ctx, 0, 1)
+    sizes = [3, 17, 1000, 5000, 64, 129]
+    reqs, keep, refs = [], [], []
+    for i, n in enumerate(sizes):
+        x, y = synth.curve(31, n, instance=i)
+        xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+        ypp = torch.empty(n, dtype=torch.float64, device="cuda")
+        yq = torch.empty(2 * n, dtype=torch.float64, device="cuda")
+        bc = (NAT, NAT) if i % 2 else (-1.0, 2.0)
+        reqs.append(spl.make_request(xt, yt, bc[0], bc[1], 2 * n, ypp, yq))
+        keep.append((xt, yt, ypp, yq))
+        refs.append((x, y, bc))
+    for t, (x, y, bc), k in zip(ctx.submit_batch(plan, reqs, keep), refs, keep):
+        st, _ = ctx.wait(t)
+        assert st == 0
+        ref = oracle.fit_eval(x, y, bc[0], bc[1], 2 * len(x))
+        assert ypp_error(k[2].cpu().numpy(), ref["ypp"]) <= 1e-8
+        assert yq_error(x, y, ref["ypp"], ref["jq"], k[3].cpu().numpy(), ref["yq"]) <= TOL_MIXED
+
+
 def test_full_size_n1e7(ctx):
     """n = M = 10^7, seed 1, in the benchmark's launch configuration; all outputs compared."""
     import torch
