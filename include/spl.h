@@ -196,6 +196,36 @@ uint64_t spl_generate_scratch_bytes(uint64_t n);
 spl_status spl_generate_curve(uint64_t seed, uint64_t instance, uint64_t n, double *x, double *y,
                               void *scratch, uint64_t scratch_bytes, void *stream);
 
+/* One instance without any allocation, for callers that cannot allocate device memory:
+ * host applications that own all of the GPU's memory themselves (a simulation or game
+ * engine, a database or plug-in host that hands out fixed pools), and code under a hard
+ * memory budget or latency deadline, where cudaMalloc/cudaFree may fail, or stall the
+ * whole device, at the wrong moment.  The paper has no counterpart; this entry point exists
+ * only for such callers.
+ *
+ * Computes what spl_submit computes with a SPL_PREC_F32_REFINE plan and refine_steps = 1
+ * (binary32 fit, one refinement step of y'', evaluation at m uniform queries), enqueued on
+ * `stream` (a cudaStream_t, NULL = legacy default stream) on the current device.  x, y,
+ * ypp_out (may be NULL) and yq_out (may be NULL when m == 0) are caller-owned device arrays,
+ * as in spl_request.  The scratch it needs (the descriptor, a status word and n binary32
+ * values) lives in one fixed array of 4 MiB + 512 B compiled into the library, held by every
+ * GPU that loads the library until the process exits; so n is limited to SPL_NOALLOC_MAX_N
+ * and larger n returns SPL_ERR_BUDGET without launching anything.  The call makes no
+ * cudaMalloc, cudaFree or other allocating call.
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress),
+ * once per device; make that first call before any stream capture.  Every call shares the
+ * same array and leaves the previous call's contents in it (each call clears what must start
+ * at zero): calls whose work overlaps on the GPU (different streams, or several host threads)
+ * race and give wrong results; order them on one stream or synchronise between them.
+ *
+ * status_out: NULL = fully asynchronous, no device-side status.  Non-NULL = the call waits for
+ * its stream and stores SPL_OK, SPL_ERR_NONFINITE or SPL_ERR_NOT_INCREASING.  Returns
+ * SPL_ERR_INVALID_ARG (as spl_submit), SPL_ERR_BUDGET (n too large) or SPL_ERR_CUDA. */
+#define SPL_NOALLOC_MAX_N 1048576u
+spl_status spl_fit_eval_noalloc(const double *x, const double *y, uint64_t n, double yp1, double ypn,
+                                uint64_t m, double *ypp_out, double *yq_out, void *stream, int32_t *status_out);
+
 #ifdef __cplusplus
 }
 #endif

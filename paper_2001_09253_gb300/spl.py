@@ -28,7 +28,9 @@ EXPORTS = [
     "spl_status_str", "spl_create", "spl_destroy", "spl_plan_create", "spl_plan_destroy", "spl_submit",
     "spl_submit_batch", "spl_poll", "spl_wait", "spl_get_stats", "spl_batch_create", "spl_batch_launch",
     "spl_batch_wait", "spl_batch_destroy", "spl_generate_scratch_bytes", "spl_generate_curve",
+    "spl_fit_eval_noalloc",
 ]
+NOALLOC_MAX_N = 1048576
 
 
 class CtxDesc(ctypes.Structure):
@@ -97,9 +99,11 @@ def load(path: str | None = None):
         L.spl_generate_scratch_bytes.argtypes = [u64]
         L.spl_generate_scratch_bytes.restype = u64
         L.spl_generate_curve.argtypes = [u64, u64, u64, vp, vp, vp, u64, vp]
+        L.spl_fit_eval_noalloc.argtypes = [vp, vp, u64, ctypes.c_double, ctypes.c_double, u64, vp, vp, vp,
+                                           ctypes.POINTER(i32)]
         for name in ["spl_create", "spl_plan_create", "spl_submit", "spl_submit_batch", "spl_poll", "spl_wait",
                      "spl_get_stats", "spl_batch_create", "spl_batch_launch", "spl_batch_wait",
-                     "spl_generate_curve"]:
+                     "spl_generate_curve", "spl_fit_eval_noalloc"]:
             getattr(L, name).restype = i32
         _lib = L
         return L
@@ -274,6 +278,20 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def fit_eval_noalloc(x, y, yp1=NATURAL, ypn=NATURAL, m=None, ypp_out=None, yq_out=None, stream=None,
+                     want_status=True):
+    """spl_fit_eval_noalloc: one instance, no allocation inside the library (device tensors
+    in and out, n <= NOALLOC_MAX_N).  Returns (call status, device status or None)."""
+    L = load()
+    n = int(x.shape[0])
+    m = n if m is None else int(m)
+    st = ctypes.c_int32(PENDING)
+    s = L.spl_fit_eval_noalloc(_ptr(x), _ptr(y), n, float(yp1), float(ypn), m, _ptr(ypp_out), _ptr(yq_out),
+                               stream.cuda_stream if stream is not None else None,
+                               ctypes.byref(st) if want_status else None)
+    return s, (st.value if want_status else None)
 
 
 def generate_curve(seed: int, n: int, instance: int = 0, device: int = 0, stream=None):
