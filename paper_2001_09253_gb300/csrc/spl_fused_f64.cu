@@ -69,12 +69,14 @@ __device__ __forceinline__ double newint64(double q, double xj, double xj1, doub
 
 __device__ __forceinline__ int slot_of(long long j, long long s0) { return (int)(j - s0) & (kRing - 1); }
 
-// 2t for a positive normal t by incrementing its exponent (integer pipe); other values
-// take the FP64 multiply.
+// 2t for a normal t by incrementing its exponent (integer pipe); other values take an
+// out-of-line FP64 multiply, so that it is never evaluated speculatively.
+__device__ __noinline__ double twice_slow(double t) { return 2.0 * t; }
 __device__ __forceinline__ double twice(double t) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(t);
   const unsigned e = (unsigned)(u >> 52) & 0x7FFu;
-  return (e - 1u < 0x7FDu) ? __longlong_as_double((long long)(u + (1ull << 52))) : 2.0 * t;
+  if (e - 1u < 0x7FDu) return __longlong_as_double((long long)(u + (1ull << 52)));
+  return twice_slow(t);
 }
 
 __device__ __forceinline__ void prefetch_l1(const void *p) {
@@ -197,16 +199,26 @@ __device__ void tile_f64(const Inst &I, long long tile, const Ring64 &ring) {
   }
 }
 
+// Persistent CTAs; each warp fetches 32 tiles at a time from a counter zeroed before the
+// launch, so tiles of uneven length (ragged tails, small instances) balance across SMs.
 __global__ void __launch_bounds__(kThreads, 1) fused_f64_kernel(const Inst *__restrict__ insts, int ninst,
-                                                                long long total_tiles) {
+                                                                long long total_tiles,
+                                                                unsigned long long *__restrict__ counter) {
   extern __shared__ double smem_ring[];
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nthreads = (long long)gridDim.x * blockDim.x;
   Ring64 ring{smem_ring, (int)threadIdx.x};
-  for (long long t = tid; t < total_tiles; t += nthreads) {
-    const int i = find_inst(insts, ninst, t);
-    const Inst I = insts[i];
-    tile_f64(I, t - I.tile_begin, ring);
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(counter, 32ull);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((long long)base >= total_tiles) break;
+    const long long t = (long long)base + lane;
+    if (t < total_tiles) {
+      const int i = find_inst(insts, ninst, t);
+      const Inst I = insts[i];
+      tile_f64(I, t - I.tile_begin, ring);
+    }
+    __syncwarp();
   }
 }
 
@@ -220,12 +232,12 @@ long long threads_f64(int sm_count, long long total_tiles) {
 }
 
 cudaError_t launch_fused_f64(const Inst *d_insts, int ninst, long long total_tiles, double *,
-                             long long threads, cudaStream_t stream) {
+                             long long threads, unsigned long long *counter, cudaStream_t stream) {
   cudaError_t e = cudaFuncSetAttribute(fused_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kSmemBytes);
   if (e != cudaSuccess) return e;
   const long long grid = threads / kThreads;
-  fused_f64_kernel<<<(unsigned)grid, kThreads, kSmemBytes, stream>>>(d_insts, ninst, total_tiles);
+  fused_f64_kernel<<<(unsigned)grid, kThreads, kSmemBytes, stream>>>(d_insts, ninst, total_tiles, counter);
   return cudaGetLastError();
 }
 

@@ -13,17 +13,18 @@ namespace spl {
 size_t ring_bytes_f64(long long threads);
 long long threads_f64(int sm_count, long long total_tiles);
 int halo_rows_f64();
+// `counter` (8 bytes of device memory) must be zero when the kernel starts.
 cudaError_t launch_fused_f64(const Inst *d_insts, int ninst, long long total_tiles, double *ring,
-                             long long threads, cudaStream_t stream);
+                             long long threads, unsigned long long *counter, cudaStream_t stream);
 
 // Mixed-precision fused fit + evaluation (spl_fused_mixed.cu).
 long long threads_mixed(int sm_count, long long total_tiles);
 // fit_only: first pass of the refined path (y'' in binary32 to each Inst::z, no queries).
 cudaError_t launch_fused_mixed(const Inst *d_insts, int ninst, long long total_tiles, long long threads,
-                               cudaStream_t stream, bool fit_only);
+                               unsigned long long *counter, cudaStream_t stream, bool fit_only);
 // Second pass of the refined path: one refinement step of y'' and the evaluation.
 cudaError_t launch_refine_mixed(const Inst *d_insts, int ninst, long long total_tiles, long long threads,
-                                cudaStream_t stream);
+                                unsigned long long *counter, cudaStream_t stream);
 
 // Device curve generator (spl_synth.cu).
 size_t generate_scratch_bytes(long long n);

@@ -10,7 +10,7 @@ namespace {
 
 constexpr unsigned long long kMaxN = SPL_NOALLOC_MAX_N;
 constexpr size_t kInstOff = 0;      // the instance descriptor
-constexpr size_t kStatusOff = 256;  // its status word (cleared by every call)
+constexpr size_t kStatusOff = 256;  // its status word and two tile counters (cleared by every call)
 constexpr size_t kZOff = 512;       // binary32 y'' of the first pass, kMaxN floats
 constexpr size_t kScratchBytes = kZOff + 4 * kMaxN;
 
@@ -41,11 +41,13 @@ spl_status setup_device(int dev, unsigned char **addr, int *sms) {
   return SPL_OK;
 }
 
-// Writes the descriptor into the scratch and clears the status word, so that no host
-// buffer has to be copied.
-__global__ void noalloc_prepare(spl::Inst I, spl::Inst *dst, unsigned *status) {
+// Writes the descriptor into the scratch and clears the status word and the tile counters,
+// so that no host buffer has to be copied.
+__global__ void noalloc_prepare(spl::Inst I, spl::Inst *dst, unsigned *status, unsigned long long *counters) {
   *dst = I;
   *status = 0u;
+  counters[0] = 0ull;
+  counters[1] = 0ull;
 }
 
 bool slope_valid(double s) { return !(s != s) && !(s < -1.7976931348623157e308); }
@@ -81,11 +83,12 @@ extern "C" spl_status spl_fit_eval_noalloc(const double *x, const double *y, uin
   I.z = reinterpret_cast<float *>(base + kZOff);
   spl::Inst *d_inst = reinterpret_cast<spl::Inst *>(base + kInstOff);
 
-  noalloc_prepare<<<1, 1, 0, st>>>(I, d_inst, I.status);
+  unsigned long long *counters = reinterpret_cast<unsigned long long *>(base + kStatusOff + 16);
+  noalloc_prepare<<<1, 1, 0, st>>>(I, d_inst, I.status, counters);
   cudaError_t e = cudaGetLastError();
   const long long threads = spl::threads_mixed(sms, I.ntiles);
-  if (e == cudaSuccess) e = spl::launch_fused_mixed(d_inst, 1, I.ntiles, threads, st, true);
-  if (e == cudaSuccess) e = spl::launch_refine_mixed(d_inst, 1, I.ntiles, threads, st);
+  if (e == cudaSuccess) e = spl::launch_fused_mixed(d_inst, 1, I.ntiles, threads, counters, st, true);
+  if (e == cudaSuccess) e = spl::launch_refine_mixed(d_inst, 1, I.ntiles, threads, counters + 1, st);
   if (e != cudaSuccess) return SPL_ERR_CUDA;
   if (status_out) {
     unsigned bits = 0;

@@ -121,6 +121,40 @@ SPL_HD bool diff_f32(double b, double a, float *out) {
   return true;
 }
 
+// b - a rounded to nearest-even binary32 for the common case of two binary64 numbers with
+// the same sign and exponent field (neighbouring knots, a query and the knot below it): the
+// encodings then differ by the exact difference in units of the shared ulp, so one integer
+// subtraction and a normalisation give the result.  Returns false when the operands are not
+// in one binade (or are zero, subnormal, infinite or NaN): use diff_f32 then.
+SPL_HD bool diff_same_f32(double b, double a, float *out) {
+  const uint64_t ub = bits64(b), ua = bits64(a);
+  const uint32_t hb = (uint32_t)(ub >> 52), ha = (uint32_t)(ua >> 52);  // sign and exponent
+  const uint32_t e = hb & 0x7FFu;
+  if (hb != ha || e == 0 || e == 0x7FF) return false;
+  int64_t D = (int64_t)(ub - ua);  // (b - a) / 2^(e - 1075), |D| < 2^52
+  if (hb & 0x800u) D = -D;          // negative operands: larger magnitude is smaller value
+  if (D == 0) {
+    *out = 0.0f;
+    return true;
+  }
+  const uint32_t sign = D < 0 ? 1u : 0u;
+  const uint64_t u = D < 0 ? (uint64_t)(-D) : (uint64_t)D;
+  const int lz = clz64(u);
+  const uint64_t nrm = u << lz;  // leading one at bit 63
+  uint64_t q = nrm >> 40;        // 24 significant bits
+  const uint64_t rem = nrm & ((1ull << 40) - 1);
+  if (rem > (1ull << 39) || (rem == (1ull << 39) && (q & 1))) ++q;
+  int msb = 63 - lz;
+  if (q == (1ull << 24)) {
+    q >>= 1;
+    ++msb;
+  }
+  const int biased = msb + (int)e - 1075 + 127;
+  if (biased < 1 || biased > 254) return false;
+  *out = from_bits32((sign << 31) | ((uint32_t)biased << 23) | ((uint32_t)q & 0x7FFFFFu));
+  return true;
+}
+
 // ---- double-float ("float-float") arithmetic: value = hi + lo, |lo| <= ulp(hi)/2 ----
 // Error-free transformations: Knuth's TwoSum, Dekker's Fast2Sum, and the FMA form of
 // TwoProduct; relative accuracy of the compound operations about 2^-46.

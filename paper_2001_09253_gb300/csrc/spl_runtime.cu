@@ -23,6 +23,11 @@ constexpr uint64_t kAlign = 256;
 
 uint64_t round_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
 
+// Per-launch status block: one status word per instance, then two tile counters (one per
+// kernel of the launch), all zeroed before the launch.
+uint64_t status_words_bytes(uint64_t count) { return round_up(4 * count, 16); }
+uint64_t status_block_bytes(uint64_t count) { return status_words_bytes(count) + 16; }
+
 double now_ms() {
   using namespace std::chrono;
   return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
@@ -253,7 +258,7 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
   lp.ring_bytes = p->precision == SPL_PREC_F64 ? spl::ring_bytes_f64(lp.threads) : 0;
 
   // footprint check against the whole budget first
-  uint64_t need = round_up(sizeof(Inst) * count, kAlign) + round_up(4ull * count, kAlign) +
+  uint64_t need = round_up(sizeof(Inst) * count, kAlign) + round_up(status_block_bytes(count), kAlign) +
                   round_up(lp.ring_bytes, kAlign);
   for (uint32_t i = 0; i < count; ++i) {
     if (reqs[i].mem == SPL_MEM_HOST) {
@@ -271,7 +276,7 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
   if (pin_need > c->pin.capacity()) return SPL_ERR_BUDGET;
 
   bool ok = dev_alloc(c, sizeof(Inst) * count, dev_blocks, d_insts_off) &&
-            dev_alloc(c, 4ull * count, dev_blocks, d_status_off) &&
+            dev_alloc(c, status_block_bytes(count), dev_blocks, d_status_off) &&
             dev_alloc(c, lp.ring_bytes, dev_blocks, d_ring_off);
   if (ok && z_bytes) {
     uint64_t zoff = 0;
@@ -315,20 +320,22 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
 }
 
 // The kernel(s) of the hot path for the plan's precision.
-cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, uint64_t d_ring_off, cudaStream_t st,
-                        int *launches) {
+cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, uint64_t d_ring_off,
+                        uint64_t d_status_off, cudaStream_t st, int *launches) {
   const Inst *insts = reinterpret_cast<const Inst *>(c->arena + d_insts_off);
   const int count = (int)lp.insts.size();
+  unsigned long long *counters =
+      reinterpret_cast<unsigned long long *>(c->arena + d_status_off + status_words_bytes(count));
   cudaError_t e;
   if (lp.precision == SPL_PREC_F64) {
     e = spl::launch_fused_f64(insts, count, lp.total_tiles, reinterpret_cast<double *>(c->arena + d_ring_off),
-                              lp.threads, st);
+                              lp.threads, counters, st);
   } else if (lp.refine_steps == 0) {
-    e = spl::launch_fused_mixed(insts, count, lp.total_tiles, lp.threads, st, false);
+    e = spl::launch_fused_mixed(insts, count, lp.total_tiles, lp.threads, counters, st, false);
   } else {
-    e = spl::launch_fused_mixed(insts, count, lp.total_tiles, lp.threads, st, true);
+    e = spl::launch_fused_mixed(insts, count, lp.total_tiles, lp.threads, counters, st, true);
     if (launches) *launches += 1;
-    if (e == cudaSuccess) e = spl::launch_refine_mixed(insts, count, lp.total_tiles, lp.threads, st);
+    if (e == cudaSuccess) e = spl::launch_refine_mixed(insts, count, lp.total_tiles, lp.threads, counters + 1, st);
   }
   if (launches) *launches += 1;
   return e;
@@ -340,7 +347,7 @@ cudaError_t enqueue(spl_ctx *c, const LaunchPlan &lp, char *pin_base, unsigned *
                     uint64_t d_status_off, uint64_t d_ring_off, cudaStream_t st, int *launches) {
   const int count = (int)lp.insts.size();
   std::memcpy(pin_base, lp.insts.data(), sizeof(Inst) * count);
-  cudaError_t e = cudaMemsetAsync(c->arena + d_status_off, 0, 4ull * count, st);
+  cudaError_t e = cudaMemsetAsync(c->arena + d_status_off, 0, status_block_bytes(count), st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->arena + d_insts_off, pin_base, sizeof(Inst) * count, cudaMemcpyHostToDevice, st);
   for (const auto &h : lp.hio) {
@@ -348,7 +355,7 @@ cudaError_t enqueue(spl_ctx *c, const LaunchPlan &lp, char *pin_base, unsigned *
     e = cudaMemcpyAsync(c->arena + h.off_x, h.hx, 8 * h.n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->arena + h.off_y, h.hy, 8 * h.n, cudaMemcpyHostToDevice, st);
   }
-  if (e == cudaSuccess) e = launch_path(c, lp, d_insts_off, d_ring_off, st, launches);
+  if (e == cudaSuccess) e = launch_path(c, lp, d_insts_off, d_ring_off, d_status_off, st, launches);
   for (const auto &h : lp.hio) {
     if (e != cudaSuccess) break;
     if (h.hypp) e = cudaMemcpyAsync(h.hypp, c->arena + h.off_ypp, 8 * h.n, cudaMemcpyDeviceToHost, st);
@@ -596,9 +603,9 @@ spl_status spl_batch_create(spl_ctx *c, spl_plan *p, const spl_request *reqs, ui
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaError_t e1 = cudaMemsetAsync(c->arena + os, 0, 4ull * count, cap);
+    cudaError_t e1 = cudaMemsetAsync(c->arena + os, 0, status_block_bytes(count), cap);
     int nl = 0;
-    if (e1 == cudaSuccess) e1 = launch_path(c, lp, oi, orr, cap, &nl);
+    if (e1 == cudaSuccess) e1 = launch_path(c, lp, oi, orr, os, cap, &nl);
     b->launches_per_replay = nl;
     if (e1 == cudaSuccess)
       e1 = cudaMemcpyAsync(b->h_status, c->arena + os, 4ull * count, cudaMemcpyDeviceToHost, cap);

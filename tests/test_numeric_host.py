@@ -96,6 +96,30 @@ def test_diff_exact_on_close_operands(lib):
             assert abs(got - float(exact)) <= ulp, (b, a, got, float(exact))
 
 
+def test_same_binade_difference(lib):
+    lib.t_diff_same_f32.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_float)]
+    lib.t_diff_same_f32.restype = ctypes.c_int
+    rng = np.random.default_rng(7)
+    hits = 0
+    for _ in range(6000):
+        a = rng.normal() * 10.0 ** rng.integers(-20, 20)
+        b = a + rng.normal() * abs(a) * 10.0 ** rng.integers(-16, 0)
+        out = ctypes.c_float()
+        ok = lib.t_diff_same_f32(float(b), float(a), ctypes.byref(out))
+        same = (np.sign(a) == np.sign(b)) and _exp(a) == _exp(b) and a != 0
+        if not same:
+            assert not ok
+            continue
+        exact = Fraction(float(b)) - Fraction(float(a))
+        if exact != 0 and not (2.0 ** -126 <= abs(float(exact)) < 2.0 ** 127):
+            assert not ok
+            continue
+        assert ok
+        hits += 1
+        assert out.value == rn32(exact), (a, b)
+    assert hits > 3000
+
+
 def test_diff_far_apart_and_signs(lib):
     rng = np.random.default_rng(1)
     for _ in range(2000):
