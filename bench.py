@@ -380,6 +380,87 @@ class Runner:
         return res, (sizes, off, X, Y, P, Q)
 
 
+def serving(r, pool_count=512, seed=3, lo=1e2, hi=1e6, rate=20000.0, warm_s=1.0, run_s=8.0):
+    """Poisson arrivals through the continuous-batching server (persistent device loop,
+    mixed precision), admission under a 150 GB HBM budget; then the same pool at saturation,
+    and the plain FP64 path on the same pool for comparison."""
+    torch, spl = r.torch, r.spl
+    from paper_2001_09253_gb300 import synth
+    sizes = synth.sizes_loguniform(seed, pool_count, lo, hi)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    total = int(off[-1])
+    X = torch.empty(total, dtype=torch.float64, device=r.dev)
+    Y = torch.empty(total, dtype=torch.float64, device=r.dev)
+    P = torch.empty(total, dtype=torch.float64, device=r.dev)
+    Q = torch.empty(total, dtype=torch.float64, device=r.dev)
+    nbytes = int(r.ctx.lib.spl_generate_scratch_bytes(int(sizes.max())))
+    scratch = torch.empty(max(nbytes, 8), dtype=torch.uint8, device=r.dev)
+    for i, nn in enumerate(sizes):
+        assert r.ctx.lib.spl_generate_curve(seed, r.rank * pool_count + i, int(nn), X[off[i]:].data_ptr(),
+                                            Y[off[i]:].data_ptr(), scratch.data_ptr(), nbytes,
+                                            r.stream.cuda_stream) == 0
+    r.stream.synchronize()
+    reqs = []
+    for i, nn in enumerate(sizes):
+        o, nn = int(off[i]), int(nn)
+        reqs.append(spl.make_request(X[o:o + nn], Y[o:o + nn], spl.NATURAL, spl.NATURAL, nn, P[o:o + nn], Q[o:o + nn]))
+    srv = spl.Server(r.ctx, max_inflight=2048, tile_rows=256, budget_bytes=150 * 10 ** 9)
+    st0 = srv.stats()
+    # warm-up trace, then the measured trace (fresh Poisson draws, pool entries cycled)
+    nw, nm = int(rate * warm_s), int(rate * run_s)
+    s, _, _ = srv.replay(reqs, np.arange(nw) % pool_count, synth.poisson_arrivals(seed + 100, rate, nw))
+    assert s == spl.OK
+    arr = synth.poisson_arrivals(seed, rate, nm)
+    pick = (np.arange(nm) * 7919) % pool_count
+    s, lat, makespan = srv.replay(reqs, pick, arr)
+    assert s == spl.OK
+    pts = float(sizes[pick].sum())
+    res = {"workload": "Poisson arrivals at %.0f requests/s for %.0f s, n log-uniform in [1e2, 1e6] (pool of %d "
+                       "distinct seeded instances, seed 3), M = n, natural ends, mixed precision (binary32 solve and "
+                       "cubic, exact binary64 differences and query positions), admission under a 150 GB HBM budget, "
+                       "persistent device loop" % (rate, run_s, pool_count),
+           "requests": nm, "offered_rate": rate, "value": nm / makespan, "unit": "instances/s",
+           "points_per_s": pts / makespan, "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                                          "p99": float(np.percentile(lat, 99)),
+                                                          "max": float(lat.max()),
+                                                          "what": "scheduled arrival to completion seen by the host"}}
+    # saturation: every request of one pass over the pool arrives at once
+    nsat = 4 * pool_count
+    s, lat2, mk2 = srv.replay(reqs, np.arange(nsat) % pool_count, np.zeros(nsat))
+    assert s == spl.OK
+    pts2 = float(sizes.sum()) * 4
+    res["saturation"] = {"requests": nsat, "value": nsat / mk2, "unit": "instances/s", "points_per_s": pts2 / mk2,
+                         "gb_per_s": BYTES_PER_POINT * pts2 / mk2 / 1e9}
+    st1 = srv.stats()
+    res["loop_launches"] = st1["loop_launches"] - st0["loop_launches"]
+    srv.close()
+    torch.cuda.synchronize(r.dev)
+    rng = np.random.default_rng(1)
+    sample = {}
+    for i in rng.choice(pool_count, size=24, replace=False):
+        o, nn = int(off[i]), int(sizes[i])
+        sample[int(i)] = (P[o:o + nn].cpu().numpy(), Q[o:o + nn].cpu().numpy())
+    # the plain FP64 path on the same pool (one graph-captured launch over all of it)
+    plan = r.plan(spl.PREC_F64, 0, max_n=int(sizes.max()))
+    b = r.ctx.batch(plan, reqs, keep=(X, Y, P, Q))
+    for _ in range(2):
+        b.launch()
+        assert (b.wait() == 0).all()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(r.stream)
+    K = 5
+    for _ in range(K):
+        b.launch()
+    e1.record(r.stream)
+    assert (b.wait() == 0).all()
+    t_ms = e0.elapsed_time(e1) / K
+    res["plain_f64_same_pool"] = {"value": pool_count / (t_ms * 1e-3), "unit": "instances/s",
+                                  "points_per_s": total / (t_ms * 1e-3), "ms_per_pool": t_ms}
+    b.close()
+    res["served_over_plain_instances_per_s"] = res["saturation"]["value"] / res["plain_f64_same_pool"]["value"]
+    return res, (sizes, seed, r.rank * pool_count, sample)
+
+
 def short_line(r, which, res):
     print(json.dumps({"profile_run": True, "path": which, "n": r.n, "steps": r.K,
                       "ms_per_step": res["ms_per_step"], "gpu_launches": res.get("launches", res.get("gpu_launches"))}))
@@ -405,6 +486,7 @@ def run_ours(args, world, rank, local):
     mixed0 = r.time_single(r.plan(spl.PREC_F32_REFINE, 0))
     mixed1 = r.time_single(r.plan(spl.PREC_F32_REFINE, 1))
     batched, bdata = r.batched()
+    served, sdata = serving(r)
     if rank != 0:
         r.ctx.close()
         return
@@ -429,6 +511,7 @@ def run_ours(args, world, rank, local):
         "mixed_f32_refine1": path_entry(mixed1, "same, plus one refinement step of y'' against a double-float "
                                                 "residual (two launches)", TOL["mixed"], "f32+df"),
         "batched": batched,
+        "serving": served,
     }
     others["mixed_f32"]["roofline"] = {"bound": "hbm", "traffic": profiled_traffic("mixed"),
                                        "achieved": others["mixed_f32"]["gb_per_s"], "peak": hbm, "unit": "GB/s",
@@ -436,7 +519,8 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu, errs = cpu_baseline_and_errors(r, main, mixed0, mixed1, bdata)
+        cpu, errs = cpu_baseline_and_errors(r, main, mixed0, mixed1, bdata, sdata)
+        others["serving"]["error_vs_oracle"] = errs["serving"]
         others["mixed_f32"]["error_vs_oracle"] = errs["mixed0"]
         others["mixed_f32_refine1"]["error_vs_oracle"] = errs["mixed1"]
         others["batched"]["error_vs_oracle"] = errs["batched"]
@@ -472,7 +556,7 @@ def run_ours(args, world, rank, local):
     r.ctx.close()
 
 
-def cpu_baseline_and_errors(r, main, mixed0, mixed1, bdata):
+def cpu_baseline_and_errors(r, main, mixed0, mixed1, bdata, sdata):
     """The FP64 oracle, as it stands, single-threaded on the host cores: its rate on the main
     workload (repeated for ~10 s) and the error of every GPU result against its outputs."""
     import oracle
@@ -510,6 +594,15 @@ def cpu_baseline_and_errors(r, main, mixed0, mixed1, bdata):
         e = error_pair(xi, yi, rf, Pc[o:o + nn], Qc[o:o + nn])
         worst = [max(worst[0], e["ypp"]), max(worst[1], e["yq"])]
     out["batched"] = {"ypp": worst[0], "yq": worst[1], "sample": "64 of 4096 instances"}
+    sizes_s, seed_s, base_s, sample = sdata
+    worst = [0.0, 0.0]
+    for i, (ypp_i, yq_i) in sample.items():
+        nn = int(sizes_s[i])
+        xi, yi = synth.curve(seed_s, nn, instance=base_s + i)
+        rf = oracle.fit_eval(xi, yi, oracle.NATURAL, oracle.NATURAL, nn)
+        e = error_pair(xi, yi, rf, ypp_i, yq_i)
+        worst = [max(worst[0], e["ypp"]), max(worst[1], e["yq"])]
+    out["serving"] = {"ypp": worst[0], "yq": worst[1], "sample": "%d of the pool's instances" % len(sample)}
     return cpu, out
 
 

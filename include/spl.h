@@ -196,6 +196,53 @@ uint64_t spl_generate_scratch_bytes(uint64_t n);
 spl_status spl_generate_curve(uint64_t seed, uint64_t instance, uint64_t n, double *x, double *y,
                               void *scratch, uint64_t scratch_bytes, void *stream);
 
+/* Serving: continuous batching of independent instances onto a persistent device loop.
+ *
+ * A server owns a persistent kernel (one CTA per SM, cooperative launch) on its own stream:
+ * a scheduler warp takes requests from a ring in mapped host memory and publishes their tiles;
+ * worker warps solve published tiles (binary32 solve and cubic, exact binary64 differences and
+ * query positions: the mixed path without refinement) while further requests arrive, so the
+ * work of requests that arrive while others run overlaps on the device.  A request is admitted
+ * when a slot is free, its tiles fit the tile map and its footprint (16 n + 8 m bytes, plus
+ * 8 n for y'' and 4 m for indices when requested) fits in budget_bytes; otherwise it waits in
+ * a host FIFO and is admitted by a later submit/poll/wait.  The device loop exits after
+ * idle_timeout_ms without work (and after 30 s in any case); the next admission relaunches it.
+ * Requests use device memory (SPL_MEM_DEVICE); results equal those of a single-instance
+ * submission bit for bit, whatever else is in flight.
+ *   max_inflight     requests resident on the device at once (slots), 1..65536.
+ *   tile_rows        knots per tile (0 = 256), >= 16.
+ *   budget_bytes     HBM budget for the footprints of resident requests.
+ *   max_tiles        tile-map capacity (0 = max(2^20, 64 max_inflight)).
+ *   idle_timeout_ms  0 = 200. */
+typedef struct spl_server spl_server;
+typedef struct spl_serve_desc {
+  uint32_t max_inflight;
+  uint32_t tile_rows;
+  uint64_t budget_bytes;
+  uint64_t max_tiles;
+  uint32_t idle_timeout_ms;
+  uint32_t reserved;
+} spl_serve_desc;
+
+spl_status spl_serve_create(spl_ctx *ctx, const spl_serve_desc *desc, spl_server **out);
+/* Queue one request; SPL_OK with a ticket (admitted now or later), or SPL_ERR_BUDGET when it
+ * can never fit, SPL_ERR_INVALID_ARG as spl_submit. */
+spl_status spl_serve_submit(spl_server *srv, const spl_request *req, uint64_t *ticket);
+/* Non-blocking; SPL_PENDING or the final status (the ticket is then released).  latency_ms in
+ * the result is submission to the poll that saw completion. */
+spl_status spl_serve_poll(spl_server *srv, uint64_t ticket, spl_result *res);
+spl_status spl_serve_wait(spl_server *srv, uint64_t ticket, uint64_t timeout_ns, spl_result *res);
+/* Replays an arrival trace: request i (i < count) is pool[pick[i]], submitted at arrival_s[i]
+ * seconds (non-decreasing) after the call starts; latency_ms[i] = time from its scheduled
+ * arrival to the completion seen by the driver.  makespan_s (may be NULL) = first arrival to
+ * last completion.  Returns the first non-OK request status, or SPL_ERR_TIMEOUT 60 s after
+ * the last arrival. */
+spl_status spl_serve_replay(spl_server *srv, const spl_request *pool, uint32_t pool_count, const uint32_t *pick,
+                            const double *arrival_s, uint64_t count, double *latency_ms, double *makespan_s);
+spl_status spl_serve_stats(spl_server *srv, uint64_t *loop_launches, uint64_t *waiting, uint64_t *resident);
+/* Stops the device loop (bounded wait) and releases the server's memory. */
+void spl_serve_destroy(spl_server *srv);
+
 /* One instance without any allocation, for callers that cannot allocate device memory:
  * host applications that own all of the GPU's memory themselves (a simulation or game
  * engine, a database or plug-in host that hands out fixed pools), and code under a hard

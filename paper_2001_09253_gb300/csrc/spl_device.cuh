@@ -28,6 +28,32 @@ struct Inst {
   float *z;             // mixed path with refinement: binary32 y'' of the first pass (n), scratch
 };
 
+// One request appended by the host to the serving ring (mapped host memory).
+struct ServeEntry {
+  Inst inst;
+  unsigned long long first_tile;  // global tile ticket of the request's first tile
+  unsigned slot, seq;
+};
+
+// Arguments of the persistent serving kernel.
+struct ServeArgs {
+  unsigned long long *published, *claimed, *consumed;  // device counters
+  unsigned *stop, *err;                                  // device flags
+  Inst *slot_inst;                                       // per slot
+  unsigned long long *slot_first;
+  unsigned *slot_done, *slot_status, *slot_seq;
+  unsigned *tile_slot;                                   // tile ticket % tile_cap -> slot
+  unsigned long long tile_cap;
+  const volatile unsigned long long *h_tail;             // mapped host memory, written by the host
+  const volatile unsigned *h_stop;
+  const ServeEntry *h_ring;
+  unsigned long long rcap;
+  volatile unsigned long long *h_consumed;               // mapped host memory, written by the device
+  volatile unsigned *h_alive;
+  volatile unsigned *h_done;                             // per slot: status, seq
+  unsigned long long idle_ns, deadline_ns;
+};
+
 // Natural end condition: section "Start and End Derivatives" (slope > 0.99e30).
 __device__ __forceinline__ bool is_natural(double slope) { return slope > 0.99e30; }
 

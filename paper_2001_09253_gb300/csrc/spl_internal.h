@@ -26,6 +26,24 @@ cudaError_t launch_fused_mixed(const Inst *d_insts, int ninst, long long total_t
 cudaError_t launch_refine_mixed(const Inst *d_insts, int ninst, long long total_tiles, long long threads,
                                 unsigned long long *counter, cudaStream_t stream);
 
+// Persistent serving loop (spl_fused_mixed.cu): a cooperative launch of one CTA per SM.
+cudaError_t launch_serve(const ServeArgs &args, int sm_count, cudaStream_t stream);
+int serve_tile_threads();
+
+}  // namespace spl
+
+// Context services for the other host translation units (defined in spl_runtime.cu; each
+// takes the context's lock).
+struct spl_ctx;
+int spl_ctx_device(spl_ctx *c);
+int spl_ctx_sms(spl_ctx *c);
+char *spl_ctx_arena_base(spl_ctx *c);
+bool spl_ctx_arena_alloc(spl_ctx *c, uint64_t bytes, uint64_t *off);
+void spl_ctx_arena_release(spl_ctx *c, uint64_t off, uint64_t bytes);
+void spl_ctx_count_launch(spl_ctx *c, int n);
+
+namespace spl {
+
 // Device curve generator (spl_synth.cu).
 size_t generate_scratch_bytes(long long n);
 cudaError_t launch_generate_curve(uint64_t seed, uint64_t instance, long long n, double *x, double *y,

@@ -387,6 +387,22 @@ void free_job(spl_ctx *c, Job *j) {
 
 }  // namespace
 
+int spl_ctx_device(spl_ctx *c) { return c->device; }
+int spl_ctx_sms(spl_ctx *c) { return c->sm_count; }
+char *spl_ctx_arena_base(spl_ctx *c) { return c->arena; }
+bool spl_ctx_arena_alloc(spl_ctx *c, uint64_t bytes, uint64_t *off) {
+  std::lock_guard<std::mutex> lk(c->mu);
+  return c->dev.alloc(bytes, off);
+}
+void spl_ctx_arena_release(spl_ctx *c, uint64_t off, uint64_t bytes) {
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->dev.release(off, bytes);
+}
+void spl_ctx_count_launch(spl_ctx *c, int n) {
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->stats.kernel_launches += (uint64_t)n;
+}
+
 extern "C" {
 
 const char *spl_status_str(int32_t s) {

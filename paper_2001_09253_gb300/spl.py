@@ -28,7 +28,8 @@ EXPORTS = [
     "spl_status_str", "spl_create", "spl_destroy", "spl_plan_create", "spl_plan_destroy", "spl_submit",
     "spl_submit_batch", "spl_poll", "spl_wait", "spl_get_stats", "spl_batch_create", "spl_batch_launch",
     "spl_batch_wait", "spl_batch_destroy", "spl_generate_scratch_bytes", "spl_generate_curve",
-    "spl_fit_eval_noalloc",
+    "spl_fit_eval_noalloc", "spl_serve_create", "spl_serve_submit", "spl_serve_poll", "spl_serve_wait",
+    "spl_serve_replay", "spl_serve_stats", "spl_serve_destroy",
 ]
 NOALLOC_MAX_N = 1048576
 
@@ -48,6 +49,11 @@ class Request(ctypes.Structure):
                 ("yp1", ctypes.c_double), ("ypn", ctypes.c_double), ("m", ctypes.c_uint64),
                 ("ypp_out", ctypes.c_void_p), ("yq_out", ctypes.c_void_p), ("jq_out", ctypes.c_void_p),
                 ("mem", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ServeDesc(ctypes.Structure):
+    _fields_ = [("max_inflight", ctypes.c_uint32), ("tile_rows", ctypes.c_uint32), ("budget_bytes", ctypes.c_uint64),
+                ("max_tiles", ctypes.c_uint64), ("idle_timeout_ms", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class Result(ctypes.Structure):
@@ -101,9 +107,19 @@ def load(path: str | None = None):
         L.spl_generate_curve.argtypes = [u64, u64, u64, vp, vp, vp, u64, vp]
         L.spl_fit_eval_noalloc.argtypes = [vp, vp, u64, ctypes.c_double, ctypes.c_double, u64, vp, vp, vp,
                                            ctypes.POINTER(i32)]
+        L.spl_serve_create.argtypes = [vp, ctypes.POINTER(ServeDesc), ctypes.POINTER(vp)]
+        L.spl_serve_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(u64)]
+        L.spl_serve_poll.argtypes = [vp, u64, ctypes.POINTER(Result)]
+        L.spl_serve_wait.argtypes = [vp, u64, u64, ctypes.POINTER(Result)]
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.spl_serve_replay.argtypes = [vp, ctypes.POINTER(Request), u32, ctypes.POINTER(u32), dp, u64, dp, dp]
+        L.spl_serve_stats.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        L.spl_serve_destroy.argtypes = [vp]
+        L.spl_serve_destroy.restype = None
         for name in ["spl_create", "spl_plan_create", "spl_submit", "spl_submit_batch", "spl_poll", "spl_wait",
                      "spl_get_stats", "spl_batch_create", "spl_batch_launch", "spl_batch_wait",
-                     "spl_generate_curve", "spl_fit_eval_noalloc"]:
+                     "spl_generate_curve", "spl_fit_eval_noalloc", "spl_serve_create", "spl_serve_submit",
+                     "spl_serve_poll", "spl_serve_wait", "spl_serve_replay", "spl_serve_stats"]:
             getattr(L, name).restype = i32
         _lib = L
         return L
@@ -271,6 +287,71 @@ class Context:
     def close(self):
         if getattr(self, "handle", None):
             self.lib.spl_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server on a persistent device loop (spl_serve_*)."""
+
+    def __init__(self, ctx: Context, max_inflight: int = 1024, tile_rows: int = 256, budget_bytes: int = 1 << 34,
+                 max_tiles: int = 0, idle_timeout_ms: int = 0):
+        self.ctx, self.lib = ctx, ctx.lib
+        d = ServeDesc(max_inflight=int(max_inflight), tile_rows=int(tile_rows), budget_bytes=int(budget_bytes),
+                      max_tiles=int(max_tiles), idle_timeout_ms=int(idle_timeout_ms), reserved=0)
+        h = ctypes.c_void_p()
+        _check(self.lib.spl_serve_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)), "spl_serve_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, x, y, yp1=NATURAL, ypn=NATURAL, m=None, ypp_out=None, yq_out=None, jq_out=None) -> int:
+        r = make_request(x, y, yp1, ypn, m, ypp_out, yq_out, jq_out)
+        t = ctypes.c_uint64()
+        _check(self.lib.spl_serve_submit(self.handle, ctypes.byref(r), ctypes.byref(t)), "spl_serve_submit")
+        self._keep[t.value] = (x, y, ypp_out, yq_out, jq_out)
+        return t.value
+
+    def poll(self, ticket: int):
+        res = Result()
+        s = self.lib.spl_serve_poll(self.handle, int(ticket), ctypes.byref(res))
+        if s != PENDING:
+            self._keep.pop(int(ticket), None)
+        return s, res
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        res = Result()
+        s = self.lib.spl_serve_wait(self.handle, int(ticket), int(timeout_s * 1e9), ctypes.byref(res))
+        if s not in (PENDING, ERR_TIMEOUT):
+            self._keep.pop(int(ticket), None)
+        return s, res
+
+    def replay(self, pool, pick, arrival_s):
+        """Replay an arrival trace (pool: list of Request; pick, arrival_s: numpy arrays)."""
+        n = len(pick)
+        arr = (Request * len(pool))(*pool)
+        pk = np.ascontiguousarray(pick, dtype=np.uint32)
+        at = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        lat = np.zeros(max(n, 1))
+        mk = ctypes.c_double()
+        dp = ctypes.POINTER(ctypes.c_double)
+        s = self.lib.spl_serve_replay(self.handle, arr, len(pool), pk.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                      at.ctypes.data_as(dp), n, lat.ctypes.data_as(dp), ctypes.byref(mk))
+        return s, lat[:n], mk.value
+
+    def stats(self) -> dict:
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(self.lib.spl_serve_stats(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "spl_serve_stats")
+        return {"loop_launches": a.value, "waiting": b.value, "resident": c.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.spl_serve_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -1,0 +1,166 @@
+"""GPU tests of the continuous-batching server (spl_serve_*): results equal a single-instance
+submission bit for bit, alone and in the mix; admission under a small budget; relaunch of the
+device loop after it went idle; per-request error isolation; trace replay."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2001_09253_gb300 import spl, synth
+from parity_util import TOL_MIXED, yq_error, ypp_error
+
+pytestmark = pytest.mark.gpu
+
+NAT = spl.NATURAL
+TILE = 256
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = spl.Context(device=0, arena_bytes=2 << 30, max_slots=4096)
+    yield c
+    c.close()
+
+
+def _pool(count, seed, lo=1e2, hi=2e5):
+    import torch
+    sizes = synth.sizes_loguniform(seed, count, lo, hi)
+    pool = []
+    for i, n in enumerate(sizes):
+        n = int(max(n, 3))
+        x, y = synth.curve(seed, n, instance=i)
+        m = n + (i * 13) % 97
+        bc = (NAT, NAT) if i % 3 else (-1.0, 0.5)
+        pool.append(dict(x=x, y=y, n=n, m=m, bc=bc, xt=torch.from_numpy(x).cuda(), yt=torch.from_numpy(y).cuda()))
+    return pool
+
+
+def _outputs(p):
+    import torch
+    return (torch.full((p["n"],), np.nan, dtype=torch.float64, device="cuda"),
+            torch.full((p["m"],), np.nan, dtype=torch.float64, device="cuda"))
+
+
+def _reference(ctx, p):
+    """The same request through spl_submit with the same tiling (mixed, no refinement)."""
+    plan = ctx.plan(max_n=1 << 26, precision=spl.PREC_F32_REFINE, refine_steps=0, tile_rows=TILE)
+    ypp, yq = _outputs(p)
+    t = ctx.submit(plan, p["xt"], p["yt"], p["bc"][0], p["bc"][1], p["m"], ypp, yq)
+    s, _ = ctx.wait(t)
+    assert s == spl.OK
+    return ypp.cpu().numpy(), yq.cpu().numpy()
+
+
+def test_alone_and_in_the_mix_are_identical(ctx):
+    import torch
+    pool = _pool(48, 5)
+    refs = [_reference(ctx, p) for p in pool]
+    srv = spl.Server(ctx, max_inflight=64, tile_rows=TILE, budget_bytes=1 << 34)
+    # alone: one request at a time
+    for p, ref in zip(pool, refs):
+        ypp, yq = _outputs(p)
+        t = srv.submit(p["xt"], p["yt"], p["bc"][0], p["bc"][1], p["m"], ypp, yq)
+        s, _ = srv.wait(t)
+        assert s == spl.OK
+        assert np.array_equal(ypp.cpu().numpy(), ref[0]) and np.array_equal(yq.cpu().numpy(), ref[1])
+    # in the mix: all in flight together
+    outs, tickets = [], []
+    for p in pool:
+        o = _outputs(p)
+        outs.append(o)
+        tickets.append(srv.submit(p["xt"], p["yt"], p["bc"][0], p["bc"][1], p["m"], o[0], o[1]))
+    for t in tickets:
+        s, _ = srv.wait(t)
+        assert s == spl.OK
+    torch.cuda.synchronize()
+    for o, ref, p in zip(outs, refs, pool):
+        assert np.array_equal(o[0].cpu().numpy(), ref[0]) and np.array_equal(o[1].cpu().numpy(), ref[1])
+    # and both agree with the oracle at the mixed tolerance
+    for o, p in list(zip(outs, pool))[:8]:
+        r = oracle.fit_eval(p["x"], p["y"], p["bc"][0], p["bc"][1], p["m"])
+        assert ypp_error(o[0].cpu().numpy(), r["ypp"]) <= TOL_MIXED
+        assert yq_error(p["x"], p["y"], r["ypp"], r["jq"], o[1].cpu().numpy(), r["yq"]) <= TOL_MIXED
+    srv.close()
+
+
+def test_admission_under_a_small_budget(ctx):
+    pool = _pool(40, 6, lo=1e4, hi=5e4)
+    biggest = max(16 * p["n"] + 8 * p["n"] + 8 * p["m"] for p in pool)
+    srv = spl.Server(ctx, max_inflight=64, tile_rows=TILE, budget_bytes=2 * biggest)
+    outs, tickets = [], []
+    waited = 0
+    for p in pool:
+        o = _outputs(p)
+        outs.append(o)
+        tickets.append(srv.submit(p["xt"], p["yt"], p["bc"][0], p["bc"][1], p["m"], o[0], o[1]))
+        waited = max(waited, srv.stats()["waiting"])
+    assert waited > 0  # some requests had to wait for memory
+    for t in tickets:
+        s, _ = srv.wait(t)
+        assert s == spl.OK
+    for o, p in zip(outs, pool):
+        ref = _reference(ctx, p)
+        assert np.array_equal(o[1].cpu().numpy(), ref[1])
+    # a request larger than the whole budget is refused
+    big = pool[0]
+    with pytest.raises(spl.SplError) as e:
+        srv2 = spl.Server(ctx, max_inflight=4, budget_bytes=1000)
+        try:
+            srv2.submit(big["xt"], big["yt"], NAT, NAT, big["m"], *_outputs(big))
+        finally:
+            srv2.close()
+    assert e.value.status == spl.ERR_BUDGET
+    srv.close()
+
+
+def test_loop_relaunches_after_idle(ctx):
+    pool = _pool(4, 7, lo=1e3, hi=1e4)
+    srv = spl.Server(ctx, max_inflight=8, tile_rows=TILE, idle_timeout_ms=20)
+    for p in pool[:2]:
+        o = _outputs(p)
+        s, _ = srv.wait(srv.submit(p["xt"], p["yt"], p["bc"][0], p["bc"][1], p["m"], o[0], o[1]))
+        assert s == spl.OK
+    time.sleep(0.2)  # the device loop leaves after 20 ms without work
+    for p in pool[2:]:
+        o = _outputs(p)
+        s, _ = srv.wait(srv.submit(p["xt"], p["yt"], p["bc"][0], p["bc"][1], p["m"], o[0], o[1]))
+        assert s == spl.OK
+        assert np.array_equal(o[1].cpu().numpy(), _reference(ctx, p)[1])
+    assert srv.stats()["loop_launches"] >= 2
+    srv.close()
+
+
+def test_bad_request_is_isolated(ctx):
+    import torch
+    pool = _pool(6, 8, lo=1e3, hi=1e4)
+    bad = dict(pool[2])
+    y = bad["y"].copy()
+    y[5] = np.nan
+    bad["yt"] = torch.from_numpy(y).cuda()
+    srv = spl.Server(ctx, max_inflight=16, tile_rows=TILE)
+    items = pool[:2] + [bad] + pool[3:]
+    outs = [_outputs(p) for p in items]
+    tickets = [srv.submit(p["xt"], p["yt"], p["bc"][0], p["bc"][1], p["m"], o[0], o[1]) for p, o in zip(items, outs)]
+    for i, t in enumerate(tickets):
+        s, _ = srv.wait(t)
+        assert s == (spl.ERR_NONFINITE if i == 2 else spl.OK)
+    srv.close()
+
+
+def test_trace_replay(ctx):
+    pool = _pool(64, 9, lo=1e2, hi=1e5)
+    reqs, keep = [], []
+    for p in pool:
+        o = _outputs(p)
+        keep.append(o)
+        reqs.append(spl.make_request(p["xt"], p["yt"], p["bc"][0], p["bc"][1], p["m"], o[0], o[1]))
+    srv = spl.Server(ctx, max_inflight=256, tile_rows=TILE)
+    count = 2000
+    arrivals = synth.poisson_arrivals(3, 20000.0, count)
+    pick = np.arange(count) % len(pool)
+    s, lat, makespan = srv.replay(reqs, pick, arrivals)
+    assert s == spl.OK
+    assert np.all(lat > 0) and np.all(np.isfinite(lat))
+    assert makespan >= arrivals[-1]
+    srv.close()
