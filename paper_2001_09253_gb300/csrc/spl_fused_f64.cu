@@ -6,51 +6,54 @@
 // the uniform grid of "Curve Interpolation".
 //
 // Parallel decomposition (GB300 design, not in the paper).  The serial Thomas sweep is cut
-// into tiles of L knots.  Every tile is solved independently by one thread:
-//   * the forward elimination starts kHaloF rows before the tile with the guess
-//     c' = d' = 0.  With b = 2(a + c) the multiplier a/(b - a c') is below 2/3 (c' <= 1/2),
-//     so the error of the guess shrinks by at least that factor per row: after 96 rows it
-//     is below 1.2e-17 of max|d'|;
-//   * the back substitution of a segment of kSeg rows starts kHaloB rows past it with the
-//     guess y'' = d'; its error shrinks by c' < 1/2 per row (below 6e-20 after 64 rows).
-// Forward results (c', d', 1/h) of the last kSeg + kHaloB rows live in a per-thread ring in
-// shared memory (192 KB for the CTA's 128 threads; lane-interleaved, conflict-free).  After
-// each segment's back substitution the thread writes its y'' and evaluates the queries whose
-// interval lies in the segment, walking the uniform grid and the knots together (the
-// monotone sweep of "Quality Checks").  1/h_j computed by the fit is reused by the
-// evaluation, so each knot costs two reciprocals; h_j is recomputed exactly.
+// into tiles of L knots.  Every tile is solved independently by one thread, in three passes
+// over per-thread global scratch (lane-interleaved, so warp accesses are coalesced when the
+// lanes move together):
+//   1. forward elimination, started some rows before the tile from the guess c' = d' = 0.
+//      With b = 2(a + c) and c' <= 1/2, row i passes on the error of d' multiplied by at most
+//      a_i / (1.5 a_i + 2 c_i) (< 2/3): the halo is grown backwards from the tile until the
+//      product of these bounds, computed on the integer/FP32 pipes from the knot widths, is
+//      below 2^-110 (at least 16 rows, so that c' has converged too, at most 192 rows, where
+//      even the worst case is below 2^-112).  The target is far below binary64 resolution
+//      because d' at the halo start may exceed the solution inside the tile by many orders of
+//      magnitude (knot gaps spread over many decades).  c', d' and 1/h of the tile's rows and
+//      of kHaloB rows past its end go to the scratch;
+//   2. back substitution from kHaloB rows past the tile, from the guess y'' = d', once over
+//      the whole tile; its error is multiplied by c'_i <= c_i / (1.5 a_i + 2 c_i) < 1/2 per
+//      row (typically ~0.27, ~1e-27 after 48 rows; 3.6e-15 in the worst case).  y'' replaces
+//      d' in the scratch;
+//   3. evaluation of the queries whose interval lies in the tile, walking the uniform grid
+//      and the knots together (the monotone sweep of "Quality Checks"), with the fit's 1/h_j.
 //
-// GB300 notes: FP64 runs at ~1.7 lanes/clk/SM here (one warp per SM sub-partition fills
-// it), so the kernel is FP64-pipe bound: one persistent CTA of four warps per SM, the ring
-// in shared memory so that no dependent load waits on L2, comparisons on integer keys and
-// divisions as a MUFU seed + 3 DFMAs.
+// GB300 notes: FP64 runs at ~1.7 lanes/clk/SM here and one warp per SM sub-partition cannot
+// keep the pipe busy through its own dependency chains, so the kernel runs two CTAs of four
+// warps per SM (two warps per sub-partition).  Scratch instead of a shared-memory ring frees
+// the shared memory for that and removes the per-segment halo recomputation; the back
+// substitution's loads do not depend on the recurrence and are issued four rows ahead.
+// Comparisons run on integer keys, divisions as a MUFU seed + 3 DFMAs, and the next row's
+// width, reciprocal and slope are computed while the current row's elimination is in flight.
 #include <algorithm>
 
 #include "spl_device.cuh"
 #include "spl_internal.h"
+#include "spl_numeric.h"
 
 namespace spl {
 
-constexpr int kThreads = 128;           // one CTA per SM, one warp per sub-partition
-constexpr int kSeg = 16;                // rows per back-substitution segment
-constexpr int kHaloB = 48;              // back-substitution halo: error <= 2^-48 of max|y''|
-constexpr int kRing = kSeg + kHaloB;    // ring rows per thread (a power of two)
-static_assert((kRing & (kRing - 1)) == 0, "ring size must be a power of two");
-constexpr int kHaloF = 96;              // forward-elimination halo: error <= (2/3)^96
+constexpr int kThreads = 128;           // four warps per CTA
+constexpr int kCtasPerSm = 2;           // two warps per SM sub-partition
+constexpr int kHaloB = 48;              // back-substitution start past the tile end
+constexpr int kHaloFMax = 192;          // forward-elimination halo, worst case: (2/3)^192
+constexpr int kHaloFMin = 16;
 constexpr int kFields = 3;              // c', d' (then y''), 1/h
-constexpr size_t kSmemBytes = (size_t)kRing * kFields * kThreads * sizeof(double);
 
-struct Ring64 {
-  double *base;  // shared memory of the CTA
-  int tid;
-  __device__ __forceinline__ double &at(int row, int f) const {
-    return base[(row * kFields + f) * kThreads + tid];
+// Per-warp scratch: rows relative to the tile start, fields, lanes.
+struct Scratch64 {
+  double *base;
+  int lane;
+  __device__ __forceinline__ double &at(long long row, int f) const {
+    return base[(((size_t)row * kFields + f) << 5) + lane];
   }
-};
-
-// State of the forward sweep after row r: the knot and value at r+1, h_r, s_r, c'_r, d'_r.
-struct Fwd64 {
-  double xn, yn, h, s, cp, dp;
 };
 
 // Evaluation of one query, "Fast Interpolation": with ba = x_{j+1}-x_j, xa = x-x_j,
@@ -67,8 +70,6 @@ __device__ __forceinline__ double newint64(double q, double xj, double xj1, doub
   return (lower + (1.0 / 6.0) * (C + D)) * inv_ba;
 }
 
-__device__ __forceinline__ int slot_of(long long j, long long s0) { return (int)(j - s0) & (kRing - 1); }
-
 // 2t for a normal t by incrementing its exponent (integer pipe); other values take an
 // out-of-line FP64 multiply, so that it is never evaluated speculatively.
 __device__ __noinline__ double twice_slow(double t) { return 2.0 * t; }
@@ -83,7 +84,41 @@ __device__ __forceinline__ void prefetch_l1(const void *p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
-__device__ void tile_f64(const Inst &I, long long tile, const Ring64 &ring) {
+// Width of interval i in binary32 for the decay bounds (never used as a value of the method);
+// negative when the integer route does not apply.
+__device__ __forceinline__ float width32(const double *x, long long i) {
+  float v;
+  return diff_same_f32(x[i + 1], x[i], &v) ? v : -1.0f;
+}
+
+// Start row of the forward halo of a tile beginning at s0 (see the header comment).
+__device__ long long halo_start(const double *x, long long n, long long s0) {
+  if (s0 <= kHaloFMin) return 0;
+  float prod = 1.0f;
+  float c = (s0 + 1 < n) ? width32(x, s0) : -1.0f;  // c_i = h_i
+  long long i = s0;
+  for (int cnt = 1; cnt <= kHaloFMax; ++cnt) {
+    const float a = width32(x, i - 1);  // a_i = h_{i-1}
+    const float f = (a > 0.0f && c > 0.0f) ? a / (1.5f * a + 2.0f * c) : 0.6667f;
+    prod *= f * 1.0001f;
+    if (cnt >= kHaloFMin && prod < 0x1p-110f) return i - 1;
+    if (i - 1 == 0) return 0;
+    --i;
+    c = a;
+  }
+  return max(s0 - kHaloFMax, 0LL);
+}
+
+// Forward state after row r: c'_r, d'_r, h_r, s_r, the precomputed interval r+1
+// (xn = x_{r+2}, yn = y_{r+2}, hn = h_{r+1}, ihn = 1/h_{r+1}, sn = s_{r+1}), and the knot and
+// value of the row after that, loaded one step ahead (xl = x_{r+3}, yl = y_{r+3}).
+struct Fwd64 {
+  double cp, dp, h, s;
+  double xn, yn, hn, ihn, sn;
+  double xl, yl;
+};
+
+__device__ void tile_f64(const Inst &I, long long tile, const Scratch64 &S) {
   const long long n = I.n, m = I.m;
   const double *__restrict__ x = I.x;
   const double *__restrict__ y = I.y;
@@ -92,13 +127,32 @@ __device__ void tile_f64(const Inst &I, long long tile, const Ring64 &ring) {
   validate_rows(I, s0, e0);
 
   const bool nat0 = is_natural(I.yp1), nat1 = is_natural(I.ypn);
-  // ---- forward elimination up to row s0 (halo rows are not stored) ----
-  long long r = max(s0 - kHaloF, 0LL);  // row whose (c', d') the state holds
+  // ---- 1. forward elimination ----
+  long long r = halo_start(x, n, s0);  // row whose (c', d') the state holds
   Fwd64 F;
+  F.hn = F.ihn = F.sn = 0.0;
+  F.xl = F.yl = 0.0;
+  // interval j (= r+1 of the state) when it exists: uses x_{j+1}, y_{j+1} (loaded one step
+  // earlier) and issues the loads of x_{j+2}, y_{j+2} for the next step
+  auto precompute_next = [&](long long j) {
+    if (j <= n - 2) {
+      const double x2 = F.xl, y2 = F.yl;
+      if (j + 2 < n) {
+        if (j + 18 < n) { prefetch_l1(x + j + 18); prefetch_l1(y + j + 18); }
+        F.xl = x[j + 2];
+        F.yl = y[j + 2];
+      }
+      F.hn = x2 - F.xn;
+      F.ihn = rcp64(F.hn);
+      F.sn = quot64(y2 - F.yn, F.hn, F.ihn);
+      F.xn = x2;
+      F.yn = y2;
+    }
+  };
   {
-    double x0 = x[r], x1 = x[r + 1], y0 = y[r], y1 = y[r + 1];
-    double h = x1 - x0, ih = rcp64(h), sl = quot64(y1 - y0, h, ih);
-    F.xn = x1; F.yn = y1; F.h = h; F.s = sl;
+    const double x0 = x[r], x1 = x[r + 1], y0 = y[r], y1 = y[r + 1];
+    const double h = x1 - x0, ih = rcp64(h), sl = quot64(y1 - y0, h, ih);
+    F.h = h; F.s = sl; F.xn = x1; F.yn = y1;
     if (r == 0 && !nat0) {            // clamped start: c'_0 = 1/2, d'_0 = 3(s_0 - y'_0)/h_0
       F.cp = 0.5;
       F.dp = 3.0 * (sl - I.yp1) * ih;
@@ -107,105 +161,110 @@ __device__ void tile_f64(const Inst &I, long long tile, const Ring64 &ring) {
       F.dp = 0.0;
     }
     if (r >= s0) {                    // r == s0 == 0: row 0 is this tile's first row
-      ring.at(0, 0) = F.cp; ring.at(0, 1) = F.dp; ring.at(0, 2) = ih;
+      S.at(0, 0) = F.cp; S.at(0, 1) = F.dp; S.at(0, 2) = ih;
+    }
+    if (r + 2 < n) {
+      F.xl = x[r + 2];
+      F.yl = y[r + 2];
+    }
+    precompute_next(r + 1);
+  }
+  const long long rlast = min(e0 + kHaloB, n) - 1;
+  while (r < rlast) {
+    const long long j = r + 1;
+    double cpj, dpj, ihj = 0.0;
+    if (j <= n - 2) {
+      const double hj = F.hn, sj = F.sn;
+      ihj = F.ihn;
+      const double den = twice(F.h + hj) - F.h * F.cp;
+      const double iden = rcp64(den);
+      cpj = hj * iden;
+      dpj = (6.0 * (sj - F.s) - F.h * F.dp) * iden;
+      F.h = hj; F.s = sj;
+      precompute_next(j + 1);  // independent of the elimination chain above
+    } else {  // j == n-1: last row
+      cpj = 0.0;
+      if (nat1) {
+        dpj = 0.0;
+      } else {
+        const double den = 2.0 * F.h - F.h * F.cp;
+        dpj = (6.0 * (I.ypn - F.s) - F.h * F.dp) * rcp64(den);
+      }
+    }
+    F.cp = cpj; F.dp = dpj;
+    r = j;
+    if (j >= s0) {
+      S.at(j - s0, 0) = cpj; S.at(j - s0, 1) = dpj; S.at(j - s0, 2) = ihj;
     }
   }
-  // advance the forward sweep so that the state holds row `target`, storing rows >= s0
-  auto forward_to = [&](long long target) {
-    while (r < target) {
-      const long long j = r + 1;
-      double cpj, dpj, ihj = 0.0;
-      if (j <= n - 2) {
-        if (j + 17 < n) { prefetch_l1(x + j + 17); prefetch_l1(y + j + 17); }
-        double x2 = x[j + 1], y2 = y[j + 1];
-        double hj = x2 - F.xn;
-        ihj = rcp64(hj);
-        double sj = quot64(y2 - F.yn, hj, ihj);
-        double den = twice(F.h + hj) - F.h * F.cp;
-        double iden = rcp64(den);
-        cpj = hj * iden;
-        dpj = (6.0 * (sj - F.s) - F.h * F.dp) * iden;
-        F.xn = x2; F.yn = y2; F.h = hj; F.s = sj;
-      } else {  // j == n-1: last row
-        cpj = 0.0;
-        if (nat1) {
-          dpj = 0.0;
-        } else {
-          double den = 2.0 * F.h - F.h * F.cp;
-          dpj = (6.0 * (I.ypn - F.s) - F.h * F.dp) * rcp64(den);
-        }
-      }
-      F.cp = cpj; F.dp = dpj;
-      r = j;
-      if (j >= s0) {
-        const int slot = slot_of(j, s0);
-        ring.at(slot, 0) = cpj; ring.at(slot, 1) = dpj; ring.at(slot, 2) = ihj;
-      }
-    }
-  };
-  if (s0 > 0) forward_to(s0);
 
-  const Grid G = make_grid(x, n, m);
-  long long k = first_query(G, x, s0);
-  // ---- segments ----
-  for (long long a = s0; a < e0; a += kSeg) {
-    const long long b = min(a + kSeg, e0);
-    const long long rlast = min(b + kHaloB, n) - 1;
-    forward_to(rlast);
-    // back substitution from rlast down to a; rows [a, b) get y'' in field 1
-    double Y = ring.at(slot_of(rlast, s0), 1);  // y''_{rlast} := d'_{rlast} (exact when rlast == n-1)
-    double Yb = Y;                              // y''_b (if b <= rlast)
-    for (long long j = rlast - 1; j >= a; --j) {
-      const int slot = slot_of(j, s0);
-      Y = ring.at(slot, 1) - ring.at(slot, 0) * Y;
-      if (j == b) Yb = Y;
-      if (j < b) ring.at(slot, 1) = Y;
+  // ---- 2. back substitution over the tile (y''_{rlast} := d'_{rlast}, exact when rlast == n-1) ----
+  {
+    const long long tl = rlast - s0;
+    double Y = S.at(tl, 1);
+    long long t = tl - 1;
+    for (; t >= 3; t -= 4) {  // loads of four rows first: they do not depend on Y
+      const double c0 = S.at(t, 0), d0 = S.at(t, 1), c1 = S.at(t - 1, 0), d1 = S.at(t - 1, 1);
+      const double c2 = S.at(t - 2, 0), d2 = S.at(t - 2, 1), c3 = S.at(t - 3, 0), d3 = S.at(t - 3, 1);
+      const double Y0 = d0 - c0 * Y;
+      const double Y1 = d1 - c1 * Y0;
+      const double Y2 = d2 - c2 * Y1;
+      const double Y3 = d3 - c3 * Y2;
+      S.at(t, 1) = Y0; S.at(t - 1, 1) = Y1; S.at(t - 2, 1) = Y2; S.at(t - 3, 1) = Y3;
+      Y = Y3;
+    }
+    for (; t >= 0; --t) {
+      Y = S.at(t, 1) - S.at(t, 0) * Y;
+      S.at(t, 1) = Y;
     }
     if (I.ypp) {
-      for (long long j = a; j < b; ++j) I.ypp[j] = ring.at(slot_of(j, s0), 1);
+      for (long long j = s0; j < e0; ++j) I.ypp[j] = S.at(j - s0, 1);
     }
-    // queries whose interval j lies in [a, b): x_k > x_a (guaranteed by k's position)
-    // and x_k <= x_b when b <= n-2
-    if (m > 0 && a <= n - 2) {
-      const long long jmax = min(b, n - 1) - 1;  // last interval of the segment
-      const bool bounded = (b <= n - 2);
-      const long long kb = bounded ? dkey(x[b]) : 0;
-      long long j = a;
-      double xj = x[j], xj1 = x[j + 1], yj = y[j], yj1 = y[j + 1];
-      double hj = xj1 - xj;
-      long long kxj1 = dkey(xj1);
-      while (k < m) {
-        const double q = G.at(k);
-        const long long kq = dkey(q);
-        if (bounded && kq > kb) break;
-        if (j < jmax && kxj1 < kq) {
-          do {
-            ++j;
-            if (j + 17 < n) { prefetch_l1(x + j + 17); prefetch_l1(y + j + 17); }
-            xj = xj1; yj = yj1;
-            xj1 = x[j + 1]; yj1 = y[j + 1];
-            kxj1 = dkey(xj1);
-          } while (j < jmax && kxj1 < kq);
-          hj = xj1 - xj;
-        }
-        const int slot = slot_of(j, s0);
-        const double ppj = ring.at(slot, 1);
-        const double ppj1 = (j + 1 == b) ? Yb : ring.at(slot_of(j + 1, s0), 1);
-        I.yq[k] = newint64(q, xj, xj1, yj, yj1, ppj, ppj1, hj, ring.at(slot, 2));
-        if (I.jq) I.jq[k] = (int32_t)j;
-        ++k;
+  }
+
+  // ---- 3. evaluation of the queries whose interval j lies in [s0, e0): x_k > x_{s0}
+  //         (first_query) and x_k <= x_{e0} when e0 <= n-2 ----
+  if (m > 0 && s0 <= n - 2) {
+    const Grid G = make_grid(x, n, m);
+    long long k = first_query(G, x, s0);
+    const long long jmax = min(e0, n - 1) - 1;
+    const bool bounded = (e0 <= n - 2);
+    const long long kb = bounded ? dkey(x[e0]) : 0;
+    long long j = s0;
+    double xj = x[j], xj1 = x[j + 1], yj = y[j], yj1 = y[j + 1];
+    double hj = xj1 - xj;
+    double ppj = S.at(0, 1), ppj1 = S.at(1, 1), ihj = S.at(0, 2);
+    long long kxj1 = dkey(xj1);
+    while (k < m) {
+      const double q = G.at(k);
+      const long long kq = dkey(q);
+      if (bounded && kq > kb) break;
+      if (j < jmax && kxj1 < kq) {
+        do {
+          ++j;
+          xj = xj1; yj = yj1;
+          xj1 = x[j + 1]; yj1 = y[j + 1];
+          kxj1 = dkey(xj1);
+        } while (j < jmax && kxj1 < kq);
+        hj = xj1 - xj;
+        ppj = S.at(j - s0, 1);
+        ppj1 = S.at(j + 1 - s0, 1);
+        ihj = S.at(j - s0, 2);
       }
+      I.yq[k] = newint64(q, xj, xj1, yj, yj1, ppj, ppj1, hj, ihj);
+      if (I.jq) I.jq[k] = (int32_t)j;
+      ++k;
     }
   }
 }
 
 // Persistent CTAs; each warp fetches 32 tiles at a time from a counter zeroed before the
 // launch, so tiles of uneven length (ragged tails, small instances) balance across SMs.
-__global__ void __launch_bounds__(kThreads, 1) fused_f64_kernel(const Inst *__restrict__ insts, int ninst,
-                                                                long long total_tiles,
-                                                                unsigned long long *__restrict__ counter) {
-  extern __shared__ double smem_ring[];
-  Ring64 ring{smem_ring, (int)threadIdx.x};
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
+    fused_f64_kernel(const Inst *__restrict__ insts, int ninst, long long total_tiles,
+                     unsigned long long *__restrict__ counter, double *__restrict__ scratch, long long rows_cap) {
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const Scratch64 S{scratch + (size_t)warp * rows_cap * kFields * 32, (int)(threadIdx.x & 31)};
   const int lane = threadIdx.x & 31;
   for (;;) {
     unsigned long long base = 0;
@@ -216,28 +275,30 @@ __global__ void __launch_bounds__(kThreads, 1) fused_f64_kernel(const Inst *__re
     if (t < total_tiles) {
       const int i = find_inst(insts, ninst, t);
       const Inst I = insts[i];
-      tile_f64(I, t - I.tile_begin, ring);
+      tile_f64(I, t - I.tile_begin, S);
     }
     __syncwarp();
   }
 }
 
-size_t ring_bytes_f64(long long) { return 0; }  // the ring lives in shared memory
+size_t ring_bytes_f64(long long threads, int tile_rows) {
+  const long long warps = (threads + 31) / 32;
+  return (size_t)warps * ((size_t)tile_rows + kHaloB) * kFields * 32 * sizeof(double);
+}
 
-int halo_rows_f64() { return kHaloF + kHaloB; }
+int halo_rows_f64() { return kHaloFMax + kHaloB; }
 
 long long threads_f64(int sm_count, long long total_tiles) {
-  long long blocks = std::min<long long>((total_tiles + kThreads - 1) / kThreads, (long long)sm_count);
+  long long blocks =
+      std::min<long long>((total_tiles + kThreads - 1) / kThreads, (long long)kCtasPerSm * sm_count);
   return std::max<long long>(blocks, 1) * kThreads;
 }
 
-cudaError_t launch_fused_f64(const Inst *d_insts, int ninst, long long total_tiles, double *,
-                             long long threads, unsigned long long *counter, cudaStream_t stream) {
-  cudaError_t e = cudaFuncSetAttribute(fused_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kSmemBytes);
-  if (e != cudaSuccess) return e;
+cudaError_t launch_fused_f64(const Inst *d_insts, int ninst, long long total_tiles, double *scratch,
+                             int tile_rows, long long threads, unsigned long long *counter, cudaStream_t stream) {
   const long long grid = threads / kThreads;
-  fused_f64_kernel<<<(unsigned)grid, kThreads, kSmemBytes, stream>>>(d_insts, ninst, total_tiles, counter);
+  fused_f64_kernel<<<(unsigned)grid, kThreads, 0, stream>>>(d_insts, ninst, total_tiles, counter, scratch,
+                                                            (long long)tile_rows + kHaloB);
   return cudaGetLastError();
 }
 

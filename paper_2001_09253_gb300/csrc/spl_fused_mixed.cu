@@ -451,11 +451,14 @@ __global__ void __launch_bounds__(kThreadsM, 1) serve_kernel(ServeArgs a) {
       if (consumed < tail) {
         __threadfence_system();  // the entry was written before the tail: read it after
         const ServeEntry *e = a.h_ring + (consumed % a.rcap);
-        // the entry is read word by word through volatile loads of mapped host memory
+        // one 8-byte word of the entry per lane from mapped host memory, shared by shuffles
+        constexpr int kWords = (int)(sizeof(ServeEntry) / 8);
+        static_assert(kWords <= 32, "a serving entry must fit in one warp's loads");
         const volatile unsigned long long *src = reinterpret_cast<const volatile unsigned long long *>(e);
+        const unsigned long long word = (lane < kWords) ? src[lane] : 0ull;
         ServeEntry ent;
         unsigned long long *dst = reinterpret_cast<unsigned long long *>(&ent);
-        for (int w = 0; w < (int)(sizeof(ServeEntry) / 8); ++w) dst[w] = src[w];
+        for (int w = 0; w < kWords; ++w) dst[w] = __shfl_sync(0xffffffffu, word, w);
         const unsigned slot = ent.slot;
         if (lane == 0) {
           ent.inst.status = a.slot_status + slot;

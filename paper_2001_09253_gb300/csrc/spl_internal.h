@@ -8,14 +8,14 @@
 
 namespace spl {
 
-// FP64 fused fit + evaluation (spl_fused_f64.cu).  `threads` must be a multiple of 128;
-// `ring` must hold ring_bytes_f64(threads) bytes.
-size_t ring_bytes_f64(long long threads);
+// FP64 fused fit + evaluation (spl_fused_f64.cu).  `threads` comes from threads_f64; `scratch`
+// must hold ring_bytes_f64(threads, tile_rows) bytes, tile_rows being the longest tile of the
+// launch; `counter` (8 bytes of device memory) must be zero when the kernel starts.
+size_t ring_bytes_f64(long long threads, int tile_rows);
 long long threads_f64(int sm_count, long long total_tiles);
 int halo_rows_f64();
-// `counter` (8 bytes of device memory) must be zero when the kernel starts.
-cudaError_t launch_fused_f64(const Inst *d_insts, int ninst, long long total_tiles, double *ring,
-                             long long threads, unsigned long long *counter, cudaStream_t stream);
+cudaError_t launch_fused_f64(const Inst *d_insts, int ninst, long long total_tiles, double *scratch,
+                             int tile_rows, long long threads, unsigned long long *counter, cudaStream_t stream);
 
 // Mixed-precision fused fit + evaluation (spl_fused_mixed.cu).
 long long threads_mixed(int sm_count, long long total_tiles);

@@ -171,10 +171,9 @@ spl_status check_request(const spl_plan *plan, const spl_request *r) {
   return SPL_OK;
 }
 
-// Launch geometry of the FP64 kernel: one thread per tile up to four warps per SM (the
-// FP64 pipe is full at one warp per SM sub-partition); more tiles are strided over them.
-// The mixed-precision kernel runs two warps per sub-partition (its binary32 and integer work
-// needs the latency hiding; its ring is half the size).
+// Launch geometry: both kernels run persistent CTAs with 256 threads per SM (two warps per
+// SM sub-partition, which the dependency chains of either kernel need to keep the pipes
+// busy); one thread per tile, tiles fetched dynamically.
 long long threads_for(const spl_ctx *c, int precision, long long total_tiles) {
   return precision == SPL_PREC_F64 ? spl::threads_f64(c->sm_count, total_tiles)
                                    : spl::threads_mixed(c->sm_count, total_tiles);
@@ -183,7 +182,7 @@ long long threads_for(const spl_ctx *c, int precision, long long total_tiles) {
 // Tile length so that one instance of total_points fills every thread of one wave; never
 // shorter than a few halos.
 int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points) {
-  const long long per_sm = precision == SPL_PREC_F64 ? 128 : 256;
+  const long long per_sm = 256;  // both kernels run 256 threads per SM
   long long target = (long long)c->sm_count * per_sm;
   long long L = (long long)((total_points + target - 1) / target);
   L = std::max<long long>(L, precision == SPL_PREC_F64 ? 256 : 128);
@@ -201,6 +200,7 @@ struct Staged {
 struct LaunchPlan {
   int precision = SPL_PREC_F64;
   int refine_steps = 0;
+  int tile_rows = 0;
   std::vector<Inst> insts;
   long long total_tiles = 0;
   long long threads = 0;
@@ -255,7 +255,8 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
   }
   lp.total_tiles = tiles;
   lp.threads = threads_for(c, p->precision, tiles);
-  lp.ring_bytes = p->precision == SPL_PREC_F64 ? spl::ring_bytes_f64(lp.threads) : 0;
+  lp.tile_rows = L;
+  lp.ring_bytes = p->precision == SPL_PREC_F64 ? spl::ring_bytes_f64(lp.threads, L) : 0;
 
   // footprint check against the whole budget first
   uint64_t need = round_up(sizeof(Inst) * count, kAlign) + round_up(status_block_bytes(count), kAlign) +
@@ -329,7 +330,7 @@ cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, 
   cudaError_t e;
   if (lp.precision == SPL_PREC_F64) {
     e = spl::launch_fused_f64(insts, count, lp.total_tiles, reinterpret_cast<double *>(c->arena + d_ring_off),
-                              lp.threads, counters, st);
+                              lp.tile_rows, lp.threads, counters, st);
   } else if (lp.refine_steps == 0) {
     e = spl::launch_fused_mixed(insts, count, lp.total_tiles, lp.threads, counters, st, false);
   } else {

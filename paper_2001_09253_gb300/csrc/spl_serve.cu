@@ -69,6 +69,7 @@ struct spl_server {
   unsigned next_seq = 1;
   uint64_t bytes_inflight = 0;
   std::vector<unsigned> free_slots;
+  std::vector<unsigned> resident;  // slots holding a request (only these are polled)
   std::vector<uint64_t> slot_ticket;
   std::map<uint64_t, int> live_first;  // first tiles of resident requests
   std::deque<uint64_t> waiting;
@@ -107,11 +108,16 @@ bool loop_running(spl_server *s) {
 // Completions, then admissions, then make sure the device loop runs if anything is resident.
 spl_status pump(spl_server *s) {
   const double t = now_s();
-  for (unsigned slot = 0; slot < s->d.max_inflight; ++slot) {
+  for (size_t ri = 0; ri < s->resident.size();) {
+    const unsigned slot = s->resident[ri];
     const uint64_t tk = s->slot_ticket[slot];
-    if (!tk) continue;
     Req &r = s->reqs[tk];
-    if (s->h_done[2 * slot + 1] != r.seq) continue;
+    if (s->h_done[2 * slot + 1] != r.seq) {
+      ++ri;
+      continue;
+    }
+    s->resident[ri] = s->resident.back();
+    s->resident.pop_back();
     std::atomic_thread_fence(std::memory_order_acquire);
     const unsigned bits = s->h_done[2 * slot];
     r.status = (bits & spl::kStNonFinite) ? SPL_ERR_NONFINITE : (bits & spl::kStNotIncreasing) ? SPL_ERR_NOT_INCREASING
@@ -143,6 +149,7 @@ spl_status pump(spl_server *s) {
     s->bytes_inflight += r.bytes;
     s->live_first[r.first_tile]++;
     s->slot_ticket[r.slot] = tk;
+    s->resident.push_back(r.slot);
     r.state = 1;
     ServeEntry &e = s->h_ring[s->tail % s->args.rcap];
     e.inst = r.inst;
@@ -154,9 +161,7 @@ spl_status pump(spl_server *s) {
     std::atomic_thread_fence(std::memory_order_seq_cst);
     admitted = true;
   }
-  bool resident = false;
-  for (unsigned slot = 0; slot < s->d.max_inflight && !resident; ++slot) resident = s->slot_ticket[slot] != 0;
-  if ((admitted || resident) && !loop_running(s)) return relaunch(s);
+  if ((admitted || !s->resident.empty()) && !loop_running(s)) return relaunch(s);
   return SPL_OK;
 }
 
