@@ -84,6 +84,10 @@ __device__ __forceinline__ void prefetch_l1(const void *p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Width of interval i in binary32 for the decay bounds (never used as a value of the method);
 // negative when the integer route does not apply.
 __device__ __forceinline__ float width32(const double *x, long long i) {
@@ -91,20 +95,33 @@ __device__ __forceinline__ float width32(const double *x, long long i) {
   return diff_same_f32(x[i + 1], x[i], &v) ? v : -1.0f;
 }
 
-// Start row of the forward halo of a tile beginning at s0 (see the header comment).
+// Start row of the forward halo of a tile beginning at s0 (see the header comment).  Rows are
+// scanned eight at a time with independent loads; the halo may end up a few rows longer than
+// the bound requires.
 __device__ long long halo_start(const double *x, long long n, long long s0) {
-  if (s0 <= kHaloFMin) return 0;
+  if (s0 <= kHaloFMin + 8) return 0;
   float prod = 1.0f;
-  float c = (s0 + 1 < n) ? width32(x, s0) : -1.0f;  // c_i = h_i
+  // bound of row i uses a_i = h_{i-1} = x_i - x_{i-1} and c_i = h_i = x_{i+1} - x_i
+  double xr = (s0 + 1 < n) ? x[s0 + 1] : x[s0];  // x_{i+1} for the first row i = s0
   long long i = s0;
-  for (int cnt = 1; cnt <= kHaloFMax; ++cnt) {
-    const float a = width32(x, i - 1);  // a_i = h_{i-1}
-    const float f = (a > 0.0f && c > 0.0f) ? a / (1.5f * a + 2.0f * c) : 0.6667f;
-    prod *= f * 1.0001f;
-    if (cnt >= kHaloFMin && prod < 0x1p-110f) return i - 1;
-    if (i - 1 == 0) return 0;
-    --i;
-    c = a;
+  for (int cnt = 0; cnt < kHaloFMax; cnt += 8) {
+    if (i - 8 <= 0) return 0;
+    double xv[9];
+#pragma unroll
+    for (int u = 0; u < 9; ++u) xv[u] = x[i - u];  // x_i .. x_{i-8}
+    float c;
+    if (!diff_same_f32(xr, xv[0], &c) || !(s0 + 1 < n)) c = -1.0f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      float a;
+      if (!diff_same_f32(xv[u], xv[u + 1], &a)) a = -1.0f;
+      const float f = (a > 0.0f && c > 0.0f) ? a / (1.5f * a + 2.0f * c) : 0.6667f;
+      prod *= f * 1.0001f;
+      c = a;
+    }
+    xr = xv[7];  // x_{i'+1} of the next chunk's first row i' = i - 8
+    i -= 8;      // rows s0 .. i+1 are covered; the guess goes on row i
+    if (cnt + 8 >= kHaloFMin && prod < 0x1p-110f) return i;
   }
   return max(s0 - kHaloFMax, 0LL);
 }
@@ -203,15 +220,23 @@ __device__ void tile_f64(const Inst &I, long long tile, const Scratch64 &S) {
     const long long tl = rlast - s0;
     double Y = S.at(tl, 1);
     long long t = tl - 1;
-    for (; t >= 3; t -= 4) {  // loads of four rows first: they do not depend on Y
-      const double c0 = S.at(t, 0), d0 = S.at(t, 1), c1 = S.at(t - 1, 0), d1 = S.at(t - 1, 1);
-      const double c2 = S.at(t - 2, 0), d2 = S.at(t - 2, 1), c3 = S.at(t - 3, 0), d3 = S.at(t - 3, 1);
-      const double Y0 = d0 - c0 * Y;
-      const double Y1 = d1 - c1 * Y0;
-      const double Y2 = d2 - c2 * Y1;
-      const double Y3 = d3 - c3 * Y2;
-      S.at(t, 1) = Y0; S.at(t - 1, 1) = Y1; S.at(t - 2, 1) = Y2; S.at(t - 3, 1) = Y3;
-      Y = Y3;
+    constexpr int kB = 8;
+    for (; t >= kB - 1; t -= kB) {  // loads of eight rows first: they do not depend on Y
+      if (t >= 40) {
+        prefetch_l2(&S.at(t - 32, 0));
+        prefetch_l2(&S.at(t - 36, 0));
+      }
+      double cc[kB], dd[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        cc[u] = S.at(t - u, 0);
+        dd[u] = S.at(t - u, 1);
+      }
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        Y = dd[u] - cc[u] * Y;
+        S.at(t - u, 1) = Y;
+      }
     }
     for (; t >= 0; --t) {
       Y = S.at(t, 1) - S.at(t, 0) * Y;
@@ -247,6 +272,8 @@ __device__ void tile_f64(const Inst &I, long long tile, const Scratch64 &S) {
           kxj1 = dkey(xj1);
         } while (j < jmax && kxj1 < kq);
         hj = xj1 - xj;
+        if (j + 9 < n) { prefetch_l1(x + j + 9); prefetch_l1(y + j + 9); }
+        if (j + 8 < rlast) prefetch_l1(&S.at(j + 8 - s0, 0));
         ppj = S.at(j - s0, 1);
         ppj1 = S.at(j + 1 - s0, 1);
         ihj = S.at(j - s0, 2);
