@@ -55,9 +55,10 @@ __device__ __noinline__ F2 sub_f64_f2(double b, double a) {
   return F2{hi, (float)(d - (double)hi)};
 }
 
-// neighbouring operands (same binade almost always)
+// neighbouring operands (same binade and a small difference almost always)
 __device__ __forceinline__ float dif32_near(double b, double a) {
   float v;
+  if (diff_small_f32(b, a, &v)) return v;
   if (diff_same_f32(b, a, &v)) return v;
   if (diff_f32(b, a, &v)) return v;
   return sub_f64_f32(b, a);
@@ -89,6 +90,11 @@ __device__ __forceinline__ double to_f64(float f) {
   if ((bits32(f) & 0x7FFFFFFFu) == 0) return from_bits64((uint64_t)(bits32(f) >> 31) << 63);
   return cvt_f32_f64(f);
 }
+
+// Difference of two values (often in different binades): one FP64 subtraction, exact or
+// rounded to 53 bits, then the integer-pipe narrowing.  The FP64 pipe is otherwise nearly
+// idle in this kernel, so this is cheaper than the integer route for unrelated operands.
+__device__ __forceinline__ float dy32(double b, double a) { return to_f32(b - a); }
 
 __device__ __forceinline__ F2 f2_of(double v) {
   const float hi = to_f32(v);
@@ -180,7 +186,7 @@ __device__ void tile_mixed(const Inst &I, long long tile, const RingM &ring) {
   FwdM F;
   {
     const double x0 = x[r], x1 = x[r + 1], y0 = y[r], y1 = y[r + 1];
-    const float h = dif32_near(x1, x0), ih = rcp32(h), sl = quot32(dif32(y1, y0), h, ih);
+    const float h = dif32_near(x1, x0), ih = rcp32(h), sl = quot32(dy32(y1, y0), h, ih);
     F.xn = x1; F.yn = y1; F.h = h; F.s = sl; F.yf = to_f32(y1);
     if (r == 0 && !nat0) {
       F.cp = 0.5f;
@@ -204,7 +210,7 @@ __device__ void tile_mixed(const Inst &I, long long tile, const RingM &ring) {
         const double x2 = x[j + 1], y2 = y[j + 1];
         hj = dif32_near(x2, F.xn);
         const float ihj = rcp32(hj);
-        const float sj = quot32(dif32(y2, F.yn), hj, ihj);
+        const float sj = quot32(dy32(y2, F.yn), hj, ihj);
         const float den = 2.0f * (F.h + hj) - F.h * F.cp;
         const float iden = rcp32(den);
         cpj = hj * iden;

@@ -155,6 +155,22 @@ SPL_HD bool diff_same_f32(double b, double a, float *out) {
   return true;
 }
 
+// Cheapest case of diff_same_f32: same sign and exponent field, 0 <= difference < 2^31 ulps,
+// and a scale 2^(e-1075) inside binary32's normal range.  The count of ulps converts to
+// binary32 with one correctly rounded int32 conversion; the power-of-two scale is exact.
+SPL_HD bool diff_small_f32(double b, double a, float *out) {
+  const uint64_t ub = bits64(b), ua = bits64(a);
+  const uint32_t hb = (uint32_t)(ub >> 52);
+  if (hb != (uint32_t)(ua >> 52)) return false;
+  const uint32_t e = hb & 0x7FFu;
+  if (e < 949u || e > 1171u) return false;  // 2^(e-1075) and 2^(e-1044) within binary32's normal range
+  const int64_t D = (hb & 0x800u) ? (int64_t)(ua - ub) : (int64_t)(ub - ua);
+  if (D < 0 || D >= (int64_t)0x80000000LL) return false;
+  const float scale = from_bits32((e - 1075u + 127u) << 23);
+  *out = (float)(int32_t)D * scale;
+  return true;
+}
+
 // ---- double-float ("float-float") arithmetic: value = hi + lo, |lo| <= ulp(hi)/2 ----
 // Error-free transformations: Knuth's TwoSum, Dekker's Fast2Sum, and the FMA form of
 // TwoProduct; relative accuracy of the compound operations about 2^-46.

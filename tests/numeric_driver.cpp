@@ -36,3 +36,7 @@ void t_df_mul_f(float ah, float al, float b, float *ph, float *pl) {
 extern "C" {
 int t_diff_same_f32(double b, double a, float *out) { return spl::diff_same_f32(b, a, out) ? 1 : 0; }
 }
+
+extern "C" {
+int t_diff_small_f32(double b, double a, float *out) { return spl::diff_small_f32(b, a, out) ? 1 : 0; }
+}

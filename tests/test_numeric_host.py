@@ -120,6 +120,31 @@ def test_same_binade_difference(lib):
     assert hits > 3000
 
 
+def test_small_same_binade_difference(lib):
+    lib.t_diff_small_f32.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_float)]
+    lib.t_diff_small_f32.restype = ctypes.c_int
+    rng = np.random.default_rng(8)
+    hits = 0
+    for _ in range(6000):
+        a = rng.normal() * 10.0 ** rng.integers(-12, 12)
+        b = a + abs(a) * rng.random() * 10.0 ** rng.integers(-16, -5)
+        if rng.random() < 0.2:
+            b = a
+        out = ctypes.c_float()
+        ok = lib.t_diff_small_f32(float(b), float(a), ctypes.byref(out))
+        if not ok:
+            continue
+        hits += 1
+        exact = Fraction(float(b)) - Fraction(float(a))
+        assert out.value == rn32(exact), (a, b)
+    assert hits > 3000
+    # refused: different binades, negative differences, large exponents
+    o = ctypes.c_float()
+    assert not lib.t_diff_small_f32(2.0, 1.9, ctypes.byref(o))
+    assert not lib.t_diff_small_f32(1.0, 1.5, ctypes.byref(o))
+    assert not lib.t_diff_small_f32(1e300, 1e300 * (1 - 1e-15), ctypes.byref(o))
+
+
 def test_diff_far_apart_and_signs(lib):
     rng = np.random.default_rng(1)
     for _ in range(2000):
