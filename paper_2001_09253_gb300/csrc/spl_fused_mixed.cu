@@ -31,12 +31,13 @@
 
 namespace spl {
 
-constexpr int kThreadsM = 256;            // one CTA per SM, two warps per sub-partition
+constexpr int kThreadsM = 512;            // one CTA per SM, four warps per sub-partition
 constexpr int kSegM = 24;
 constexpr int kHaloBM = 24;
 constexpr int kRingM = kSegM + kHaloBM;
 constexpr int kHaloFM = 48;
-constexpr int kFieldsM = 4;               // c', d' (then y''), h, y (binary32)
+constexpr int kFieldsM = 2;               // c', d' (then y'')
+constexpr int kPrefetchM = 32;            // rows between an L2 prefetch of x, y and their load
 constexpr size_t kSmemM = (size_t)kRingM * kFieldsM * kThreadsM * sizeof(float);
 
 struct RingM {
@@ -117,16 +118,19 @@ __device__ __forceinline__ float newint32(float xa, float bx, float yj, float yj
   return (lower + (1.0f / 6.0f) * (C + D)) * inv_ba;
 }
 
-__device__ __forceinline__ void prefetch_l1m(const void *p) {
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+__device__ __forceinline__ void prefetch_l2m(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 // Queries of intervals [a, b) (local rows ta..tb of the tile), with y'' of the segment in
-// ring field 1 and y''_b in Yb; returns the next query index.
+// ring field 1 and y''_b in Yb; returns the next query index.  Knots and values come from
+// global memory (L2: the forward sweep touched them a segment earlier); the right end of the
+// next interval is loaded one interval ahead.
 __device__ __forceinline__ long long eval_segment(const Inst &I, const Grid &G, const RingM &ring, long long s0,
                                                   int ta, int tb, float Yb, long long k) {
   const long long n = I.n, m = I.m;
   const double *__restrict__ x = I.x;
+  const double *__restrict__ y = I.y;
   const long long a = s0 + ta, b = s0 + tb;
   if (m == 0 || a > n - 2) return k;
   const long long jmax = min(b, n - 1) - 1;
@@ -134,41 +138,59 @@ __device__ __forceinline__ long long eval_segment(const Inst &I, const Grid &G, 
   const long long kb = bounded ? dkey(x[b]) : 0;
   long long j = a;
   int slot = ta % kRingM;
-  double xj = x[j], xj1 = x[j + 1];
+  double xj = x[j], xj1 = x[j + 1], yj = y[j], yj1 = y[j + 1];
+  double xj2 = 0.0, yj2 = 0.0;  // x_{j+2}, y_{j+2}
+  if (j + 2 < n) { xj2 = x[j + 2]; yj2 = y[j + 2]; }
   long long kxj1 = dkey(xj1);
-  float ba = ring.at(slot, 2), iba = rcp32(ba);
+  float ba = dif32_near(xj1, xj), iba = rcp32(ba);
+  float fy0 = to_f32(yj), fy1 = to_f32(yj1);
   while (k < m) {
     const double q = G.at(k);
     const long long kq = dkey(q);
     if (bounded && kq > kb) break;
     if (j < jmax && kxj1 < kq) {
+      const long long j_old = j;
       do {
         ++j;
-        xj = xj1;
-        xj1 = x[j + 1];
+        xj = xj1; yj = yj1;
+        xj1 = xj2; yj1 = yj2;
+        if (j + 2 < n) { xj2 = x[j + 2]; yj2 = y[j + 2]; }
         kxj1 = dkey(xj1);
       } while (j < jmax && kxj1 < kq);
       slot = (int)(j - s0) % kRingM;
-      ba = ring.at(slot, 2);
+      ba = dif32_near(xj1, xj);
       iba = rcp32(ba);
+      fy0 = (j == j_old + 1) ? fy1 : to_f32(yj);
+      fy1 = to_f32(yj1);
     }
     const int slot1 = (slot + 1 == kRingM) ? 0 : slot + 1;
     const float xa = dif32_near(q, xj);
     const float bx = ba - xa;
     const float ppj = ring.at(slot, 1);
     const float ppj1 = (j + 1 == b) ? Yb : ring.at(slot1, 1);
-    I.yq[k] = to_f64(newint32(xa, bx, ring.at(slot, 3), ring.at(slot1, 3), ppj, ppj1, ba, iba));
+    I.yq[k] = to_f64(newint32(xa, bx, fy0, fy1, ppj, ppj1, ba, iba));
     if (I.jq) I.jq[k] = (int32_t)j;
     ++k;
   }
   return k;
 }
 
+// Forward state at row r: (c'_r, d'_r), h_r, s_r, the knot and value of row r+1 and the
+// loads of rows r+2 and r+3 already in flight.
 struct FwdM {
-  double xn, yn;  // knot and value at r+1 (binary64)
+  double xn, yn;  // x_{r+1}, y_{r+1}
+  double xa, ya;  // x_{r+2}, y_{r+2}
+  double xb, yb;  // x_{r+3}, y_{r+3}
   float h, s, cp, dp;
-  float yf;       // y_{r+1} in binary32
 };
+
+// Input checks of row j (section "Generating Second Derivatives" takes strictly increasing
+// knots; finite values are required on top), made while the forward sweep passes it.
+__device__ __forceinline__ unsigned row_check(double xj, double yj, bool has_next, double xj1) {
+  unsigned bad = (!finite64(xj) || !finite64(yj)) ? kStNonFinite : 0u;
+  if (has_next && !(dkey(xj1) > dkey(xj))) bad |= kStNotIncreasing;
+  return bad;
+}
 
 // kFitOnly: first pass of the refined path; y'' (binary32) goes to the scratch I.z and no
 // query is evaluated.
@@ -179,15 +201,18 @@ __device__ void tile_mixed(const Inst &I, long long tile, const RingM &ring) {
   const double *__restrict__ y = I.y;
   const long long s0 = tile * (long long)I.tile_rows;
   const long long e0 = min(s0 + (long long)I.tile_rows, n);
-  validate_rows(I, s0, e0);
 
   const bool nat0 = is_natural(I.yp1), nat1 = is_natural(I.ypn);
+  unsigned bad = 0;
   long long r = max(s0 - kHaloFM, 0LL);
   FwdM F;
   {
     const double x0 = x[r], x1 = x[r + 1], y0 = y[r], y1 = y[r + 1];
+    F.xa = F.ya = F.xb = F.yb = 0.0;
+    if (r + 2 < n) { F.xa = x[r + 2]; F.ya = y[r + 2]; }
+    if (r + 3 < n) { F.xb = x[r + 3]; F.yb = y[r + 3]; }
     const float h = dif32_near(x1, x0), ih = rcp32(h), sl = quot32(dy32(y1, y0), h, ih);
-    F.xn = x1; F.yn = y1; F.h = h; F.s = sl; F.yf = to_f32(y1);
+    F.xn = x1; F.yn = y1; F.h = h; F.s = sl;
     if (r == 0 && !nat0) {
       F.cp = 0.5f;
       F.dp = 3.0f * (sl - to_f32(I.yp1)) * ih;
@@ -196,27 +221,32 @@ __device__ void tile_mixed(const Inst &I, long long tile, const RingM &ring) {
       F.dp = 0.0f;
     }
     if (r >= s0) {
-      ring.at(0, 0) = F.cp; ring.at(0, 1) = F.dp; ring.at(0, 2) = h; ring.at(0, 3) = to_f32(y0);
+      ring.at(0, 0) = F.cp; ring.at(0, 1) = F.dp;
+      bad |= row_check(x0, y0, true, x1);
     }
   }
   int slot_r = (int)(r - s0);  // only meaningful once r >= s0
   auto forward_to = [&](long long target) {
     while (r < target) {
       const long long j = r + 1;
-      float cpj, dpj, hj = 0.0f;
-      const float yj = F.yf;
+      float cpj, dpj;
+      const bool owned = (j >= s0 && j < e0);
       if (j <= n - 2) {
-        if (j + 17 < n) { prefetch_l1m(x + j + 17); prefetch_l1m(y + j + 17); }
-        const double x2 = x[j + 1], y2 = y[j + 1];
-        hj = dif32_near(x2, F.xn);
+        const double x2 = F.xa, y2 = F.ya;
+        F.xa = F.xb; F.ya = F.yb;
+        if (j + 3 < n) { F.xb = x[j + 3]; F.yb = y[j + 3]; }
+        if (j + 3 + kPrefetchM < n) { prefetch_l2m(x + j + 3 + kPrefetchM); prefetch_l2m(y + j + 3 + kPrefetchM); }
+        if (owned) bad |= row_check(F.xn, F.yn, true, x2);
+        const float hj = dif32_near(x2, F.xn);
         const float ihj = rcp32(hj);
         const float sj = quot32(dy32(y2, F.yn), hj, ihj);
         const float den = 2.0f * (F.h + hj) - F.h * F.cp;
         const float iden = rcp32(den);
         cpj = hj * iden;
         dpj = (6.0f * (sj - F.s) - F.h * F.dp) * iden;
-        F.xn = x2; F.yn = y2; F.h = hj; F.s = sj; F.yf = to_f32(y2);
+        F.xn = x2; F.yn = y2; F.h = hj; F.s = sj;
       } else {
+        if (owned) bad |= row_check(F.xn, F.yn, false, 0.0);
         cpj = 0.0f;
         if (nat1) {
           dpj = 0.0f;
@@ -229,7 +259,7 @@ __device__ void tile_mixed(const Inst &I, long long tile, const RingM &ring) {
       r = j;
       if (j >= s0) {
         slot_r = (j == s0) ? 0 : ((slot_r + 1 == kRingM) ? 0 : slot_r + 1);
-        ring.at(slot_r, 0) = cpj; ring.at(slot_r, 1) = dpj; ring.at(slot_r, 2) = hj; ring.at(slot_r, 3) = yj;
+        ring.at(slot_r, 0) = cpj; ring.at(slot_r, 1) = dpj;
       }
     }
   };
@@ -261,15 +291,17 @@ __device__ void tile_mixed(const Inst &I, long long tile, const RingM &ring) {
     }
     k = eval_segment(I, G, ring, s0, ta, tb, Yb, k);
   }
+  if (bad) atomicOr(I.status, bad);
 }
 
 // ---- refinement pass ----
 struct FwdR {
   double xn, yn;  // x_{r+1}, y_{r+1}
+  double xa, ya;  // x_{r+2}, y_{r+2} (loaded one step early)
   F2 h, s;        // h_r, s_r
   float zr, zn;   // Z_r, Z_{r+1}
+  float za;       // Z_{r+2}
   float cp, dp;   // Thomas state of the correction system at row r
-  float yf;       // y_{r+1} in binary32
 };
 
 __device__ void tile_refine(const Inst &I, long long tile, const RingM &ring) {
@@ -282,17 +314,16 @@ __device__ void tile_refine(const Inst &I, long long tile, const RingM &ring) {
   const bool nat0 = is_natural(I.yp1), nat1 = is_natural(I.ypn);
   long long r = max(s0 - kHaloFM, 0LL);
   FwdR F;
-  float z_first;  // Z_r at the start
-  // Ring field 3 carries Z through the forward and backward sweeps; after a segment's back
-  // substitution its rows are switched to y (binary32) for the evaluation.
   {
     const double x0 = x[r], x1 = x[r + 1], y0 = y[r], y1 = y[r + 1];
     const float z0 = z[r], z1 = z[r + 1];
+    F.xa = F.ya = 0.0;
+    F.za = 0.0f;
+    if (r + 2 < n) { F.xa = x[r + 2]; F.ya = y[r + 2]; F.za = z[r + 2]; }
     const F2 h = dif2(x1, x0);
     const float ih = rcp32(h.hi);
     const F2 sl = df_div(dif2(y1, y0), h, ih);
-    F.xn = x1; F.yn = y1; F.h = h; F.s = sl; F.zr = z0; F.zn = z1; F.yf = to_f32(y1);
-    z_first = z0;
+    F.xn = x1; F.yn = y1; F.h = h; F.s = sl; F.zr = z0; F.zn = z1;
     if (r == 0 && !nat0) {
       // clamped first row: 6(s_0 - y'_0) - (2 h_0 Z_0 + h_0 Z_1), divided by b = 2 h_0
       const F2 d = df_mul_f(df_add(sl, df_neg(f2_of(I.yp1))), 6.0f);
@@ -307,21 +338,21 @@ __device__ void tile_refine(const Inst &I, long long tile, const RingM &ring) {
       F.cp = 0.0f;
       F.dp = 0.0f;
     }
-    if (r >= s0) {
-      // field 3 holds Z until the back substitution, then y (binary32) for the evaluation
-      ring.at(0, 0) = F.cp; ring.at(0, 1) = F.dp; ring.at(0, 2) = h.hi; ring.at(0, 3) = z_first;
-    }
+    if (r >= s0) { ring.at(0, 0) = F.cp; ring.at(0, 1) = F.dp; }
   }
   int slot_r = (int)(r - s0);
   auto forward_to = [&](long long target) {
     while (r < target) {
       const long long j = r + 1;
-      float cpj, dpj, hst = 0.0f;
-      const float zj = F.zn;
+      float cpj, dpj;
       if (j <= n - 2) {
-        if (j + 17 < n) { prefetch_l1m(x + j + 17); prefetch_l1m(y + j + 17); prefetch_l1m(z + j + 33); }
-        const double x2 = x[j + 1], y2 = y[j + 1];
-        const float z2 = z[j + 1];
+        const double x2 = F.xa, y2 = F.ya;
+        const float z2 = F.za;
+        if (j + 2 < n) { F.xa = x[j + 2]; F.ya = y[j + 2]; F.za = z[j + 2]; }
+        if (j + 2 + kPrefetchM < n) {
+          prefetch_l2m(x + j + 2 + kPrefetchM); prefetch_l2m(y + j + 2 + kPrefetchM);
+          prefetch_l2m(z + j + 2 + kPrefetchM);
+        }
         const F2 hj = dif2(x2, F.xn);
         const float ihj = rcp32(hj.hi);
         const F2 sj = df_div(dif2(y2, F.yn), hj, ihj);
@@ -334,7 +365,6 @@ __device__ void tile_refine(const Inst &I, long long tile, const RingM &ring) {
         const float iden = rcp32(den);
         cpj = hj.hi * iden;
         dpj = (rf - hf * F.dp) * iden;
-        hst = hj.hi;
         F.xn = x2; F.yn = y2; F.h = hj; F.s = sj; F.zr = F.zn; F.zn = z2;
       } else {  // last row
         cpj = 0.0f;
@@ -353,7 +383,7 @@ __device__ void tile_refine(const Inst &I, long long tile, const RingM &ring) {
       r = j;
       if (j >= s0) {
         slot_r = (j == s0) ? 0 : ((slot_r + 1 == kRingM) ? 0 : slot_r + 1);
-        ring.at(slot_r, 0) = cpj; ring.at(slot_r, 1) = dpj; ring.at(slot_r, 2) = hst; ring.at(slot_r, 3) = zj;
+        ring.at(slot_r, 0) = cpj; ring.at(slot_r, 1) = dpj;
       }
     }
   };
@@ -376,22 +406,15 @@ __device__ void tile_refine(const Inst &I, long long tile, const RingM &ring) {
       if (t == tb) Db = D;
       if (t < tb) ring.at(slot, 1) = D;
     }
-    // y'' = Z + delta; the ring then holds y'' (field 1) and y in binary32 (field 3)
-    const float z_tb = (tb <= tl) ? ring.at(tb % kRingM, 3) : 0.0f;
-    const float Yb = (tb <= tl) ? z_tb + Db : 0.0f;
-    const int tend = min(tb + 1, tl + 1);
-    for (int t = ta; t < tend; ++t) {
+    // y'' = Z + delta; field 1 then holds y'' for the evaluation
+    const float Yb = (tb <= tl) ? z[s0 + tb] + Db : 0.0f;
+    for (int t = ta; t < tb; ++t) {
       const int sl = t % kRingM;
-      if (t < tb) {
-        const float zj = ring.at(sl, 3), dj = ring.at(sl, 1);
-        if (I.ypp) I.ypp[s0 + t] = to_f64(zj) + to_f64(dj);
-        ring.at(sl, 1) = zj + dj;
-      }
-      ring.at(sl, 3) = to_f32(y[s0 + t]);
+      const float zj = z[s0 + t], dj = ring.at(sl, 1);
+      if (I.ypp) I.ypp[s0 + t] = to_f64(zj) + to_f64(dj);
+      ring.at(sl, 1) = zj + dj;
     }
     k = eval_segment(I, G, ring, s0, ta, tb, Yb, k);
-    // rows [tb, tl] keep Z in field 3 for the next segment: restore the one overwritten above
-    if (tb <= tl) ring.at(tb % kRingM, 3) = z_tb;
   }
 }
 
@@ -557,6 +580,8 @@ cudaError_t launch_serve(const ServeArgs &args, int sm_count, cudaStream_t strea
 }
 
 int serve_tile_threads() { return kThreadsM; }
+
+int mixed_threads_per_sm() { return kThreadsM; }
 
 long long threads_mixed(int sm_count, long long total_tiles) {
   long long blocks = std::min<long long>((total_tiles + kThreadsM - 1) / kThreadsM, (long long)sm_count);

@@ -29,6 +29,7 @@ cudaError_t launch_refine_mixed(const Inst *d_insts, int ninst, long long total_
 // Persistent serving loop (spl_fused_mixed.cu): a cooperative launch of one CTA per SM.
 cudaError_t launch_serve(const ServeArgs &args, int sm_count, cudaStream_t stream);
 int serve_tile_threads();
+int mixed_threads_per_sm();  // threads of one mixed-kernel CTA (one CTA per SM)
 
 }  // namespace spl
 

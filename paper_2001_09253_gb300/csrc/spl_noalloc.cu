@@ -73,7 +73,7 @@ extern "C" spl_status spl_fit_eval_noalloc(const double *x, const double *y, uin
   I.x = x; I.y = y; I.ypp = ypp_out; I.yq = yq_out; I.jq = nullptr;
   I.n = (long long)n; I.m = (long long)m;
   I.yp1 = yp1; I.ypn = ypn;
-  long long target = (long long)sms * 256;  // one tile per thread of the mixed kernels' wave
+  long long target = (long long)sms * spl::mixed_threads_per_sm();  // one tile per thread of one wave
   long long L = ((long long)n + target - 1) / target;
   L = L < 128 ? 128 : L;
   I.tile_rows = (int)L;

@@ -171,9 +171,9 @@ spl_status check_request(const spl_plan *plan, const spl_request *r) {
   return SPL_OK;
 }
 
-// Launch geometry: both kernels run persistent CTAs with 256 threads per SM (two warps per
-// SM sub-partition, which the dependency chains of either kernel need to keep the pipes
-// busy); one thread per tile, tiles fetched dynamically.
+// Launch geometry: persistent CTAs, one thread per tile, tiles fetched dynamically.  The FP64
+// kernel runs 256 threads per SM (two warps per SM sub-partition keep the FP64 pipe busy);
+// the mixed kernels 512 (four warps per sub-partition hide the L2 latency of their loads).
 long long threads_for(const spl_ctx *c, int precision, long long total_tiles) {
   return precision == SPL_PREC_F64 ? spl::threads_f64(c->sm_count, total_tiles)
                                    : spl::threads_mixed(c->sm_count, total_tiles);
@@ -182,7 +182,7 @@ long long threads_for(const spl_ctx *c, int precision, long long total_tiles) {
 // Tile length so that one instance of total_points fills every thread of one wave; never
 // shorter than a few halos.
 int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points) {
-  const long long per_sm = 256;  // both kernels run 256 threads per SM
+  const long long per_sm = precision == SPL_PREC_F64 ? 256 : spl::mixed_threads_per_sm();
   long long target = (long long)c->sm_count * per_sm;
   long long L = (long long)((total_points + target - 1) / target);
   L = std::max<long long>(L, precision == SPL_PREC_F64 ? 256 : 128);
