@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--only", default="", choices=["", "f64", "mixed", "mixed-refine", "batched"],
                     help="time one path only and print a short line (profiling runs)")
     ap.add_argument("--n", type=int, default=N_POINTS, help="knots = queries per instance (profiling runs)")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving leg (launch-list captures: its persistent loop waits on the host, "
+                         "which a profiler that serialises launches would stall)")
     return ap.parse_args()
 
 
@@ -486,7 +489,7 @@ def run_ours(args, world, rank, local):
     mixed0 = r.time_single(r.plan(spl.PREC_F32_REFINE, 0))
     mixed1 = r.time_single(r.plan(spl.PREC_F32_REFINE, 1))
     batched, bdata = r.batched()
-    served, sdata = serving(r)
+    served, sdata = (None, None) if args.no_serving else serving(r)
     if rank != 0:
         r.ctx.close()
         return
@@ -520,7 +523,8 @@ def run_ours(args, world, rank, local):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu, errs = cpu_baseline_and_errors(r, main, mixed0, mixed1, bdata, sdata)
-        others["serving"]["error_vs_oracle"] = errs["serving"]
+        if served is not None:
+            others["serving"]["error_vs_oracle"] = errs["serving"]
         others["mixed_f32"]["error_vs_oracle"] = errs["mixed0"]
         others["mixed_f32_refine1"]["error_vs_oracle"] = errs["mixed1"]
         others["batched"]["error_vs_oracle"] = errs["batched"]
@@ -594,6 +598,8 @@ def cpu_baseline_and_errors(r, main, mixed0, mixed1, bdata, sdata):
         e = error_pair(xi, yi, rf, Pc[o:o + nn], Qc[o:o + nn])
         worst = [max(worst[0], e["ypp"]), max(worst[1], e["yq"])]
     out["batched"] = {"ypp": worst[0], "yq": worst[1], "sample": "64 of 4096 instances"}
+    if sdata is None:
+        return cpu, out
     sizes_s, seed_s, base_s, sample = sdata
     worst = [0.0, 0.0]
     for i, (ypp_i, yq_i) in sample.items():

@@ -23,7 +23,7 @@ struct Inst {
   long long tile_begin; // global index of this instance's first tile
   long long ntiles;     // tiles of this instance
   int tile_rows;        // knots per tile (the last tile of an instance is ragged)
-  int pad;
+  int pad;              // bit 0: grouped tile geometry (FP64 kernel)
   unsigned *status;     // device word, OR of kSt* bits
   float *z;             // mixed path with refinement: binary32 y'' of the first pass (n), scratch
 };
@@ -156,16 +156,12 @@ __device__ __forceinline__ int find_inst(const Inst *insts, int ninst, long long
   return lo;
 }
 
-// Validation of the rows a tile owns (section "Generating Second Derivatives" assumes
-// strictly increasing knots; finite inputs are required on top).
-__device__ __forceinline__ void validate_rows(const Inst &I, long long s, long long e) {
-  unsigned bad = 0;
-  for (long long j = s; j < e; ++j) {
-    double xj = I.x[j], yj = I.y[j];
-    if (!finite64(xj) || !finite64(yj)) bad |= kStNonFinite;
-    if (j + 1 < I.n && !(dkey(I.x[j + 1]) > dkey(xj))) bad |= kStNotIncreasing;
-  }
-  if (bad) atomicOr(I.status, bad);
+// Input checks of row j (section "Generating Second Derivatives" takes strictly increasing
+// knots; finite values are required on top), made while a forward sweep passes the row.
+__device__ __forceinline__ unsigned row_check(double xj, double yj, bool has_next, double xj1) {
+  unsigned bad = (!finite64(xj) || !finite64(yj)) ? kStNonFinite : 0u;
+  if (has_next && !(dkey(xj1) > dkey(xj))) bad |= kStNotIncreasing;
+  return bad;
 }
 
 }  // namespace spl

@@ -135,22 +135,48 @@ struct Fwd64 {
   double xl, yl;
 };
 
-__device__ void tile_f64(const Inst &I, long long tile, const Scratch64 &S) {
-  const long long n = I.n, m = I.m;
+// Rows of a tile.  Plain geometry: tile k covers [kL, (k+1)L).  Grouped geometry (instances
+// whose tiles are aligned to warps, flag bit 0): the 32 tiles of a warp cover 32L - kHaloB
+// consecutive rows, the last of them being kHaloB rows shorter, because every lane but the
+// last takes the rows past its tile (the back substitution's start) from the next lane's
+// forward sweep instead of recomputing them.
+struct TileRows {
+  long long s0, e0;
+  bool succ;  // the next lane holds rows [e0, e0 + kHaloB) of its own forward sweep
+};
+
+__device__ __forceinline__ TileRows tile_rows_of(const Inst &I, long long tile) {
+  const long long n = I.n, L = I.tile_rows;
+  TileRows T;
+  if (I.pad & 1) {
+    const long long lane = tile & 31;
+    T.s0 = (tile >> 5) * (32 * L - kHaloB) + lane * L;
+    T.e0 = min(T.s0 + (lane == 31 ? L - kHaloB : L), n);
+    T.succ = lane < 31 && T.e0 < n;
+  } else {
+    T.s0 = tile * L;
+    T.e0 = min(T.s0 + L, n);
+    T.succ = false;
+  }
+  return T;
+}
+
+// Forward elimination of a tile (rows from the halo start to rlast) into the scratch; returns
+// rlast and ORs the input checks of the tile's rows into *bad.
+__device__ long long tile_forward(const Inst &I, const TileRows &T, const Scratch64 &S, unsigned *bad_out) {
+  const long long n = I.n;
   const double *__restrict__ x = I.x;
   const double *__restrict__ y = I.y;
-  const long long s0 = tile * (long long)I.tile_rows;
-  const long long e0 = min(s0 + (long long)I.tile_rows, n);
-  validate_rows(I, s0, e0);
-
+  const long long s0 = T.s0, e0 = T.e0;
   const bool nat0 = is_natural(I.yp1), nat1 = is_natural(I.ypn);
+  unsigned bad = 0;  // input checks of the tile's rows, made as the forward sweep passes them
   // ---- 1. forward elimination ----
   long long r = halo_start(x, n, s0);  // row whose (c', d') the state holds
   Fwd64 F;
   F.hn = F.ihn = F.sn = 0.0;
   F.xl = F.yl = 0.0;
   // interval j (= r+1 of the state) when it exists: uses x_{j+1}, y_{j+1} (loaded one step
-  // earlier) and issues the loads of x_{j+2}, y_{j+2} for the next step
+  // earlier) and issues the loads of x_{j+2}, y_{j+2} for the next step; row j is checked
   auto precompute_next = [&](long long j) {
     if (j <= n - 2) {
       const double x2 = F.xl, y2 = F.yl;
@@ -159,11 +185,14 @@ __device__ void tile_f64(const Inst &I, long long tile, const Scratch64 &S) {
         F.xl = x[j + 2];
         F.yl = y[j + 2];
       }
+      if (j >= s0 && j < e0) bad |= row_check(F.xn, F.yn, true, x2);
       F.hn = x2 - F.xn;
       F.ihn = rcp64(F.hn);
       F.sn = quot64(y2 - F.yn, F.hn, F.ihn);
       F.xn = x2;
       F.yn = y2;
+    } else if (j == n - 1 && j >= s0 && j < e0) {
+      bad |= row_check(F.xn, F.yn, false, 0.0);
     }
   };
   {
@@ -179,6 +208,7 @@ __device__ void tile_f64(const Inst &I, long long tile, const Scratch64 &S) {
     }
     if (r >= s0) {                    // r == s0 == 0: row 0 is this tile's first row
       S.at(0, 0) = F.cp; S.at(0, 1) = F.dp; S.at(0, 2) = ih;
+      bad |= row_check(x0, y0, true, x1);
     }
     if (r + 2 < n) {
       F.xl = x[r + 2];
@@ -186,7 +216,7 @@ __device__ void tile_f64(const Inst &I, long long tile, const Scratch64 &S) {
     }
     precompute_next(r + 1);
   }
-  const long long rlast = min(e0 + kHaloB, n) - 1;
+  const long long rlast = T.succ ? e0 - 1 : min(e0 + kHaloB, n) - 1;
   while (r < rlast) {
     const long long j = r + 1;
     double cpj, dpj, ihj = 0.0;
@@ -215,17 +245,35 @@ __device__ void tile_f64(const Inst &I, long long tile, const Scratch64 &S) {
     }
   }
 
-  // ---- 2. back substitution over the tile (y''_{rlast} := d'_{rlast}, exact when rlast == n-1) ----
-  {
+  *bad_out = bad;
+  return rlast;
+}
+
+// Back substitution from rlast (y''_{rlast} := d'_{rlast}, exact when rlast == n-1), fused
+// with the evaluation: row t's y'' completes interval t, whose queries are evaluated right
+// away, walking the grid downwards.  With T.succ the rows past the tile come from the next
+// lane's scratch (rows it computed after its own halo).
+__device__ void tile_backward_eval(const Inst &I, const TileRows &T, long long rlast, const Scratch64 &S) {
+  const long long n = I.n, m = I.m;
+  const double *__restrict__ x = I.x;
+  const double *__restrict__ y = I.y;
+  const long long s0 = T.s0, e0 = T.e0;
+  const long long te = e0 - 1 - s0;  // last row of the tile (local)
+  double Y;
+  long long t;
+  if (T.succ) {
+    const Scratch64 Sn{S.base, S.lane + 1};  // the next lane's tile starts at row e0
+    long long u = min(e0 + kHaloB, n) - 1 - e0;
+    Y = Sn.at(u, 1);
+    for (--u; u >= 0; --u) Y = Sn.at(u, 1) - Sn.at(u, 0) * Y;
+    t = te;
+  } else {
     const long long tl = rlast - s0;
-    double Y = S.at(tl, 1);
-    long long t = tl - 1;
+    Y = S.at(tl, 1);
+    t = tl - 1;
+  {  // rows past the tile: the recurrence alone, loads of eight rows first
     constexpr int kB = 8;
-    for (; t >= kB - 1; t -= kB) {  // loads of eight rows first: they do not depend on Y
-      if (t >= 40) {
-        prefetch_l2(&S.at(t - 32, 0));
-        prefetch_l2(&S.at(t - 36, 0));
-      }
+    for (; t - (kB - 1) > te; t -= kB) {
       double cc[kB], dd[kB];
 #pragma unroll
       for (int u = 0; u < kB; ++u) {
@@ -233,55 +281,54 @@ __device__ void tile_f64(const Inst &I, long long tile, const Scratch64 &S) {
         dd[u] = S.at(t - u, 1);
       }
 #pragma unroll
-      for (int u = 0; u < kB; ++u) {
-        Y = dd[u] - cc[u] * Y;
-        S.at(t - u, 1) = Y;
-      }
+      for (int u = 0; u < kB; ++u) Y = dd[u] - cc[u] * Y;
     }
-    for (; t >= 0; --t) {
-      Y = S.at(t, 1) - S.at(t, 0) * Y;
-      S.at(t, 1) = Y;
-    }
-    if (I.ypp) {
-      for (long long j = s0; j < e0; ++j) I.ypp[j] = S.at(j - s0, 1);
-    }
+    for (; t > te; --t) Y = S.at(t, 1) - S.at(t, 0) * Y;
   }
+  }
+  // here Y = y''_{t+1}: y''_{e0} (t = te), or y''_{n-1} when the tile ends at row n-1 (t = te - 1)
+  if (t == te - 1 && I.ypp) I.ypp[n - 1] = Y;
 
-  // ---- 3. evaluation of the queries whose interval j lies in [s0, e0): x_k > x_{s0}
-  //         (first_query) and x_k <= x_{e0} when e0 <= n-2 ----
-  if (m > 0 && s0 <= n - 2) {
-    const Grid G = make_grid(x, n, m);
-    long long k = first_query(G, x, s0);
-    const long long jmax = min(e0, n - 1) - 1;
-    const bool bounded = (e0 <= n - 2);
-    const long long kb = bounded ? dkey(x[e0]) : 0;
-    long long j = s0;
-    double xj = x[j], xj1 = x[j + 1], yj = y[j], yj1 = y[j + 1];
-    double hj = xj1 - xj;
-    double ppj = S.at(0, 1), ppj1 = S.at(1, 1), ihj = S.at(0, 2);
-    long long kxj1 = dkey(xj1);
-    while (k < m) {
-      const double q = G.at(k);
-      const long long kq = dkey(q);
-      if (bounded && kq > kb) break;
-      if (j < jmax && kxj1 < kq) {
-        do {
-          ++j;
-          xj = xj1; yj = yj1;
-          xj1 = x[j + 1]; yj1 = y[j + 1];
-          kxj1 = dkey(xj1);
-        } while (j < jmax && kxj1 < kq);
-        hj = xj1 - xj;
-        if (j + 9 < n) { prefetch_l1(x + j + 9); prefetch_l1(y + j + 9); }
-        if (j + 8 < rlast) prefetch_l1(&S.at(j + 8 - s0, 0));
-        ppj = S.at(j - s0, 1);
-        ppj1 = S.at(j + 1 - s0, 1);
-        ihj = S.at(j - s0, 2);
+  // queries of the tile: k in [klo, khi], x_k > x_{s0} (first_query) and x_k <= x_{e0} when
+  // e0 <= n-2; interval t takes those with x_t < x_k (the lowest interval all the rest)
+  const bool evaluate = (m > 0 && s0 <= n - 2);
+  const Grid G = make_grid(x, n, m);
+  const long long klo = evaluate ? first_query(G, x, s0) : 0;
+  long long k = evaluate ? ((e0 <= n - 2) ? first_query(G, x, e0) - 1 : m - 1) : -1;
+  double q = 0.0;
+  long long kq = 0;
+  if (k >= klo) { q = G.at(k); kq = dkey(q); }
+  double xt1 = x[s0 + t + 1], yt1 = y[s0 + t + 1];  // knot and value of row t+1
+  // row t's loads one row ahead
+  double c_t = 0.0, d_t = 0.0, ih_t = 0.0, x_t = 0.0, y_t = 0.0;
+  if (t >= 0) {
+    c_t = S.at(t, 0); d_t = S.at(t, 1); ih_t = S.at(t, 2);
+    x_t = x[s0 + t]; y_t = y[s0 + t];
+  }
+  for (; t >= 0; --t) {
+    const double c = c_t, d = d_t, ih = ih_t, xt = x_t, yt = y_t;
+    if (t > 0) {
+      if (t >= 16) {
+        prefetch_l2(&S.at(t - 16, 0)); prefetch_l2(&S.at(t - 16, 1)); prefetch_l2(&S.at(t - 16, 2));
+        prefetch_l2(x + s0 + t - 16); prefetch_l2(y + s0 + t - 16);
       }
-      I.yq[k] = newint64(q, xj, xj1, yj, yj1, ppj, ppj1, hj, ihj);
-      if (I.jq) I.jq[k] = (int32_t)j;
-      ++k;
+      c_t = S.at(t - 1, 0); d_t = S.at(t - 1, 1); ih_t = S.at(t - 1, 2);
+      x_t = x[s0 + t - 1]; y_t = y[s0 + t - 1];
     }
+    const double Yt = d - c * Y;  // y''_t
+    if (I.ypp) I.ypp[s0 + t] = Yt;
+    if (k >= klo) {
+      const long long kxt = dkey(xt);
+      const double h = xt1 - xt;
+      while (k >= klo && (t == 0 || kq > kxt)) {
+        I.yq[k] = newint64(q, xt, xt1, yt, yt1, Yt, Y, h, ih);
+        if (I.jq) I.jq[k] = (int32_t)(s0 + t);
+        --k;
+        if (k >= klo) { q = G.at(k); kq = dkey(q); }
+      }
+    }
+    Y = Yt;
+    xt1 = xt; yt1 = yt;
   }
 }
 
@@ -299,12 +346,25 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     base = __shfl_sync(0xffffffffu, base, 0);
     if ((long long)base >= total_tiles) break;
     const long long t = (long long)base + lane;
+    // every lane passes both warp barriers; lanes without a tile, or with an empty one, idle
+    Inst I;
+    TileRows T;
+    T.s0 = T.e0 = 0;
+    T.succ = false;
+    long long rlast = -1;
+    unsigned bad = 0;
     if (t < total_tiles) {
       const int i = find_inst(insts, ninst, t);
-      const Inst I = insts[i];
-      tile_f64(I, t - I.tile_begin, S);
+      I = insts[i];
+      T = tile_rows_of(I, t - I.tile_begin);
+      if (T.s0 < I.n) rlast = tile_forward(I, T, S, &bad);
     }
-    __syncwarp();
+    __syncwarp();  // the next lane's forward rows are in the scratch
+    if (rlast >= 0) {
+      tile_backward_eval(I, T, rlast, S);
+      if (bad) atomicOr(I.status, bad);
+    }
+    __syncwarp();  // the scratch is reused by the next batch of tiles
   }
 }
 
@@ -312,6 +372,10 @@ size_t ring_bytes_f64(long long threads, int tile_rows) {
   const long long warps = (threads + 31) / 32;
   return (size_t)warps * ((size_t)tile_rows + kHaloB) * kFields * 32 * sizeof(double);
 }
+
+int f64_threads_per_sm() { return kThreads * kCtasPerSm; }
+
+int overhang_rows_f64() { return kHaloB; }
 
 int halo_rows_f64() { return kHaloFMax + kHaloB; }
 

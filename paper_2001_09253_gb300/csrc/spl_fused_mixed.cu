@@ -184,14 +184,6 @@ struct FwdM {
   float h, s, cp, dp;
 };
 
-// Input checks of row j (section "Generating Second Derivatives" takes strictly increasing
-// knots; finite values are required on top), made while the forward sweep passes it.
-__device__ __forceinline__ unsigned row_check(double xj, double yj, bool has_next, double xj1) {
-  unsigned bad = (!finite64(xj) || !finite64(yj)) ? kStNonFinite : 0u;
-  if (has_next && !(dkey(xj1) > dkey(xj))) bad |= kStNotIncreasing;
-  return bad;
-}
-
 // kFitOnly: first pass of the refined path; y'' (binary32) goes to the scratch I.z and no
 // query is evaluated.
 template <bool kFitOnly>
