@@ -46,14 +46,19 @@ constexpr int kHaloB = 48;              // back-substitution start past the tile
 constexpr int kHaloFMax = 192;          // forward-elimination halo, worst case: (2/3)^192
 constexpr int kHaloFMin = 16;
 constexpr int kFields = 3;              // c', d' (then y''), 1/h
+constexpr int kHaloC = 16;              // c'-only rows before a chained tile: error factor <= 1/12 per row
+constexpr int kLane0Short = 40;         // the first lane of a group runs a full halo: its tile is shorter
+constexpr int kMRows = 192;             // sensitivity rows kept per lane: (2/3)^192 < 2^-110
 
 // Per-warp scratch: rows relative to the tile start, fields, lanes.
 struct Scratch64 {
-  double *base;
+  double *base;  // rows x kFields x 32 lanes
+  double *mb;    // kMRows x 32 lanes: sensitivities of a chained tile's d' to d'_{s0-1}
   int lane;
   __device__ __forceinline__ double &at(long long row, int f) const {
     return base[(((size_t)row * kFields + f) << 5) + lane];
   }
+  __device__ __forceinline__ double &m(int row) const { return mb[(row << 5) + lane]; }
 };
 
 // Evaluation of one query, "Fast Interpolation": with ba = x_{j+1}-x_j, xa = x-x_j,
@@ -135,14 +140,22 @@ struct Fwd64 {
   double xl, yl;
 };
 
-// Rows of a tile.  Plain geometry: tile k covers [kL, (k+1)L).  Grouped geometry (instances
-// whose tiles are aligned to warps, flag bit 0): the 32 tiles of a warp cover 32L - kHaloB
-// consecutive rows, the last of them being kHaloB rows shorter, because every lane but the
-// last takes the rows past its tile (the back substitution's start) from the next lane's
-// forward sweep instead of recomputing them.
+// Rows of a tile.  Plain geometry: tile k covers [kL, (k+1)L), each tile starting its forward
+// elimination a halo earlier.  Grouped geometry (instances whose tiles are aligned to warps,
+// flag bit 0): the 32 tiles of a warp cover 32L - kHaloB - kLane0Short consecutive rows.
+//   * Every lane but the last takes the rows past its tile (the back substitution's start)
+//     from the next lane's forward sweep; the last lane computes them, so its tile is kHaloB
+//     rows shorter.
+//   * Only the first lane runs a halo (its tile is kLane0Short rows shorter).  The others are
+//     chained: they start at their first row with the exact c' (kHaloC rows of the c'
+//     recurrence alone before it) and the guess d' = 0, and keep the sensitivity M_i of their
+//     d'_i to the true d'_{s0-1}, which is linear: d'_i = d'_i(guess) + M_i d'_{s0-1}.  After
+//     the sweep a warp scan over the lanes' affine maps gives every lane its d'_{s0-1}, and the
+//     rows with |M_i| >= 2^-110 are corrected.
 struct TileRows {
   long long s0, e0;
-  bool succ;  // the next lane holds rows [e0, e0 + kHaloB) of its own forward sweep
+  bool succ;   // the next lane holds rows [e0, e0 + kHaloB) of its own forward sweep
+  bool chain;  // chained start (see above)
 };
 
 __device__ __forceinline__ TileRows tile_rows_of(const Inst &I, long long tile) {
@@ -150,28 +163,58 @@ __device__ __forceinline__ TileRows tile_rows_of(const Inst &I, long long tile) 
   TileRows T;
   if (I.pad & 1) {
     const long long lane = tile & 31;
-    T.s0 = (tile >> 5) * (32 * L - kHaloB) + lane * L;
-    T.e0 = min(T.s0 + (lane == 31 ? L - kHaloB : L), n);
+    const long long g0 = (tile >> 5) * (32 * L - kHaloB - kLane0Short);
+    T.s0 = lane == 0 ? g0 : g0 + lane * L - kLane0Short;
+    const long long len = lane == 0 ? L - kLane0Short : (lane == 31 ? L - kHaloB : L);
+    T.e0 = min(T.s0 + len, n);
     T.succ = lane < 31 && T.e0 < n;
+    T.chain = lane > 0;
   } else {
     T.s0 = tile * L;
     T.e0 = min(T.s0 + L, n);
     T.succ = false;
+    T.chain = false;
   }
   return T;
 }
 
-// Forward elimination of a tile (rows from the halo start to rlast) into the scratch; returns
-// rlast and ORs the input checks of the tile's rows into *bad.
-__device__ long long tile_forward(const Inst &I, const TileRows &T, const Scratch64 &S, unsigned *bad_out) {
+// What the forward sweep hands to the lane scan.
+struct FwdOut {
+  long long rlast;  // last row of the sweep
+  double A, B;      // d' of the tile's last row as computed, and its sensitivity M there
+  int K;            // stored sensitivities (rows s0 .. s0+K-1)
+  unsigned bad;     // input checks of the tile's rows
+};
+
+// Forward elimination of a tile (rows from the halo start, or from s0 when chained, to
+// rlast) into the scratch.
+__device__ FwdOut tile_forward(const Inst &I, const TileRows &T, const Scratch64 &S) {
   const long long n = I.n;
   const double *__restrict__ x = I.x;
   const double *__restrict__ y = I.y;
   const long long s0 = T.s0, e0 = T.e0;
   const bool nat0 = is_natural(I.yp1), nat1 = is_natural(I.ypn);
   unsigned bad = 0;  // input checks of the tile's rows, made as the forward sweep passes them
-  // ---- 1. forward elimination ----
-  long long r = halo_start(x, n, s0);  // row whose (c', d') the state holds
+  // ---- 1. start: halo guess, or exact c'_{s0-1} for a chained tile ----
+  long long r;
+  double cp_start = 0.0;
+  if (T.chain) {
+    const long long i0 = max(s0 - 1 - kHaloC, 0LL);
+    double c = (i0 == 0 && !nat0) ? 0.5 : 0.0;  // exact at row 0, a guess elsewhere
+    double xb = x[i0 + 1];
+    double hp = xb - x[i0];
+    for (long long i = i0 + 1; i <= s0 - 1; ++i) {
+      const double xc = x[i + 1];
+      const double hi = xc - xb;
+      c = hi * rcp64(twice(hp + hi) - hp * c);
+      hp = hi;
+      xb = xc;
+    }
+    cp_start = c;
+    r = s0 - 1;
+  } else {
+    r = halo_start(x, n, s0);  // row whose (c', d') the state holds
+  }
   Fwd64 F;
   F.hn = F.ihn = F.sn = 0.0;
   F.xl = F.yl = 0.0;
@@ -199,7 +242,10 @@ __device__ long long tile_forward(const Inst &I, const TileRows &T, const Scratc
     const double x0 = x[r], x1 = x[r + 1], y0 = y[r], y1 = y[r + 1];
     const double h = x1 - x0, ih = rcp64(h), sl = quot64(y1 - y0, h, ih);
     F.h = h; F.s = sl; F.xn = x1; F.yn = y1;
-    if (r == 0 && !nat0) {            // clamped start: c'_0 = 1/2, d'_0 = 3(s_0 - y'_0)/h_0
+    if (T.chain) {                    // exact c'_{s0-1}, guess d'_{s0-1} = 0 (corrected later)
+      F.cp = cp_start;
+      F.dp = 0.0;
+    } else if (r == 0 && !nat0) {     // clamped start: c'_0 = 1/2, d'_0 = 3(s_0 - y'_0)/h_0
       F.cp = 0.5;
       F.dp = 3.0 * (sl - I.yp1) * ih;
     } else {                          // natural start, or the halo guess
@@ -216,37 +262,57 @@ __device__ long long tile_forward(const Inst &I, const TileRows &T, const Scratc
     }
     precompute_next(r + 1);
   }
+  FwdOut out;
+  out.A = 0.0;
+  out.B = 0.0;
+  double M = 1.0;       // sensitivity of d'_r to d'_{s0-1} (chained tiles)
+  int K = 0;
+  bool track = T.chain;
   const long long rlast = T.succ ? e0 - 1 : min(e0 + kHaloB, n) - 1;
   while (r < rlast) {
     const long long j = r + 1;
-    double cpj, dpj, ihj = 0.0;
+    double cpj, dpj, ihj = 0.0, iden;
+    const double a = F.h;  // a_j = h_{j-1}
     if (j <= n - 2) {
       const double hj = F.hn, sj = F.sn;
       ihj = F.ihn;
       const double den = twice(F.h + hj) - F.h * F.cp;
-      const double iden = rcp64(den);
+      iden = rcp64(den);
       cpj = hj * iden;
       dpj = (6.0 * (sj - F.s) - F.h * F.dp) * iden;
       F.h = hj; F.s = sj;
       precompute_next(j + 1);  // independent of the elimination chain above
     } else {  // j == n-1: last row
       cpj = 0.0;
-      if (nat1) {
-        dpj = 0.0;
-      } else {
-        const double den = 2.0 * F.h - F.h * F.cp;
-        dpj = (6.0 * (I.ypn - F.s) - F.h * F.dp) * rcp64(den);
-      }
+      const double den = 2.0 * F.h - F.h * F.cp;
+      iden = rcp64(den);
+      dpj = nat1 ? 0.0 : (6.0 * (I.ypn - F.s) - F.h * F.dp) * iden;
     }
     F.cp = cpj; F.dp = dpj;
     r = j;
     if (j >= s0) {
       S.at(j - s0, 0) = cpj; S.at(j - s0, 1) = dpj; S.at(j - s0, 2) = ihj;
     }
+    if (track) {  // d'_j = (r_j - a_j d'_{j-1}) / den_j: the sensitivity picks up -a_j / den_j
+      M *= (j == n - 1 && nat1) ? 0.0 : -a * iden;
+      S.m(K++) = M;
+      const int ex = (int)((__double_as_longlong(M) >> 52) & 0x7FF);
+      if (ex < 1023 - 110 || K == kMRows) track = false;
+    }
+    if (j == e0 - 1) {
+      out.A = dpj;
+      out.B = track ? M : 0.0;
+    }
   }
+  out.rlast = rlast;
+  out.K = K;
+  out.bad = bad;
+  return out;
+}
 
-  *bad_out = bad;
-  return rlast;
+// Chained tile: add M_i d'_{s0-1} to the stored d' of its first K rows.
+__device__ void tile_correct(const FwdOut &o, double delta, const Scratch64 &S) {
+  for (int k = 0; k < o.K; ++k) S.at(k, 1) = fma(S.m(k), delta, S.at(k, 1));
 }
 
 // Back substitution from rlast (y''_{rlast} := d'_{rlast}, exact when rlast == n-1), fused
@@ -262,7 +328,7 @@ __device__ void tile_backward_eval(const Inst &I, const TileRows &T, long long r
   double Y;
   long long t;
   if (T.succ) {
-    const Scratch64 Sn{S.base, S.lane + 1};  // the next lane's tile starts at row e0
+    const Scratch64 Sn{S.base, S.mb, S.lane + 1};  // the next lane's tile starts at row e0
     long long u = min(e0 + kHaloB, n) - 1 - e0;
     Y = Sn.at(u, 1);
     for (--u; u >= 0; --u) Y = Sn.at(u, 1) - Sn.at(u, 0) * Y;
@@ -290,46 +356,56 @@ __device__ void tile_backward_eval(const Inst &I, const TileRows &T, long long r
   if (t == te - 1 && I.ypp) I.ypp[n - 1] = Y;
 
   // queries of the tile: k in [klo, khi], x_k > x_{s0} (first_query) and x_k <= x_{e0} when
-  // e0 <= n-2; interval t takes those with x_t < x_k (the lowest interval all the rest)
+  // e0 <= n-2; interval t takes those with x_t < x_k (the lowest interval all the rest).  The
+  // loop runs one query per iteration, walking the rows down as far as the query needs, so
+  // that the lanes of a warp do the same FP64 work per iteration whatever the spread of the
+  // queries over their intervals.
   const bool evaluate = (m > 0 && s0 <= n - 2);
   const Grid G = make_grid(x, n, m);
   const long long klo = evaluate ? first_query(G, x, s0) : 0;
   long long k = evaluate ? ((e0 <= n - 2) ? first_query(G, x, e0) - 1 : m - 1) : -1;
-  double q = 0.0;
-  long long kq = 0;
-  if (k >= klo) { q = G.at(k); kq = dkey(q); }
-  double xt1 = x[s0 + t + 1], yt1 = y[s0 + t + 1];  // knot and value of row t+1
-  // row t's loads one row ahead
-  double c_t = 0.0, d_t = 0.0, ih_t = 0.0, x_t = 0.0, y_t = 0.0;
-  if (t >= 0) {
-    c_t = S.at(t, 0); d_t = S.at(t, 1); ih_t = S.at(t, 2);
-    x_t = x[s0 + t]; y_t = y[s0 + t];
-  }
-  for (; t >= 0; --t) {
-    const double c = c_t, d = d_t, ih = ih_t, xt = x_t, yt = y_t;
-    if (t > 0) {
-      if (t >= 16) {
-        prefetch_l2(&S.at(t - 16, 0)); prefetch_l2(&S.at(t - 16, 1)); prefetch_l2(&S.at(t - 16, 2));
-        prefetch_l2(x + s0 + t - 16); prefetch_l2(y + s0 + t - 16);
+  if (t < 0) return;  // a one-row tile at the end of the instance
+  // current row t: y''_t (Yt), y''_{t+1} (Yt1), its knot, value, 1/h and width; the next row
+  // down is loaded one step ahead
+  double Yt1 = Y;
+  double xt1 = x[s0 + t + 1], yt1 = y[s0 + t + 1];
+  double xt = x[s0 + t], yt = y[s0 + t], iht = S.at(t, 2);
+  double Yt = S.at(t, 1) - S.at(t, 0) * Yt1;
+  if (I.ypp) I.ypp[s0 + t] = Yt;
+  double c_n = 0.0, d_n = 0.0, ih_n = 0.0, x_n = 0.0, y_n = 0.0;
+  auto load_next = [&](long long row) {  // row t-1
+    if (row >= 0) {
+      if (row >= 8) {
+        prefetch_l1(&S.at(row - 8, 0)); prefetch_l1(&S.at(row - 8, 1)); prefetch_l1(&S.at(row - 8, 2));
+        prefetch_l1(x + s0 + row - 8); prefetch_l1(y + s0 + row - 8);
       }
-      c_t = S.at(t - 1, 0); d_t = S.at(t - 1, 1); ih_t = S.at(t - 1, 2);
-      x_t = x[s0 + t - 1]; y_t = y[s0 + t - 1];
+      c_n = S.at(row, 0); d_n = S.at(row, 1); ih_n = S.at(row, 2);
+      x_n = x[s0 + row]; y_n = y[s0 + row];
     }
-    const double Yt = d - c * Y;  // y''_t
+  };
+  load_next(t - 1);
+  auto step_down = [&]() {  // t -> t-1: one back-substitution step
+    --t;
+    Yt1 = Yt; xt1 = xt; yt1 = yt;
+    xt = x_n; yt = y_n; iht = ih_n;
+    Yt = d_n - c_n * Yt1;
     if (I.ypp) I.ypp[s0 + t] = Yt;
-    if (k >= klo) {
-      const long long kxt = dkey(xt);
-      const double h = xt1 - xt;
-      while (k >= klo && (t == 0 || kq > kxt)) {
-        I.yq[k] = newint64(q, xt, xt1, yt, yt1, Yt, Y, h, ih);
-        if (I.jq) I.jq[k] = (int32_t)(s0 + t);
-        --k;
-        if (k >= klo) { q = G.at(k); kq = dkey(q); }
-      }
+    load_next(t - 1);
+  };
+  long long kxt = dkey(xt);
+  double q = k >= klo ? G.at(k) : 0.0;  // the next query is formed one iteration ahead
+  for (; k >= klo; --k) {
+    const long long kq = dkey(q);
+    const double qn = k > klo ? G.at(k - 1) : 0.0;
+    while (t > 0 && kq <= kxt) {
+      step_down();
+      kxt = dkey(xt);
     }
-    Y = Yt;
-    xt1 = xt; yt1 = yt;
+    I.yq[k] = newint64(q, xt, xt1, yt, yt1, Yt, Yt1, xt1 - xt, iht);
+    if (I.jq) I.jq[k] = (int32_t)(s0 + t);
+    q = qn;
   }
+  while (t > 0) step_down();
 }
 
 // Persistent CTAs; each warp fetches 32 tiles at a time from a counter zeroed before the
@@ -338,7 +414,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     fused_f64_kernel(const Inst *__restrict__ insts, int ninst, long long total_tiles,
                      unsigned long long *__restrict__ counter, double *__restrict__ scratch, long long rows_cap) {
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const Scratch64 S{scratch + (size_t)warp * rows_cap * kFields * 32, (int)(threadIdx.x & 31)};
+  double *wbase = scratch + (size_t)warp * (rows_cap * kFields + kMRows) * 32;
+  const Scratch64 S{wbase, wbase + (size_t)rows_cap * kFields * 32, (int)(threadIdx.x & 31)};
   const int lane = threadIdx.x & 31;
   for (;;) {
     unsigned long long base = 0;
@@ -346,23 +423,40 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     base = __shfl_sync(0xffffffffu, base, 0);
     if ((long long)base >= total_tiles) break;
     const long long t = (long long)base + lane;
-    // every lane passes both warp barriers; lanes without a tile, or with an empty one, idle
+    // every lane takes part in the warp barriers and the scan; lanes without a tile, or with
+    // an empty one, idle
     Inst I;
     TileRows T;
     T.s0 = T.e0 = 0;
-    T.succ = false;
-    long long rlast = -1;
-    unsigned bad = 0;
+    T.succ = T.chain = false;
+    FwdOut o;
+    o.rlast = -1;
+    o.A = o.B = 0.0;
+    o.K = 0;
+    o.bad = 0;
     if (t < total_tiles) {
       const int i = find_inst(insts, ninst, t);
       I = insts[i];
       T = tile_rows_of(I, t - I.tile_begin);
-      if (T.s0 < I.n) rlast = tile_forward(I, T, S, &bad);
+      if (T.s0 < I.n) o = tile_forward(I, T, S);
     }
-    __syncwarp();  // the next lane's forward rows are in the scratch
-    if (rlast >= 0) {
-      tile_backward_eval(I, T, rlast, S);
-      if (bad) atomicOr(I.status, bad);
+    // d'_{s0-1} of every chained lane: inclusive scan of the maps delta -> A + B delta (the
+    // first lane of a group has B = 0), then the previous lane's result
+    double sa = o.A, sb = o.B;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const double pa = __shfl_up_sync(0xffffffffu, sa, off), pb = __shfl_up_sync(0xffffffffu, sb, off);
+      if (lane >= off) {
+        sa = fma(sb, pa, sa);
+        sb *= pb;
+      }
+    }
+    const double delta = __shfl_up_sync(0xffffffffu, sa, 1);
+    if (o.rlast >= 0 && T.chain) tile_correct(o, delta, S);
+    __syncwarp();  // the next lane's corrected forward rows are in the scratch
+    if (o.rlast >= 0) {
+      tile_backward_eval(I, T, o.rlast, S);
+      if (o.bad) atomicOr(I.status, o.bad);
     }
     __syncwarp();  // the scratch is reused by the next batch of tiles
   }
@@ -370,12 +464,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
 
 size_t ring_bytes_f64(long long threads, int tile_rows) {
   const long long warps = (threads + 31) / 32;
-  return (size_t)warps * ((size_t)tile_rows + kHaloB) * kFields * 32 * sizeof(double);
+  return (size_t)warps * (((size_t)tile_rows + kHaloB) * kFields + kMRows) * 32 * sizeof(double);
 }
 
 int f64_threads_per_sm() { return kThreads * kCtasPerSm; }
 
 int overhang_rows_f64() { return kHaloB; }
+
+int lane0_short_rows_f64() { return kLane0Short; }
 
 int halo_rows_f64() { return kHaloFMax + kHaloB; }
 

@@ -15,6 +15,7 @@ size_t ring_bytes_f64(long long threads, int tile_rows);
 long long threads_f64(int sm_count, long long total_tiles);
 int halo_rows_f64();
 int overhang_rows_f64();  // rows past a tile that start its back substitution
+int lane0_short_rows_f64();  // rows the first tile of an FP64 warp group gives up for its halo
 int f64_threads_per_sm();  // resident threads of the FP64 kernel per SM
 cudaError_t launch_fused_f64(const Inst *d_insts, int ninst, long long total_tiles, double *scratch,
                              int tile_rows, long long threads, unsigned long long *counter, cudaStream_t stream);

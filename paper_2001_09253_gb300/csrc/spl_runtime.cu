@@ -180,8 +180,8 @@ long long threads_for(const spl_ctx *c, int precision, long long total_tiles) {
 }
 
 // Tile length so that one instance of total_points fills every thread of one wave; never
-// shorter than a few halos.  FP64 tiles come in warp groups of 32L - overhang rows, so L is
-// chosen for the group count to match the warps.
+// shorter than a few halos.  FP64 tiles come in warp groups of 32L - overhang - lane0_short
+// rows, so L is chosen for the group count to match the warps.
 int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points) {
   const long long per_sm = precision == SPL_PREC_F64 ? spl::f64_threads_per_sm() : spl::mixed_threads_per_sm();
   const long long target = (long long)c->sm_count * per_sm;
@@ -189,7 +189,7 @@ int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points) {
   if (precision == SPL_PREC_F64) {
     const long long warps = std::max<long long>(target / 32, 1);
     const long long per_warp = (long long)((total_points + warps - 1) / warps);
-    L = (per_warp + spl::overhang_rows_f64() + 31) / 32;
+    L = (per_warp + spl::overhang_rows_f64() + spl::lane0_short_rows_f64() + 31) / 32;
   }
   L = std::max<long long>(L, 128);
   L = std::min<long long>(L, 1 << 20);
@@ -247,8 +247,9 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
   lp.refine_steps = p->precision == SPL_PREC_F64 ? 0 : p->refine_steps;
   lp.insts.resize(count);
   // FP64 instances of 32 tiles or more use the grouped geometry: their tiles start on a warp
-  // boundary, and each warp's 32 tiles cover 32L - overhang rows (the FP64 kernel's lanes take
-  // the rows past their tile from the next lane)
+  // boundary, and each warp's 32 tiles cover 32L - overhang - lane0_short rows (the FP64
+  // kernel's lanes take the rows past their tile from the next lane and, but for the first,
+  // their start state from the previous one)
   const long long ov = p->precision == SPL_PREC_F64 ? spl::overhang_rows_f64() : 0;
   long long tiles = 0;
   for (uint32_t i = 0; i < count; ++i) {
@@ -260,8 +261,8 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
     I.yp1 = r.yp1; I.ypn = r.ypn;
     I.tile_rows = L;
     I.ntiles = ((long long)r.n + L - 1) / L;
-    if (ov > 0 && I.ntiles >= 32 && L > 2 * ov) {
-      const long long G = 32LL * L - ov;
+    if (ov > 0 && I.ntiles >= 32 && L > ov + spl::lane0_short_rows_f64()) {
+      const long long G = 32LL * L - ov - spl::lane0_short_rows_f64();
       tiles = (tiles + 31) / 32 * 32;
       I.ntiles = 32 * (((long long)r.n + G - 1) / G);
       I.pad = 1;
