@@ -47,7 +47,7 @@ constexpr int kHaloFMax = 192;          // forward-elimination halo, worst case:
 constexpr int kHaloFMin = 16;
 constexpr int kFields = 3;              // c', d' (then y''), 1/h
 constexpr int kHaloC = 16;              // c'-only rows before a chained tile: error factor <= 1/12 per row
-constexpr int kLane0Short = 40;         // the first lane of a group runs a full halo: its tile is shorter
+constexpr int kLane0Short = 56;         // the first lane of a group runs a full halo: its tile is shorter
 constexpr int kMRows = 192;             // sensitivity rows kept per lane: (2/3)^192 < 2^-110
 
 // Per-warp scratch: rows relative to the tile start, fields, lanes.
