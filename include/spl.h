@@ -84,7 +84,7 @@ typedef struct spl_batch spl_batch;
  *   arena_bytes  size of the arena.  It is also the memory budget: requests whose
  *                footprint (inputs, outputs, scratch) cannot fit are refused with
  *                SPL_ERR_BUDGET, requests that do not fit right now with SPL_ERR_QUEUE_FULL
- *                (or wait in the serving queue, see spl_serve_start).
+ *                (or wait in the serving queue, see spl_serve_create).
  *   max_slots    requests that may be in flight at once (>= 1). */
 typedef struct spl_ctx_desc {
   int32_t device;
