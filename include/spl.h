@@ -8,7 +8,8 @@
  *           "Start and End Derivatives" (an end slope > 0.99e30 selects the
  *           natural end y'' = 0, any other finite slope clamps S' there), solved
  *           as Thomas' algorithm of section "Implementation" prescribes;
- *   eval  - S(x_k) at M uniformly spaced queries x_k = x_0 + k*step,
+ *   eval  - S(x_k) at M uniformly spaced queries x_k = x_0 + k*step (or at M explicit
+ *           positions, see spl_query_mode),
  *           step = (x_{n-1}-x_0)/(M-1), the last query forced to x_{n-1}
  *           (section "Curve Interpolation", benchmark step 8), each query
  *           bracketed to the interval j with x_j < x_k <= x_{j+1} (j = 0 for
@@ -70,6 +71,28 @@ typedef enum spl_mem {
                                its arena and copies results back before completion */
 } spl_mem;
 
+/* Where the queries come from (plan option). */
+typedef enum spl_query_mode {
+  SPL_QUERY_UNIFORM = 0,    /* m uniform queries on [x_0, x_{n-1}] (section "Curve Interpolation") */
+  SPL_QUERY_EXPLICIT = 1    /* m caller-given positions xq[m], any order, each bracketed by
+                               bisection (the interval search of section "Quality Checks" for an
+                               unsorted query; SPL_PREC_F64 plans only) */
+} spl_query_mode;
+
+/* Form of the evaluation (plan option; used when the queries are evaluated by the separate
+ * evaluation kernel, i.e. explicit queries or a request with ypp_in).  The three variants of
+ * section "Fast Interpolation" benchmarked in section "Curve Interpolation":
+ *   ORIG   inv_ba = 1/(x_{j+1}-x_j) formed first, the sum multiplied by it (the paper's newint);
+ *   NOINV  the sum divided by (x_{j+1}-x_j) at the end;
+ *   VOL    ORIG with inv_ba kept in a volatile local (a memory round trip pins the division
+ *          before the cubic, the paper's scheduling trick).
+ * All three agree to rounding; the fused uniform-grid kernels always use ORIG. */
+typedef enum spl_eval_variant {
+  SPL_EVAL_ORIG = 0,
+  SPL_EVAL_NOINV = 1,
+  SPL_EVAL_VOL = 2
+} spl_eval_variant;
+
 typedef struct spl_ctx spl_ctx;
 typedef struct spl_plan spl_plan;
 typedef struct spl_batch spl_batch;
@@ -102,12 +125,16 @@ typedef struct spl_ctx_desc {
  *                 system formed in double-float arithmetic, then the evaluation).  Other
  *                 values are SPL_ERR_INVALID_ARG.
  *   tile_rows     knots per tile of the chunked solve; 0 picks it from the device and n.
- *                 Exposed so tests can force many small tiles; values below 16 are refused. */
+ *                 Exposed so tests can force many small tiles; values below 16 are refused.
+ *   query_mode    spl_query_mode; SPL_QUERY_EXPLICIT needs precision SPL_PREC_F64.
+ *   eval_variant  spl_eval_variant of the separate evaluation kernel. */
 typedef struct spl_plan_desc {
   uint64_t max_n;
   int32_t precision;
   int32_t refine_steps;
   int32_t tile_rows;
+  int32_t query_mode;
+  int32_t eval_variant;
   int32_t reserved;
 } spl_plan_desc;
 
@@ -115,11 +142,18 @@ typedef struct spl_plan_desc {
  *   n, x, y      knots (strictly increasing) and values, n >= 3.
  *   yp1, ypn     end slopes S'(x_0), S'(x_{n-1}); a value > 0.99e30 (e.g. 1e32 or +inf)
  *                selects the natural end.  NaN or -inf is SPL_ERR_INVALID_ARG.
- *   m            number of uniform queries (0 = fit only; 1 = the single query x_0).
+ *   m            number of queries (0 = fit only; uniform mode: 1 = the single query x_0).
  *   ypp_out      y''[n] output, or NULL if not wanted.
  *   yq_out       S(x_k)[m] output (NULL allowed only when m == 0).
  *   jq_out       optional int32 bracket index per query (j of the interval used), or NULL.
- *   mem          spl_mem: where x, y and the outputs live. */
+ *   mem          spl_mem: where every array of the request lives.
+ *   xq           explicit-mode plans: the m query positions (finite, any order; a query
+ *                below x_0 or above x_{n-1} is extrapolated by the end cubic).  Must be NULL
+ *                in uniform mode.  A non-finite position completes with SPL_ERR_NONFINITE.
+ *   ypp_in       NULL: fit, then evaluate.  Otherwise y''[n] of an earlier fit of the same
+ *                x, y (SPL_PREC_F64 plans only): the fit is skipped and only the evaluation
+ *                runs ("fit once, evaluate many"); ypp_out and the end slopes are ignored.
+ *                Every request of one spl_submit_batch call must agree on NULL or not. */
 typedef struct spl_request {
   uint64_t n;
   const double *x;
@@ -132,6 +166,8 @@ typedef struct spl_request {
   int32_t *jq_out;
   int32_t mem;
   int32_t reserved;
+  const double *xq;
+  const double *ypp_in;
 } spl_request;
 
 /* Completion record.

@@ -26,6 +26,9 @@ struct Inst {
   int pad;              // bit 0: grouped tile geometry (FP64 kernel)
   unsigned *status;     // device word, OR of kSt* bits
   float *z;             // mixed path with refinement: binary32 y'' of the first pass (n), scratch
+  const double *xq;     // separate evaluation: explicit query positions (mq), or null for the grid
+  long long mq;         // separate evaluation: queries (the fused kernels see m = 0 then)
+  long long q_begin;    // separate evaluation: global index of this instance's first query
 };
 
 // One request appended by the host to the serving ring (mapped host memory).

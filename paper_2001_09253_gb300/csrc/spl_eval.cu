@@ -1,0 +1,108 @@
+// Evaluation of a fitted spline at a batch of queries, one thread per query: explicit query
+// positions in any order (or the uniform grid of section "Curve Interpolation"), each
+// bracketed by bisection, then one of the three forms of section "Fast Interpolation" that the
+// paper benchmarks (section "Curve Interpolation": newint orig / noinv / vol).
+//
+// Bracketing is the definition the monotone sweep of section "Quality Checks" implements for
+// sorted queries: the largest i in [0, n-2] with x_i < q, or 0 when there is none.  It runs on
+// the order-preserving integer keys of the binary64 values, so the index is bit-identical to a
+// binary64 comparison; a query equal to a knot takes the interval on its left.  Each probe is a
+// dependent load: sorted queries share their probe paths between neighbouring threads (cache
+// hits), unsorted ones pay about log2(n) latencies each, hidden by many threads per SM.
+#include <algorithm>
+
+#include "spl_device.cuh"
+#include "spl_internal.h"
+
+namespace spl {
+
+constexpr int kThreadsE = 256;
+constexpr int kBlocksPerSmE = 8;
+
+__device__ __forceinline__ long long bracket_bisect(const double *__restrict__ x, long long n, long long kq) {
+  long long lo = 0, hi = n - 1;  // knots x_0..x_{n-2} below q: a count in [lo, hi]
+  while (lo < hi) {
+    const long long mid = lo + ((hi - lo) >> 1);
+    if (dkey(x[mid]) < kq) lo = mid + 1; else hi = mid;
+  }
+  return lo > 0 ? lo - 1 : 0;
+}
+
+// The one-division form, with ba = x_{j+1}-x_j, xa = x-x_j, bx = x_{j+1}-x:
+//   y = (xa y_{j+1} + bx y_j + (1/6)((xa^2-ba^2) xa y''_{j+1} + (bx^2-ba^2) bx y''_j)) / ba.
+// kVariant 0 (orig): inv_ba = 1/ba formed first, the sum multiplied by it.
+// kVariant 1 (noinv): the sum divided by ba.
+// kVariant 2 (vol): orig with inv_ba held in a volatile local, whose store and reload pin the
+// division ahead of the cubic.
+template <int kVariant>
+__device__ __forceinline__ double newint_variant(double q, double xj, double xj1, double yj, double yj1, double ppj,
+                                                 double ppj1) {
+  const double ba = xj1 - xj;
+  double inv_ba = 0.0;
+  volatile double inv_pinned;
+  if (kVariant == 0) inv_ba = 1.0 / ba;
+  if (kVariant == 2) inv_pinned = 1.0 / ba;
+  const double xa = q - xj;
+  const double bx = xj1 - q;
+  const double ba2 = ba * ba;
+  const double lower = xa * yj1 + bx * yj;
+  const double C = (xa * xa - ba2) * xa * ppj1;
+  const double D = (bx * bx - ba2) * bx * ppj;
+  const double sum = lower + (1.0 / 6.0) * (C + D);
+  if (kVariant == 1) return sum / ba;
+  if (kVariant == 2) return sum * inv_pinned;
+  return sum * inv_ba;
+}
+
+template <int kVariant>
+__global__ void __launch_bounds__(kThreadsE) eval_kernel(const Inst *__restrict__ insts, int ninst,
+                                                         long long total_q) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  int cur = -1;  // instance whose grid is cached
+  Grid G{};
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total_q; g += stride) {
+    int lo = 0, hi = ninst - 1;  // the instance owning query g: last with q_begin <= g
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (insts[mid].q_begin <= g) lo = mid; else hi = mid - 1;
+    }
+    const Inst &I = insts[lo];
+    const long long n = I.n, k = g - I.q_begin;
+    const double *__restrict__ x = I.x;
+    double q;
+    if (I.xq) {
+      q = I.xq[k];
+      if (!finite64(q)) {
+        atomicOr(I.status, kStNonFinite);
+        continue;
+      }
+    } else {
+      if (lo != cur) {
+        G = make_grid(x, n, I.mq);
+        cur = lo;
+      }
+      q = G.at(k);
+    }
+    const long long j = bracket_bisect(x, n, dkey(q));
+    const double *__restrict__ y = I.y;
+    const double *__restrict__ ypp = I.ypp;
+    I.yq[k] = newint_variant<kVariant>(q, x[j], x[j + 1], y[j], y[j + 1], ypp[j], ypp[j + 1]);
+    if (I.jq) I.jq[k] = (int32_t)j;
+  }
+}
+
+cudaError_t launch_eval(const Inst *d_insts, int ninst, long long total_q, int variant, int sm_count,
+                        cudaStream_t stream) {
+  if (total_q <= 0) return cudaSuccess;
+  const long long blocks =
+      std::min<long long>((total_q + kThreadsE - 1) / kThreadsE, (long long)sm_count * kBlocksPerSmE);
+  const unsigned grid = (unsigned)std::max<long long>(blocks, 1);
+  switch (variant) {
+    case 1: eval_kernel<1><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q); break;
+    case 2: eval_kernel<2><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q); break;
+    default: eval_kernel<0><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace spl

@@ -34,6 +34,11 @@ cudaError_t launch_serve(const ServeArgs &args, int sm_count, cudaStream_t strea
 int serve_tile_threads();
 int mixed_threads_per_sm();  // threads of one mixed-kernel CTA (one CTA per SM)
 
+// Separate evaluation (spl_eval.cu): queries q_begin .. q_begin+mq-1 of each instance, explicit
+// (Inst::xq) or on the uniform grid, with the y'' in Inst::ypp; variant = spl_eval_variant.
+cudaError_t launch_eval(const Inst *d_insts, int ninst, long long total_q, int variant, int sm_count,
+                        cudaStream_t stream);
+
 }  // namespace spl
 
 // Context services for the other host translation units (defined in spl_runtime.cu; each

@@ -95,6 +95,8 @@ struct spl_plan {
   int precision;
   int refine_steps;
   int tile_rows;
+  int query_mode;
+  int eval_variant;
 };
 
 struct Job;
@@ -168,6 +170,12 @@ spl_status check_request(const spl_plan *plan, const spl_request *r) {
   if (r->m > 0 && !r->yq_out) return SPL_ERR_INVALID_ARG;
   if (!slope_ok(r->yp1) || !slope_ok(r->ypn)) return SPL_ERR_INVALID_ARG;
   if (r->mem != SPL_MEM_DEVICE && r->mem != SPL_MEM_HOST) return SPL_ERR_INVALID_ARG;
+  if (plan->query_mode == SPL_QUERY_EXPLICIT) {
+    if (r->m > 0 && !r->xq) return SPL_ERR_INVALID_ARG;
+  } else if (r->xq) {
+    return SPL_ERR_INVALID_ARG;
+  }
+  if (r->ypp_in && plan->precision != SPL_PREC_F64) return SPL_ERR_INVALID_ARG;
   return SPL_OK;
 }
 
@@ -211,13 +219,17 @@ struct LaunchPlan {
   long long total_tiles = 0;
   long long threads = 0;
   uint64_t ring_bytes = 0;
+  bool fit = true;             // run the fit kernel(s)
+  bool separate_eval = false;  // evaluate with the separate kernel (explicit queries, stored y'')
+  int eval_variant = 0;
+  long long total_queries = 0;
   // host-memory staging: device copies of inputs/outputs
   struct HostIO {
-    const double *hx, *hy;
+    const double *hx, *hy, *hxq, *hyppin;
     double *hypp, *hyq;
     int32_t *hjq;
     uint64_t n, m;
-    uint64_t off_x, off_y, off_ypp, off_yq, off_jq;
+    uint64_t off_x, off_y, off_ypp, off_yq, off_jq, off_xq, off_yppin;
   };
   std::vector<HostIO> hio;
 };
@@ -245,6 +257,9 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
   const int L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points);
   lp.precision = p->precision;
   lp.refine_steps = p->precision == SPL_PREC_F64 ? 0 : p->refine_steps;
+  lp.fit = reqs[0].ypp_in == nullptr;
+  lp.separate_eval = p->query_mode == SPL_QUERY_EXPLICIT || !lp.fit;
+  lp.eval_variant = p->eval_variant;
   lp.insts.resize(count);
   // FP64 instances of 32 tiles or more use the grouped geometry: their tiles start on a warp
   // boundary, and each warp's 32 tiles cover 32L - overhang - lane0_short rows (the FP64
@@ -269,21 +284,38 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
     }
     I.tile_begin = tiles;
     tiles += I.ntiles;
+    if (lp.separate_eval) {  // the fit kernel sees no queries; the evaluation kernel takes them
+      I.xq = r.xq;
+      I.mq = I.m;
+      I.m = 0;
+      I.q_begin = lp.total_queries;
+      lp.total_queries += I.mq;
+      if (!lp.fit) I.ypp = const_cast<double *>(r.ypp_in);
+    }
   }
   lp.total_tiles = tiles;
   lp.threads = threads_for(c, p->precision, tiles);
   lp.tile_rows = L;
-  lp.ring_bytes = p->precision == SPL_PREC_F64 ? spl::ring_bytes_f64(lp.threads, L) : 0;
+  lp.ring_bytes = (p->precision == SPL_PREC_F64 && lp.fit) ? spl::ring_bytes_f64(lp.threads, L) : 0;
 
   // footprint check against the whole budget first
   uint64_t need = round_up(sizeof(Inst) * count, kAlign) + round_up(status_block_bytes(count), kAlign) +
                   round_up(lp.ring_bytes, kAlign);
+  // a fit feeding the separate evaluation needs y'' somewhere: the caller's ypp_out or scratch
+  auto needs_ypp_scratch = [&](const spl_request &r) {
+    return lp.separate_eval && lp.fit && r.m > 0 && (!r.ypp_out || r.mem == SPL_MEM_HOST);
+  };
   for (uint32_t i = 0; i < count; ++i) {
-    if (reqs[i].mem == SPL_MEM_HOST) {
-      need += round_up(8 * reqs[i].n, kAlign) * 2;
-      if (reqs[i].ypp_out) need += round_up(8 * reqs[i].n, kAlign);
-      if (reqs[i].m) need += round_up(8 * reqs[i].m, kAlign);
-      if (reqs[i].jq_out && reqs[i].m) need += round_up(4 * reqs[i].m, kAlign);
+    const spl_request &r = reqs[i];
+    if (r.mem == SPL_MEM_HOST) {
+      need += round_up(8 * r.n, kAlign) * 2;
+      if (r.ypp_out && lp.fit) need += round_up(8 * r.n, kAlign);
+      if (r.m) need += round_up(8 * r.m, kAlign);
+      if (r.jq_out && r.m) need += round_up(4 * r.m, kAlign);
+      if (r.xq && r.m) need += round_up(8 * r.m, kAlign);
+      if (r.ypp_in) need += round_up(8 * r.n, kAlign);
+    } else if (needs_ypp_scratch(r)) {
+      need += round_up(8 * r.n, kAlign);
     }
   }
   // refined mixed path: binary32 y'' of the first pass, one float per knot (scratch)
@@ -307,21 +339,35 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
   }
   for (uint32_t i = 0; ok && i < count; ++i) {
     const spl_request &r = reqs[i];
-    if (r.mem != SPL_MEM_HOST) continue;
+    if (r.mem != SPL_MEM_HOST) {
+      if (needs_ypp_scratch(r)) {  // device request: y'' for the evaluation, not returned
+        uint64_t off = 0;
+        ok = dev_alloc(c, 8 * r.n, dev_blocks, &off);
+        if (ok) lp.insts[i].ypp = reinterpret_cast<double *>(c->arena + off);
+      }
+      continue;
+    }
     LaunchPlan::HostIO h{};
-    h.hx = r.x; h.hy = r.y; h.hypp = r.ypp_out; h.hyq = r.yq_out; h.hjq = r.jq_out;
+    h.hx = r.x; h.hy = r.y; h.hyq = r.yq_out; h.hjq = r.jq_out;
+    h.hypp = lp.fit ? r.ypp_out : nullptr;
+    h.hxq = (r.xq && r.m) ? r.xq : nullptr;
+    h.hyppin = r.ypp_in;
     h.n = r.n; h.m = r.m;
     ok = dev_alloc(c, 8 * r.n, dev_blocks, &h.off_x) && dev_alloc(c, 8 * r.n, dev_blocks, &h.off_y);
-    if (ok && r.ypp_out) ok = dev_alloc(c, 8 * r.n, dev_blocks, &h.off_ypp);
+    const bool dev_ypp = (lp.fit && r.ypp_out) || needs_ypp_scratch(r) || r.ypp_in;
+    if (ok && dev_ypp) ok = dev_alloc(c, 8 * r.n, dev_blocks, &h.off_ypp);
     if (ok && r.m) ok = dev_alloc(c, 8 * r.m, dev_blocks, &h.off_yq);
     if (ok && r.jq_out && r.m) ok = dev_alloc(c, 4 * r.m, dev_blocks, &h.off_jq);
+    if (ok && h.hxq) ok = dev_alloc(c, 8 * r.m, dev_blocks, &h.off_xq);
+    h.off_yppin = h.off_ypp;
     if (ok) {
       Inst &I = lp.insts[i];
       I.x = reinterpret_cast<const double *>(c->arena + h.off_x);
       I.y = reinterpret_cast<const double *>(c->arena + h.off_y);
-      I.ypp = r.ypp_out ? reinterpret_cast<double *>(c->arena + h.off_ypp) : nullptr;
+      I.ypp = dev_ypp ? reinterpret_cast<double *>(c->arena + h.off_ypp) : nullptr;
       I.yq = r.m ? reinterpret_cast<double *>(c->arena + h.off_yq) : nullptr;
       I.jq = (r.jq_out && r.m) ? reinterpret_cast<int32_t *>(c->arena + h.off_jq) : nullptr;
+      if (h.hxq) I.xq = reinterpret_cast<const double *>(c->arena + h.off_xq);
       lp.hio.push_back(h);
     }
   }
@@ -344,18 +390,25 @@ cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, 
   const int count = (int)lp.insts.size();
   unsigned long long *counters =
       reinterpret_cast<unsigned long long *>(c->arena + d_status_off + status_words_bytes(count));
-  cudaError_t e;
-  if (lp.precision == SPL_PREC_F64) {
+  cudaError_t e = cudaSuccess;
+  if (!lp.fit) {
+    // stored y'': evaluation only
+  } else if (lp.precision == SPL_PREC_F64) {
     e = spl::launch_fused_f64(insts, count, lp.total_tiles, reinterpret_cast<double *>(c->arena + d_ring_off),
                               lp.tile_rows, lp.threads, counters, st);
+    if (launches) *launches += 1;
   } else if (lp.refine_steps == 0) {
     e = spl::launch_fused_mixed(insts, count, lp.total_tiles, lp.threads, counters, st, false);
+    if (launches) *launches += 1;
   } else {
     e = spl::launch_fused_mixed(insts, count, lp.total_tiles, lp.threads, counters, st, true);
-    if (launches) *launches += 1;
     if (e == cudaSuccess) e = spl::launch_refine_mixed(insts, count, lp.total_tiles, lp.threads, counters + 1, st);
+    if (launches) *launches += 2;
   }
-  if (launches) *launches += 1;
+  if (e == cudaSuccess && lp.separate_eval && lp.total_queries > 0) {
+    e = spl::launch_eval(insts, count, lp.total_queries, lp.eval_variant, c->sm_count, st);
+    if (launches) *launches += 1;
+  }
   return e;
 }
 
@@ -372,6 +425,9 @@ cudaError_t enqueue(spl_ctx *c, const LaunchPlan &lp, char *pin_base, unsigned *
     if (e != cudaSuccess) break;
     e = cudaMemcpyAsync(c->arena + h.off_x, h.hx, 8 * h.n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->arena + h.off_y, h.hy, 8 * h.n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && h.hxq) e = cudaMemcpyAsync(c->arena + h.off_xq, h.hxq, 8 * h.m, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && h.hyppin)
+      e = cudaMemcpyAsync(c->arena + h.off_yppin, h.hyppin, 8 * h.n, cudaMemcpyHostToDevice, st);
   }
   if (e == cudaSuccess) e = launch_path(c, lp, d_insts_off, d_ring_off, d_status_off, st, launches);
   for (const auto &h : lp.hio) {
@@ -496,6 +552,9 @@ spl_status spl_plan_create(spl_ctx *c, const spl_plan_desc *d, spl_plan **out) {
   if (d->refine_steps < 0 || d->refine_steps > 1) return SPL_ERR_INVALID_ARG;
   if (d->precision == SPL_PREC_F64 && d->refine_steps != 0) return SPL_ERR_INVALID_ARG;
   if (d->tile_rows != 0 && d->tile_rows < 16) return SPL_ERR_INVALID_ARG;
+  if (d->query_mode != SPL_QUERY_UNIFORM && d->query_mode != SPL_QUERY_EXPLICIT) return SPL_ERR_INVALID_ARG;
+  if (d->query_mode == SPL_QUERY_EXPLICIT && d->precision != SPL_PREC_F64) return SPL_ERR_INVALID_ARG;
+  if (d->eval_variant < SPL_EVAL_ORIG || d->eval_variant > SPL_EVAL_VOL) return SPL_ERR_INVALID_ARG;
   spl_plan *p = new (std::nothrow) spl_plan();
   if (!p) return SPL_ERR_CUDA;
   p->ctx = c;
@@ -503,6 +562,8 @@ spl_status spl_plan_create(spl_ctx *c, const spl_plan_desc *d, spl_plan **out) {
   p->precision = d->precision;
   p->refine_steps = d->refine_steps;
   p->tile_rows = d->tile_rows;
+  p->query_mode = d->query_mode;
+  p->eval_variant = d->eval_variant;
   *out = p;
   return SPL_OK;
 }
@@ -515,6 +576,7 @@ spl_status spl_submit_batch(spl_ctx *c, spl_plan *p, const spl_request *reqs, ui
     spl_status s = check_request(p, &reqs[i]);
     if (s != SPL_OK) return s;
     if (reqs[i].mem != reqs[0].mem) return SPL_ERR_INVALID_ARG;
+    if ((reqs[i].ypp_in == nullptr) != (reqs[0].ypp_in == nullptr)) return SPL_ERR_INVALID_ARG;
   }
   std::lock_guard<std::mutex> lk(c->mu);
   if ((int)count > c->max_slots) return SPL_ERR_BUDGET;
@@ -616,6 +678,7 @@ spl_status spl_batch_create(spl_ctx *c, spl_plan *p, const spl_request *reqs, ui
     spl_status s = check_request(p, &reqs[i]);
     if (s != SPL_OK) return s;
     if (reqs[i].mem != SPL_MEM_DEVICE) return SPL_ERR_INVALID_ARG;
+    if ((reqs[i].ypp_in == nullptr) != (reqs[0].ypp_in == nullptr)) return SPL_ERR_INVALID_ARG;
   }
   std::lock_guard<std::mutex> lk(c->mu);
   if (cudaSetDevice(c->device) != cudaSuccess) return SPL_ERR_CUDA;

@@ -265,6 +265,7 @@ spl_status spl_serve_submit(spl_server *s, const spl_request *r, uint64_t *ticke
   if (!s || !r || !ticket) return SPL_ERR_INVALID_ARG;
   if (r->n < 3 || !r->x || !r->y || (r->m > 0 && !r->yq_out) || r->mem != SPL_MEM_DEVICE) return SPL_ERR_INVALID_ARG;
   if (r->n > (1ull << 40) || r->m > (1ull << 40)) return SPL_ERR_INVALID_ARG;
+  if (r->xq || r->ypp_in) return SPL_ERR_INVALID_ARG;  // served requests: uniform queries, fit included
   if (std::isnan(r->yp1) || std::isnan(r->ypn) || (std::isinf(r->yp1) && r->yp1 < 0) ||
       (std::isinf(r->ypn) && r->ypn < 0))
     return SPL_ERR_INVALID_ARG;

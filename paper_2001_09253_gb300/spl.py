@@ -22,6 +22,8 @@ ERR_INVALID_ARG, ERR_NOT_INCREASING, ERR_NONFINITE, ERR_BUDGET = -1, -2, -3, -4
 ERR_QUEUE_FULL, ERR_TIMEOUT, ERR_CUDA, ERR_UNKNOWN_TICKET, ERR_STATE = -5, -6, -7, -8, -9
 PREC_F64, PREC_F32_REFINE = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
+QUERY_UNIFORM, QUERY_EXPLICIT = 0, 1
+EVAL_ORIG, EVAL_NOINV, EVAL_VOL = 0, 1, 2
 NATURAL = 1e32
 
 EXPORTS = [
@@ -41,14 +43,16 @@ class CtxDesc(ctypes.Structure):
 
 class PlanDesc(ctypes.Structure):
     _fields_ = [("max_n", ctypes.c_uint64), ("precision", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
-                ("tile_rows", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tile_rows", ctypes.c_int32), ("query_mode", ctypes.c_int32), ("eval_variant", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
                 ("yp1", ctypes.c_double), ("ypn", ctypes.c_double), ("m", ctypes.c_uint64),
                 ("ypp_out", ctypes.c_void_p), ("yq_out", ctypes.c_void_p), ("jq_out", ctypes.c_void_p),
-                ("mem", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("mem", ctypes.c_int32), ("reserved", ctypes.c_int32), ("xq", ctypes.c_void_p),
+                ("ypp_in", ctypes.c_void_p)]
 
 
 class ServeDesc(ctypes.Structure):
@@ -156,23 +160,27 @@ def _is_host(a) -> bool:
     return a.device.type == "cpu"
 
 
-def make_request(x, y, yp1=NATURAL, ypn=NATURAL, m=None, ypp_out=None, yq_out=None, jq_out=None) -> Request:
+def make_request(x, y, yp1=NATURAL, ypn=NATURAL, m=None, ypp_out=None, yq_out=None, jq_out=None,
+                 xq=None, ypp_in=None) -> Request:
     n = int(x.shape[0])
-    m = n if m is None else int(m)
+    if m is None:
+        m = int(xq.shape[0]) if xq is not None else n
     r = Request()
     r.n, r.x, r.y = n, _ptr(x), _ptr(y)
-    r.yp1, r.ypn, r.m = float(yp1), float(ypn), m
+    r.yp1, r.ypn, r.m = float(yp1), float(ypn), int(m)
     r.ypp_out, r.yq_out, r.jq_out = _ptr(ypp_out), _ptr(yq_out), _ptr(jq_out)
+    r.xq, r.ypp_in = _ptr(xq), _ptr(ypp_in)
     r.mem = MEM_HOST if _is_host(x) else MEM_DEVICE
     return r
 
 
 class Plan:
     def __init__(self, ctx: "Context", max_n: int, precision: int = PREC_F64, refine_steps: int = 0,
-                 tile_rows: int = 0):
+                 tile_rows: int = 0, query_mode: int = 0, eval_variant: int = 0):
         self.ctx = ctx
         d = PlanDesc(max_n=int(max_n), precision=int(precision), refine_steps=int(refine_steps),
-                     tile_rows=int(tile_rows), reserved=0)
+                     tile_rows=int(tile_rows), query_mode=int(query_mode), eval_variant=int(eval_variant),
+                     reserved=0)
         h = ctypes.c_void_p()
         _check(ctx.lib.spl_plan_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)), "spl_plan_create")
         self.handle = h
@@ -242,12 +250,13 @@ class Context:
         self.handle = h
         self._keep = {}
 
-    def plan(self, max_n: int, precision: int = PREC_F64, refine_steps: int = 0, tile_rows: int = 0) -> Plan:
-        return Plan(self, max_n, precision, refine_steps, tile_rows)
+    def plan(self, max_n: int, precision: int = PREC_F64, refine_steps: int = 0, tile_rows: int = 0,
+             query_mode: int = 0, eval_variant: int = 0) -> Plan:
+        return Plan(self, max_n, precision, refine_steps, tile_rows, query_mode, eval_variant)
 
     def submit(self, plan: Plan, x, y, yp1=NATURAL, ypn=NATURAL, m=None, ypp_out=None, yq_out=None,
-               jq_out=None) -> int:
-        r = make_request(x, y, yp1, ypn, m, ypp_out, yq_out, jq_out)
+               jq_out=None, xq=None, ypp_in=None) -> int:
+        r = make_request(x, y, yp1, ypn, m, ypp_out, yq_out, jq_out, xq, ypp_in)
         t = ctypes.c_uint64()
         _check(self.lib.spl_submit(self.handle, plan.handle, ctypes.byref(r), ctypes.byref(t)), "spl_submit")
         self._keep[t.value] = (x, y, ypp_out, yq_out, jq_out)
