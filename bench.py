@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
-    ap.add_argument("--only", default="", choices=["", "f64", "mixed", "mixed-refine", "batched"],
+    ap.add_argument("--only", default="", choices=["", "f64", "mixed", "mixed-refine", "batched", "variants",
+                                                   "schedule"],
                     help="time one path only and print a short line (profiling runs)")
     ap.add_argument("--n", type=int, default=N_POINTS, help="knots = queries per instance (profiling runs)")
     ap.add_argument("--no-serving", action="store_true",
@@ -382,6 +383,117 @@ class Runner:
         b.close()
         return res, (sizes, off, X, Y, P, Q)
 
+    def _timed_submit(self, plan, m, yq, jq=None, xq=None, ypp_in=None, x=None, y=None, ypp_out=None):
+        """One request bracketed by CUDA events on the context's stream; returns device ms."""
+        torch, spl = self.torch, self.spl
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        t = self.ctx.submit(plan, self.x if x is None else x, self.y if y is None else y, spl.NATURAL,
+                            spl.NATURAL, m, ypp_out, yq, jq, xq=xq, ypp_in=ypp_in)
+        e1.record(self.stream)
+        s, _ = self.ctx.wait(t, 120.0)
+        assert s == spl.OK, spl.status_str(s)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    def eval_variants(self, reps=None):
+        """The three forms of section "Fast Interpolation" that the paper benchmarks (orig: one
+        reciprocal then a multiply; noinv: a division at the end; vol: orig with the reciprocal
+        pinned through a volatile local) on the separate evaluation kernel, from one stored FP64
+        fit of the n = 1e7 curve: M = n sorted queries (the uniform grid) and M = n unsorted ones
+        (seeded uniform positions).  The variants run in a shuffled order in every repetition, as
+        in the paper's benchmark; each launch is timed with CUDA events."""
+        torch, spl = self.torch, self.spl
+        n = self.n
+        K = reps or min(self.K, 30)
+        ypp = torch.empty(n, dtype=torch.float64, device=self.dev)
+        self._timed_submit(self.plan(spl.PREC_F64), 0, None, ypp_out=ypp)
+        rng = np.random.default_rng(4)
+        lo, hi = float(self.x[0]), float(self.x[-1])
+        xq = torch.from_numpy(rng.uniform(lo, hi, n)).to(self.dev)
+        yq = torch.empty(n, dtype=torch.float64, device=self.dev)
+        jq = torch.empty(n, dtype=torch.int32, device=self.dev)
+        names = ["orig", "noinv", "vol"]
+        out, samples = {}, {}
+        pick = np.sort(rng.choice(n, size=20000, replace=False))
+        for mode, label in ((spl.QUERY_UNIFORM, "sorted"), (spl.QUERY_EXPLICIT, "unsorted")):
+            plans = [self.ctx.plan(n, spl.PREC_F64, query_mode=mode, eval_variant=v) for v in range(3)]
+            times = [[] for _ in range(3)]
+            q = xq if mode == spl.QUERY_EXPLICIT else None
+            for rep in range(self.W + K):
+                for v in rng.permutation(3):
+                    ms = self._timed_submit(plans[v], n, yq, jq, xq=q, ypp_in=ypp)
+                    if rep >= self.W:
+                        times[v].append(ms)
+                    if rep == self.W + K - 1:
+                        samples[(label, names[v])] = (yq.cpu().numpy()[pick], jq.cpu().numpy()[pick])
+            out[label] = {names[v]: {"ms_median": float(np.median(times[v])), "ms_min": float(np.min(times[v])),
+                                     "queries_per_s": n / (np.median(times[v]) * 1e-3), "reps": K}
+                          for v in range(3)}
+            out[label]["fastest"] = names[int(np.argmin([np.median(t) for t in times]))]
+        res = {"workload": "evaluation only from a stored FP64 fit of the n = 1e7 curve (seed 1), M = 1e7 "
+                           "queries: the uniform grid (sorted) and seeded uniform positions (unsorted), "
+                           "bisection bracketing", **out}
+        return res, (pick, xq.cpu().numpy()[pick], samples)
+
+    def n_schedule(self, draws=256, seed=5):
+        """The paper's schedule of curve sizes: n = round((r (sqrt(1048576) - sqrt(4)) + sqrt(4))^2)
+        for r on an even grid of 524,288 points in [0, 1], shuffled (section "Curve
+        Interpolation", benchmark steps 2-4); here a seeded sample of `draws` entries of it.  Per
+        draw: a new benchmark curve (device generator), then the fused FP64 fit + evaluation
+        (M = n) and the three evaluation forms from the stored fit, in a shuffled order, each
+        timed with CUDA events.  Reported as distributions of ns per point (the paper's point
+        that no single central value describes such timings), overall and by size."""
+        torch, spl = self.torch, self.spl
+        rng = np.random.default_rng(seed)
+        r = np.linspace(0.0, 1.0, 524288)
+        sizes = np.rint((r * (np.sqrt(1048576.0) - np.sqrt(4.0)) + np.sqrt(4.0)) ** 2).astype(np.int64)
+        rng.shuffle(sizes)
+        sizes = sizes[:draws]
+        nmax = int(sizes.max())
+        fused = self.ctx.plan(nmax, spl.PREC_F64)
+        evals = [self.ctx.plan(nmax, spl.PREC_F64, eval_variant=v) for v in range(3)]
+        X = torch.empty(nmax, dtype=torch.float64, device=self.dev)
+        Y = torch.empty(nmax, dtype=torch.float64, device=self.dev)
+        ypp = torch.empty(nmax, dtype=torch.float64, device=self.dev)
+        yq = torch.empty(nmax, dtype=torch.float64, device=self.dev)
+        names = ["fit+eval (fused)", "eval orig", "eval noinv", "eval vol"]
+        ns = {k: [] for k in names}
+        for i, n in enumerate(sizes):
+            n = int(n)
+            with torch.cuda.stream(self.stream):
+                x, y = spl.generate_curve(seed, n, instance=i, device=self.local, stream=self.stream)
+            X[:n].copy_(x)
+            Y[:n].copy_(y)
+            torch.cuda.synchronize(self.dev)
+            xs, ys = X[:n], Y[:n]
+            for k in rng.permutation(4):
+                if k == 0:
+                    ms = self._timed_submit(fused, n, yq[:n], x=xs, y=ys, ypp_out=ypp[:n])
+                else:
+                    ms = self._timed_submit(evals[k - 1], n, yq[:n], ypp_in=ypp[:n], x=xs, y=ys)
+                ns[names[k]].append(ms * 1e6 / n)
+        sizes_f = sizes.astype(np.float64)
+
+        def dist(v, mask=None):
+            a = np.asarray(v)
+            if mask is not None:
+                a = a[mask]
+            if a.size == 0:
+                return None
+            lo_, hi_ = np.quantile(a, [0.1, 0.9])
+            trimmed = a[(a >= lo_) & (a <= hi_)]
+            return {"count": int(a.size), "min": float(a.min()), "median": float(np.median(a)),
+                    "trimmed_mean_10": float(trimmed.mean()), "mean": float(a.mean()),
+                    "p99": float(np.quantile(a, 0.99)), "std": float(a.std())}
+
+        bins = {"n<1e3": sizes_f < 1e3, "1e3<=n<1e5": (sizes_f >= 1e3) & (sizes_f < 1e5), "n>=1e5": sizes_f >= 1e5}
+        out = {k: {"all": dist(v), **{b: dist(v, msk) for b, msk in bins.items()}} for k, v in ns.items()}
+        return {"workload": "the paper's size schedule n = round((r (1024 - 2) + 2)^2), r on 524,288 even "
+                            "points, shuffled; %d seeded draws (n from %d to %d), one new curve per draw, "
+                            "routines in shuffled order" % (draws, int(sizes.min()), nmax),
+                "unit": "ns per point", "routines": out}
+
 
 def serving(r, pool_count=512, seed=3, lo=1e2, hi=1e6, rate=20000.0, warm_s=1.0, run_s=8.0):
     """Poisson arrivals through the continuous-batching server (persistent device loop,
@@ -473,6 +585,12 @@ def run_ours(args, world, rank, local):
     r = Runner(args, world, rank, local)
     spl = r.spl
     if args.only:
+        if args.only in ("variants", "schedule"):
+            res = r.eval_variants()[0] if args.only == "variants" else r.n_schedule()
+            if rank == 0:
+                print(json.dumps({"profile_run": True, "path": args.only, "result": res}))
+            r.ctx.close()
+            return
         if args.only == "batched":
             res, _ = r.batched(steps=max(args.steps, 1))
         else:
@@ -490,6 +608,8 @@ def run_ours(args, world, rank, local):
     mixed1 = r.time_single(r.plan(spl.PREC_F32_REFINE, 1))
     batched, bdata = r.batched()
     served, sdata = (None, None) if args.no_serving else serving(r)
+    variants, vdata = r.eval_variants()
+    schedule = r.n_schedule()
     if rank != 0:
         r.ctx.close()
         return
@@ -515,6 +635,8 @@ def run_ours(args, world, rank, local):
                                                 "residual (two launches)", TOL["mixed"], "f32+df"),
         "batched": batched,
         "serving": served,
+        "newint_variants": variants,
+        "n_schedule": schedule,
     }
     others["mixed_f32"]["roofline"] = {"bound": "hbm", "traffic": profiled_traffic("mixed"),
                                        "achieved": others["mixed_f32"]["gb_per_s"], "peak": hbm, "unit": "GB/s",
@@ -522,12 +644,13 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu, errs = cpu_baseline_and_errors(r, main, mixed0, mixed1, bdata, sdata)
+        cpu, errs = cpu_baseline_and_errors(r, main, mixed0, mixed1, bdata, sdata, vdata)
         if served is not None:
             others["serving"]["error_vs_oracle"] = errs["serving"]
         others["mixed_f32"]["error_vs_oracle"] = errs["mixed0"]
         others["mixed_f32_refine1"]["error_vs_oracle"] = errs["mixed1"]
         others["batched"]["error_vs_oracle"] = errs["batched"]
+        others["newint_variants"]["error_vs_oracle"] = errs["variants"]
         main_err = errs["f64"]
     else:
         main_err = None
@@ -560,7 +683,7 @@ def run_ours(args, world, rank, local):
     r.ctx.close()
 
 
-def cpu_baseline_and_errors(r, main, mixed0, mixed1, bdata, sdata):
+def cpu_baseline_and_errors(r, main, mixed0, mixed1, bdata, sdata, vdata=None):
     """The FP64 oracle, as it stands, single-threaded on the host cores: its rate on the main
     workload (repeated for ~10 s) and the error of every GPU result against its outputs."""
     import oracle
@@ -598,6 +721,25 @@ def cpu_baseline_and_errors(r, main, mixed0, mixed1, bdata, sdata):
         e = error_pair(xi, yi, rf, Pc[o:o + nn], Qc[o:o + nn])
         worst = [max(worst[0], e["ypp"]), max(worst[1], e["yq"])]
     out["batched"] = {"ypp": worst[0], "yq": worst[1], "sample": "64 of 4096 instances"}
+    if vdata is not None:
+        # evaluation forms: brackets bit-exact and values within the FP64 tolerance on a sample,
+        # against the oracle's bisection and its interpolation form with the oracle's y''
+        pick, xq_pick, samples = vdata
+        grid_q = oracle.grid(x, n)[pick]
+        ve = {}
+        for (label, name), (yq_s, jq_s) in samples.items():
+            q = grid_q if label == "sorted" else xq_pick
+            jref = oracle.bracket_any(x, q)
+            yref = oracle.evaluate(x, y, ref["ypp"], q, jref)
+            j64 = jq_s.astype(np.int64)
+            same = bool(np.array_equal(j64, jref))
+            h = x[jref + 1] - x[jref]
+            curv = h * h * np.maximum(np.abs(ref["ypp"][jref]), np.abs(ref["ypp"][jref + 1])) / 6.0
+            scale = np.maximum.reduce([np.abs(y[jref]), np.abs(y[jref + 1]), np.abs(yref), curv])
+            ve["%s/%s" % (label, name)] = {"brackets_bit_exact": same,
+                                            "yq": float(np.max(np.abs(yq_s - yref) / scale))}
+        ve["sample"] = "%d of the 1e7 queries per variant and ordering" % len(pick)
+        out["variants"] = ve
     if sdata is None:
         return cpu, out
     sizes_s, seed_s, base_s, sample = sdata
