@@ -249,7 +249,15 @@ spl_status spl_generate_curve(uint64_t seed, uint64_t instance, uint64_t n, doub
  *   tile_rows        knots per tile (0 = 256), >= 16.
  *   budget_bytes     HBM budget for the footprints of resident requests.
  *   max_tiles        tile-map capacity (0 = max(2^20, 64 max_inflight)).
- *   idle_timeout_ms  0 = 200. */
+ *   idle_timeout_ms  0 = 200.
+ *   deadline_ms      longest run of one launch of the loop (0 = 30,000); its worker warps give
+ *                    up waiting for work one second after it.  A worker that gives up raises
+ *                    the loop's error flag: the host then completes every request resident on
+ *                    the device with SPL_ERR_TIMEOUT, drops their tiles and relaunches for the
+ *                    rest, so the context stays usable.
+ *   fault_flags      failure-detection tests only (0 otherwise): bit 0 makes the scheduler warp
+ *                    leave at once without publishing any work or the stop word, so that the
+ *                    workers' bounded waits run out. */
 typedef struct spl_server spl_server;
 typedef struct spl_serve_desc {
   uint32_t max_inflight;
@@ -257,6 +265,8 @@ typedef struct spl_serve_desc {
   uint64_t budget_bytes;
   uint64_t max_tiles;
   uint32_t idle_timeout_ms;
+  uint32_t deadline_ms;
+  uint32_t fault_flags;
   uint32_t reserved;
 } spl_serve_desc;
 

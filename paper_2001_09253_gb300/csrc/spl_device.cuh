@@ -55,6 +55,7 @@ struct ServeArgs {
   volatile unsigned *h_alive;
   volatile unsigned *h_done;                             // per slot: status, seq
   unsigned long long idle_ns, deadline_ns;
+  unsigned fault_flags;                                  // tests: bit 0, the scheduler leaves at once
 };
 
 // Natural end condition: section "Start and End Derivatives" (slope > 0.99e30).

@@ -462,6 +462,7 @@ __global__ void __launch_bounds__(kThreadsM, 1) serve_kernel(ServeArgs a) {
   volatile unsigned long long *published = a.published;
   volatile unsigned *stop = a.stop;
 
+  if (scheduler && (a.fault_flags & 1u)) return;  // failure-detection tests: no work is published
   if (scheduler) {
     unsigned long long consumed = *a.consumed;
     unsigned long long last_work = t_start;

@@ -97,16 +97,56 @@ spl_status relaunch(spl_server *s) {
   return SPL_OK;
 }
 
-bool loop_running(spl_server *s) {
+// The loop has exited: if a worker gave up waiting (error flag), every request still resident
+// on the device and not completed completes with SPL_ERR_TIMEOUT, and the device counters are
+// moved past the dropped tiles and ring entries so that the next launch starts clean.
+spl_status after_exit(spl_server *s) {
+  unsigned err = 0;
+  if (cudaMemcpy(&err, s->args.err, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return SPL_ERR_CUDA;
+  if (!err) return SPL_OK;
+  const double t = now_s();
+  std::atomic_thread_fence(std::memory_order_acquire);
+  for (size_t ri = 0; ri < s->resident.size();) {
+    const unsigned slot = s->resident[ri];
+    Req &r = s->reqs[s->slot_ticket[slot]];
+    if (s->h_done[2 * slot + 1] == r.seq) {  // finished before the failure: harvested as usual
+      ++ri;
+      continue;
+    }
+    r.status = SPL_ERR_TIMEOUT;
+    r.state = 2;
+    r.t_done = t;
+    s->slot_ticket[slot] = 0;
+    s->free_slots.push_back(slot);
+    s->bytes_inflight -= r.bytes;
+    auto it = s->live_first.find(r.first_tile);
+    if (it != s->live_first.end() && --it->second == 0) s->live_first.erase(it);
+    s->resident[ri] = s->resident.back();
+    s->resident.pop_back();
+  }
+  const unsigned long long ctr[3] = {s->next_tile, s->next_tile, s->tail};  // published, claimed, consumed
+  cudaError_t e = cudaMemcpy(s->args.published, ctr, sizeof(ctr), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(s->args.err, 0, sizeof(unsigned));
+  *s->h_consumed = s->tail;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  return e == cudaSuccess ? SPL_OK : SPL_ERR_CUDA;
+}
+
+bool loop_running(spl_server *s, spl_status *st) {
+  *st = SPL_OK;
   if (!s->launched) return false;
   cudaError_t q = cudaEventQuery(s->ev_exit);
   if (q == cudaErrorNotReady) return true;
   s->launched = false;
+  *st = after_exit(s);
   return false;
 }
 
 // Completions, then admissions, then make sure the device loop runs if anything is resident.
 spl_status pump(spl_server *s) {
+  spl_status xs = SPL_OK;
+  const bool running = loop_running(s, &xs);
+  if (xs != SPL_OK) return xs;
   const double t = now_s();
   for (size_t ri = 0; ri < s->resident.size();) {
     const unsigned slot = s->resident[ri];
@@ -161,7 +201,7 @@ spl_status pump(spl_server *s) {
     std::atomic_thread_fence(std::memory_order_seq_cst);
     admitted = true;
   }
-  if ((admitted || !s->resident.empty()) && !loop_running(s)) return relaunch(s);
+  if ((admitted || !s->resident.empty()) && !running) return relaunch(s);
   return SPL_OK;
 }
 
@@ -222,7 +262,9 @@ spl_status spl_serve_create(spl_ctx *c, const spl_serve_desc *d, spl_server **ou
   a.tile_cap = tile_cap;
   a.rcap = rcap;
   a.idle_ns = (unsigned long long)s->d.idle_timeout_ms * 1000000ull;
-  a.deadline_ns = 30ull * 1000000000ull;  // a single launch never runs longer; the host relaunches
+  // a single launch never runs longer than the deadline; the host relaunches
+  a.deadline_ns = (unsigned long long)(s->d.deadline_ms ? s->d.deadline_ms : 30000u) * 1000000ull;
+  a.fault_flags = s->d.fault_flags;
   // mapped host block: tail, stop, consumed, alive, done words, ring
   const uint64_t hbytes = 256 + up256(8ull * S) + sizeof(ServeEntry) * rcap;
   if (cudaHostAlloc(&s->hblock, hbytes, cudaHostAllocMapped) != cudaSuccess) {

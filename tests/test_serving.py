@@ -1,6 +1,7 @@
 """GPU tests of the continuous-batching server (spl_serve_*): results equal a single-instance
 submission bit for bit, alone and in the mix; admission under a small budget; relaunch of the
-device loop after it went idle; per-request error isolation; trace replay."""
+device loop after it went idle; per-request error isolation; trace replay; failure detection
+through the loop's bounded waits."""
 import time
 
 import numpy as np
@@ -129,6 +130,36 @@ def test_loop_relaunches_after_idle(ctx):
         assert np.array_equal(o[1].cpu().numpy(), _reference(ctx, p)[1])
     assert srv.stats()["loop_launches"] >= 2
     srv.close()
+
+
+def test_worker_wait_runs_out_and_the_context_stays_usable(ctx):
+    """Failure detection without a GPU fault: the scheduler warp is told to leave at once
+    (fault_flags bit 0), so nothing publishes work and the workers' bounded waits run out one
+    second after the loop's 100 ms deadline; the host reads the loop's error flag and completes
+    the request with SPL_ERR_TIMEOUT.  The context stays usable: a normal server on it then
+    finishes its requests with the expected results."""
+    pool = _pool(3, 8, lo=1e3, hi=1e4)
+    bad = spl.Server(ctx, max_inflight=4, tile_rows=TILE, idle_timeout_ms=20, deadline_ms=100, fault_flags=1)
+    p = pool[0]
+    o = _outputs(p)
+    t = bad.submit(p["xt"], p["yt"], p["bc"][0], p["bc"][1], p["m"], o[0], o[1])
+    s, _ = bad.poll(t)
+    assert s == spl.PENDING
+    t0 = time.time()
+    while s == spl.PENDING and time.time() - t0 < 20.0:
+        time.sleep(0.05)
+        s, _ = bad.poll(t)
+    assert s == spl.ERR_TIMEOUT  # completed by the failure path, not by a host-side wait limit
+    assert 0.5 < time.time() - t0 < 10.0
+    bad.close()
+    good = spl.Server(ctx, max_inflight=4, tile_rows=TILE, idle_timeout_ms=20)
+    for p in pool:
+        o = _outputs(p)
+        s, _ = good.wait(good.submit(p["xt"], p["yt"], p["bc"][0], p["bc"][1], p["m"], o[0], o[1]))
+        assert s == spl.OK
+        ref = _reference(ctx, p)
+        assert np.array_equal(o[1].cpu().numpy(), ref[1]) and np.array_equal(o[0].cpu().numpy(), ref[0])
+    good.close()
 
 
 def test_bad_request_is_isolated(ctx):
