@@ -578,7 +578,8 @@ def serving(r, pool_count=512, seed=3, lo=1e2, hi=1e6, rate=20000.0, warm_s=1.0,
 
 def short_line(r, which, res):
     print(json.dumps({"profile_run": True, "path": which, "n": r.n, "steps": r.K,
-                      "ms_per_step": res["ms_per_step"], "gpu_launches": res.get("launches", res.get("gpu_launches"))}))
+                      "ms_per_step": res["ms_per_step"], "gpu_launches": res.get("launches", res.get("gpu_launches")),
+                      "e2e": res.get("e2e")}))
 
 
 def run_ours(args, world, rank, local):
@@ -595,7 +596,10 @@ def run_ours(args, world, rank, local):
             res, _ = r.batched(steps=max(args.steps, 1))
         else:
             prec = spl.PREC_F64 if args.only == "f64" else spl.PREC_F32_REFINE
-            res = r.time_single(r.plan(prec, 1 if args.only == "mixed-refine" else 0))
+            plan = r.plan(prec, 1 if args.only == "mixed-refine" else 0)
+            res = r.time_single(plan)
+            if args.only == "f64" and not args.no_e2e:
+                res["e2e"] = r.time_e2e(plan)
         if rank == 0:
             short_line(r, args.only, res)
         r.ctx.close()

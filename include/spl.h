@@ -28,9 +28,12 @@
  *     addresses (pinned memory gives asynchronous copies).
  *   - The caller owns every input and output array; the library owns its
  *     scratch, which it carves from the arena given at creation.
- *   - One context orders all of its GPU work on one CUDA stream.  Calls on a
- *     context are serialised by an internal lock; distinct contexts are
- *     independent.
+ *   - One context orders its GPU work on one CUDA stream; requests with host
+ *     (SPL_MEM_HOST) arrays additionally copy their inputs and outputs on two
+ *     copy streams the context owns, ordered against the kernels by events, so
+ *     that the copies of one request overlap the kernels of its neighbours.
+ *     Calls on a context are serialised by an internal lock; distinct contexts
+ *     are independent.
  *   - Nothing falls back to the CPU: without the CUDA device the calls fail
  *     with SPL_ERR_CUDA.
  */

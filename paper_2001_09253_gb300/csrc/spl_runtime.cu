@@ -109,6 +109,7 @@ struct Ticket {
 
 struct Job {
   cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_kernel = nullptr;  // host-memory requests: copies pipelined
   std::vector<Block> dev_blocks;   // arena blocks, released once the GPU is done
   Block pin_block;                 // pinned staging block
   int count = 0;
@@ -122,6 +123,7 @@ struct Job {
 struct spl_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t s_in = nullptr, s_out = nullptr;  // copy streams of host-memory requests (lazy)
   char *arena = nullptr;
   bool own_arena = false;
   int max_slots = 1;
@@ -413,33 +415,50 @@ cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, 
 }
 
 // Enqueue the launch described by lp: statuses cleared, descriptors uploaded, host inputs
-// copied in, the fused kernel, outputs and statuses copied back.
+// copied in, the fused kernel, outputs and statuses copied back.  Device-memory requests run
+// everything on the context's stream.  Host-memory requests put their input copies on the
+// context's input-copy stream and their output copies (and the status words) on its
+// output-copy stream, ordered against the kernels by events, so that the copies of one request
+// overlap the kernels of its neighbours; the job is then complete when its output copies are.
 cudaError_t enqueue(spl_ctx *c, const LaunchPlan &lp, char *pin_base, unsigned *h_status, uint64_t d_insts_off,
-                    uint64_t d_status_off, uint64_t d_ring_off, cudaStream_t st, int *launches) {
+                    uint64_t d_status_off, uint64_t d_ring_off, cudaStream_t st, int *launches, Job *job) {
   const int count = (int)lp.insts.size();
+  const bool piped = !lp.hio.empty() && job && c->s_in && c->s_out;
+  cudaStream_t s_in = piped ? c->s_in : st, s_out = piped ? c->s_out : st;
   std::memcpy(pin_base, lp.insts.data(), sizeof(Inst) * count);
-  cudaError_t e = cudaMemsetAsync(c->arena + d_status_off, 0, status_block_bytes(count), st);
+  // statuses and descriptors go with the inputs: on the input stream when the copies are
+  // pipelined, so that the kernel waits on one event and no small copy of the kernel's stream
+  // queues behind a neighbour's large input copy on the copy engine
+  cudaError_t e = cudaMemsetAsync(c->arena + d_status_off, 0, status_block_bytes(count), s_in);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->arena + d_insts_off, pin_base, sizeof(Inst) * count, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(c->arena + d_insts_off, pin_base, sizeof(Inst) * count, cudaMemcpyHostToDevice, s_in);
   for (const auto &h : lp.hio) {
     if (e != cudaSuccess) break;
-    e = cudaMemcpyAsync(c->arena + h.off_x, h.hx, 8 * h.n, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c->arena + h.off_y, h.hy, 8 * h.n, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && h.hxq) e = cudaMemcpyAsync(c->arena + h.off_xq, h.hxq, 8 * h.m, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(c->arena + h.off_x, h.hx, 8 * h.n, cudaMemcpyHostToDevice, s_in);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->arena + h.off_y, h.hy, 8 * h.n, cudaMemcpyHostToDevice, s_in);
+    if (e == cudaSuccess && h.hxq) e = cudaMemcpyAsync(c->arena + h.off_xq, h.hxq, 8 * h.m, cudaMemcpyHostToDevice, s_in);
     if (e == cudaSuccess && h.hyppin)
-      e = cudaMemcpyAsync(c->arena + h.off_yppin, h.hyppin, 8 * h.n, cudaMemcpyHostToDevice, st);
+      e = cudaMemcpyAsync(c->arena + h.off_yppin, h.hyppin, 8 * h.n, cudaMemcpyHostToDevice, s_in);
+  }
+  if (piped) {
+    if (e == cudaSuccess) e = cudaEventRecord(job->ev_in, s_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, job->ev_in, 0);
   }
   if (e == cudaSuccess) e = launch_path(c, lp, d_insts_off, d_ring_off, d_status_off, st, launches);
+  if (piped) {
+    if (e == cudaSuccess) e = cudaEventRecord(job->ev_kernel, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, job->ev_kernel, 0);
+  }
   for (const auto &h : lp.hio) {
     if (e != cudaSuccess) break;
-    if (h.hypp) e = cudaMemcpyAsync(h.hypp, c->arena + h.off_ypp, 8 * h.n, cudaMemcpyDeviceToHost, st);
+    if (h.hypp) e = cudaMemcpyAsync(h.hypp, c->arena + h.off_ypp, 8 * h.n, cudaMemcpyDeviceToHost, s_out);
     if (e == cudaSuccess && h.m)
-      e = cudaMemcpyAsync(h.hyq, c->arena + h.off_yq, 8 * h.m, cudaMemcpyDeviceToHost, st);
+      e = cudaMemcpyAsync(h.hyq, c->arena + h.off_yq, 8 * h.m, cudaMemcpyDeviceToHost, s_out);
     if (e == cudaSuccess && h.hjq && h.m)
-      e = cudaMemcpyAsync(h.hjq, c->arena + h.off_jq, 4 * h.m, cudaMemcpyDeviceToHost, st);
+      e = cudaMemcpyAsync(h.hjq, c->arena + h.off_jq, 4 * h.m, cudaMemcpyDeviceToHost, s_out);
   }
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h_status, c->arena + d_status_off, 4ull * count, cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(h_status, c->arena + d_status_off, 4ull * count, cudaMemcpyDeviceToHost, s_out);
   return e;
 }
 
@@ -456,6 +475,8 @@ void free_job(spl_ctx *c, Job *j) {
   c->slots_used -= j->count;
   if (j->ev_start) cudaEventDestroy(j->ev_start);
   if (j->ev_done) cudaEventDestroy(j->ev_done);
+  if (j->ev_in) cudaEventDestroy(j->ev_in);
+  if (j->ev_kernel) cudaEventDestroy(j->ev_kernel);
   delete j;
 }
 
@@ -531,6 +552,8 @@ void spl_destroy(spl_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  if (c->s_in) cudaStreamSynchronize(c->s_in);
+  if (c->s_out) cudaStreamSynchronize(c->s_out);
   std::vector<Job *> jobs;
   for (auto &kv : c->tickets) jobs.push_back(kv.second.job);
   std::sort(jobs.begin(), jobs.end());
@@ -541,6 +564,8 @@ void spl_destroy(spl_ctx *c) {
   }
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->own_arena) cudaFree(c->arena);
+  if (c->s_in) cudaStreamDestroy(c->s_in);
+  if (c->s_out) cudaStreamDestroy(c->s_out);
   delete c;
 }
 
@@ -603,12 +628,20 @@ spl_status spl_submit_batch(spl_ctx *c, spl_plan *p, const spl_request *reqs, ui
   j->h_status = reinterpret_cast<unsigned *>(pin_base + round_up(sizeof(Inst) * count, 64));
   cudaError_t e = cudaEventCreate(&j->ev_start);
   if (e == cudaSuccess) e = cudaEventCreate(&j->ev_done);
-  if (e == cudaSuccess) e = cudaEventRecord(j->ev_start, c->stream);
+  const bool host_io = !lp.hio.empty();
+  if (host_io && e == cudaSuccess && !c->s_in) e = cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking);
+  if (host_io && e == cudaSuccess && !c->s_out) e = cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking);
+  if (host_io && e == cudaSuccess) e = cudaEventCreateWithFlags(&j->ev_in, cudaEventDisableTiming);
+  if (host_io && e == cudaSuccess) e = cudaEventCreateWithFlags(&j->ev_kernel, cudaEventDisableTiming);
+  cudaStream_t s_first = host_io ? c->s_in : c->stream, s_last = host_io ? c->s_out : c->stream;
+  if (e == cudaSuccess) e = cudaEventRecord(j->ev_start, s_first);
   int launches = 0;
-  if (e == cudaSuccess) e = enqueue(c, lp, pin_base, j->h_status, oi, os, orr, c->stream, &launches);
-  if (e == cudaSuccess) e = cudaEventRecord(j->ev_done, c->stream);
+  if (e == cudaSuccess) e = enqueue(c, lp, pin_base, j->h_status, oi, os, orr, c->stream, &launches, j);
+  if (e == cudaSuccess) e = cudaEventRecord(j->ev_done, s_last);
   if (e != cudaSuccess) {
     cudaStreamSynchronize(c->stream);
+    if (c->s_in) cudaStreamSynchronize(c->s_in);
+    if (c->s_out) cudaStreamSynchronize(c->s_out);
     free_job(c, j);
     return SPL_ERR_CUDA;
   }
