@@ -194,7 +194,8 @@ typedef struct spl_stats {
 const char *spl_status_str(int32_t status);
 
 spl_status spl_create(spl_ctx **out, const spl_ctx_desc *desc);
-void spl_destroy(spl_ctx *ctx);  /* waits for the context's work; NULL is a no-op */
+void spl_destroy(spl_ctx *ctx);  /* waits for the context's work; NULL is a no-op.  Destroy the
+                                    context's servers first: they use its arena. */
 
 spl_status spl_plan_create(spl_ctx *ctx, const spl_plan_desc *desc, spl_plan **out);
 void spl_plan_destroy(spl_plan *plan);

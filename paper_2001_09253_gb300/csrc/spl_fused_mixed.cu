@@ -56,8 +56,14 @@ __device__ __noinline__ F2 sub_f64_f2(double b, double a) {
   return F2{hi, (float)(d - (double)hi)};
 }
 
-// neighbouring operands (same binade and a small difference almost always)
+// neighbouring operands (same binade and a small difference almost always).  For two finite
+// numbers with the same sign and exponent field the FP64 subtraction is exact (Sterbenz) and
+// the conversion rounds the exact difference once, exactly as the integer routes do: one FP64
+// subtraction and one conversion instead of ~60 integer instructions; other pairs take the
+// integer routes.
 __device__ __forceinline__ float dif32_near(double b, double a) {
+  const unsigned hb = (unsigned)(bits64(b) >> 32), ha = (unsigned)(bits64(a) >> 32);
+  if (((hb ^ ha) >> 20) == 0u && ((hb >> 20) & 0x7FFu) != 0x7FFu) return (float)(b - a);
   float v;
   if (diff_small_f32(b, a, &v)) return v;
   if (diff_same_f32(b, a, &v)) return v;
@@ -120,6 +126,10 @@ __device__ __forceinline__ float newint32(float xa, float bx, float yj, float yj
 
 __device__ __forceinline__ void prefetch_l2m(const void *p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+__device__ __forceinline__ void prefetch_l1m(const void *p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
 // Queries of intervals [a, b) (local rows ta..tb of the tile), with y'' of the segment in
@@ -600,6 +610,308 @@ cudaError_t launch_fused_mixed(const Inst *d_insts, int ninst, long long total_t
 cudaError_t launch_refine_mixed(const Inst *d_insts, int ninst, long long total_tiles, long long threads,
                                 unsigned long long *counter, cudaStream_t stream) {
   return launch_mode<2>(d_insts, ninst, total_tiles, threads, counter, stream);
+}
+
+// ---------------------------------------------------------------------------------------
+// Tiled binary32 fit + evaluation (no refinement): the decomposition of the plain FP64 kernel
+// (spl_fused_f64.cu) with the binary32 arithmetic above.  One thread per tile, a warp's 32
+// tiles grouped (instances of >= 32 tiles):
+//   * only the first lane of a group runs a forward halo (48 rows, (2/3)^48 < 2^-28); its tile
+//     is kLane0ShortT rows shorter;
+//   * the other lanes are chained: the exact c'_{s0-1} from 8 rows of the c' recurrence alone
+//     (error factor <= 1/12 per row), the guess d'_{s0-1} = 0, and the sensitivity M_i of
+//     their d'_i to the true d'_{s0-1}, kept while |M_i| >= 2^-100; a warp scan over the lanes'
+//     affine maps then gives every lane its d'_{s0-1} and the kept rows are corrected;
+//   * the back substitution starts 24 rows past a tile (error x c' < 1/2 per row: 2^-24),
+//     taken from the next lane's forward sweep (the last lane's tile is 24 rows shorter);
+//   * the back substitution is fused with the evaluation, one query per iteration, the rows
+//     walked down as far as the query needs.
+// (c', d') live in per-warp scratch in global memory (binary32, lane-interleaved).
+constexpr int kThreadsT = 512;          // one CTA per SM, four warps per sub-partition
+constexpr int kOvT = 24;                // back-substitution start past a tile
+constexpr int kLane0ShortT = 48;        // the first lane's forward halo
+constexpr int kHaloCT = 8;              // c'-only rows before a chained tile
+constexpr int kMRowsT = 192;            // sensitivities kept per lane: (2/3)^192 < 2^-112
+constexpr float kMStopT = 0x1p-100f;    // far below binary32 resolution: d'_{s0-1} may exceed the
+                                        // tile's values by many orders of magnitude (tiny gaps)
+
+struct ScrT {
+  float *base;  // rows x {c', d'} x 32 lanes
+  float *mb;    // kMRowsT x 32 lanes
+  int lane;
+  __device__ __forceinline__ float &at(long long row, int f) const { return base[(((size_t)row * 2 + f) << 5) + lane]; }
+  __device__ __forceinline__ float &m(int row) const { return mb[(row << 5) + lane]; }
+};
+
+struct RowsT {
+  long long s0, e0;
+  bool succ, chain;
+};
+
+__device__ __forceinline__ RowsT rows_of_t(const Inst &I, long long tile) {
+  const long long n = I.n, L = I.tile_rows;
+  RowsT T;
+  if (I.pad & 1) {
+    const long long lane = tile & 31;
+    const long long g0 = (tile >> 5) * (32 * L - kOvT - kLane0ShortT);
+    T.s0 = lane == 0 ? g0 : g0 + lane * L - kLane0ShortT;
+    const long long len = lane == 0 ? L - kLane0ShortT : (lane == 31 ? L - kOvT : L);
+    T.e0 = min(T.s0 + len, n);
+    T.succ = lane < 31 && T.e0 < n;
+    T.chain = lane > 0;
+  } else {
+    T.s0 = tile * L;
+    T.e0 = min(T.s0 + L, n);
+    T.succ = T.chain = false;
+  }
+  return T;
+}
+
+struct FwdOutT {
+  long long rlast;
+  float A, B;
+  int K;
+  unsigned bad;
+};
+
+__device__ FwdOutT tile_forward_t(const Inst &I, const RowsT &T, const ScrT &S) {
+  const long long n = I.n;
+  const double *__restrict__ x = I.x;
+  const double *__restrict__ y = I.y;
+  const long long s0 = T.s0, e0 = T.e0;
+  const bool nat0 = is_natural(I.yp1), nat1 = is_natural(I.ypn);
+  unsigned bad = 0;
+  long long r;
+  float cp_start = 0.0f;
+  if (T.chain) {
+    const long long i0 = max(s0 - 1 - kHaloCT, 0LL);
+    float c = (i0 == 0 && !nat0) ? 0.5f : 0.0f;  // exact at row 0, a guess elsewhere
+    double xb = x[i0 + 1];
+    float hp = dif32_near(xb, x[i0]);
+    for (long long i = i0 + 1; i <= s0 - 1; ++i) {
+      const double xc = x[i + 1];
+      const float hi = dif32_near(xc, xb);
+      c = hi * rcp32(2.0f * (hp + hi) - hp * c);
+      hp = hi;
+      xb = xc;
+    }
+    cp_start = c;
+    r = s0 - 1;
+  } else {
+    r = max(s0 - kLane0ShortT, 0LL);
+  }
+  FwdM F;
+  {
+    const double x0 = x[r], x1 = x[r + 1], y0 = y[r], y1 = y[r + 1];
+    F.xa = F.ya = F.xb = F.yb = 0.0;
+    if (r + 2 < n) { F.xa = x[r + 2]; F.ya = y[r + 2]; }
+    if (r + 3 < n) { F.xb = x[r + 3]; F.yb = y[r + 3]; }
+    const float h = dif32_near(x1, x0), ih = rcp32(h), sl = quot32(dy32(y1, y0), h, ih);
+    F.xn = x1; F.yn = y1; F.h = h; F.s = sl;
+    if (T.chain) {
+      F.cp = cp_start;
+      F.dp = 0.0f;
+    } else if (r == 0 && !nat0) {
+      F.cp = 0.5f;
+      F.dp = 3.0f * (sl - to_f32(I.yp1)) * ih;
+    } else {
+      F.cp = 0.0f;
+      F.dp = 0.0f;
+    }
+    if (r >= s0) {
+      S.at(0, 0) = F.cp; S.at(0, 1) = F.dp;
+      bad |= row_check(x0, y0, true, x1);
+    }
+  }
+  FwdOutT out;
+  out.A = out.B = 0.0f;
+  float M = 1.0f;
+  int K = 0;
+  bool track = T.chain;
+  const long long rlast = T.succ ? e0 - 1 : min(e0 + kOvT, n) - 1;
+  while (r < rlast) {
+    const long long j = r + 1;
+    const bool owned = (j >= s0 && j < e0);
+    const float a = F.h;
+    float cpj, dpj, iden;
+    if (j <= n - 2) {
+      const double x2 = F.xa, y2 = F.ya;
+      F.xa = F.xb; F.ya = F.yb;
+      if (j + 3 < n) { F.xb = x[j + 3]; F.yb = y[j + 3]; }
+      if (j + 3 + kPrefetchM < n) { prefetch_l2m(x + j + 3 + kPrefetchM); prefetch_l2m(y + j + 3 + kPrefetchM); }
+      if (owned) bad |= row_check(F.xn, F.yn, true, x2);
+      const float hj = dif32_near(x2, F.xn);
+      const float ihj = rcp32(hj);
+      const float sj = quot32(dy32(y2, F.yn), hj, ihj);
+      iden = rcp32(2.0f * (F.h + hj) - F.h * F.cp);
+      cpj = hj * iden;
+      dpj = (6.0f * (sj - F.s) - F.h * F.dp) * iden;
+      F.xn = x2; F.yn = y2; F.h = hj; F.s = sj;
+    } else {
+      if (owned) bad |= row_check(F.xn, F.yn, false, 0.0);
+      cpj = 0.0f;
+      iden = rcp32(2.0f * F.h - F.h * F.cp);
+      dpj = nat1 ? 0.0f : (6.0f * (to_f32(I.ypn) - F.s) - F.h * F.dp) * iden;
+    }
+    F.cp = cpj; F.dp = dpj;
+    r = j;
+    if (j >= s0) { S.at(j - s0, 0) = cpj; S.at(j - s0, 1) = dpj; }
+    if (track) {  // d'_j = (r_j - a_j d'_{j-1}) / den_j: the sensitivity picks up -a_j / den_j
+      M *= (j == n - 1 && nat1) ? 0.0f : -a * iden;
+      S.m(K++) = M;
+      if (!(fabsf(M) >= kMStopT) || K == kMRowsT) track = false;
+    }
+    if (j == e0 - 1) {
+      out.A = dpj;
+      out.B = track ? M : 0.0f;
+    }
+  }
+  out.rlast = rlast;
+  out.K = K;
+  out.bad = bad;
+  return out;
+}
+
+__device__ void tile_bwd_eval_t(const Inst &I, const RowsT &T, long long rlast, const ScrT &S) {
+  const long long n = I.n, m = I.m;
+  const double *__restrict__ x = I.x;
+  const double *__restrict__ y = I.y;
+  const long long s0 = T.s0, e0 = T.e0;
+  const long long te = e0 - 1 - s0;
+  float Y;
+  long long t;
+  if (T.succ) {
+    const ScrT Sn{S.base, S.mb, S.lane + 1};
+    long long u = min(e0 + kOvT, n) - 1 - e0;
+    Y = Sn.at(u, 1);
+    for (--u; u >= 0; --u) Y = Sn.at(u, 1) - Sn.at(u, 0) * Y;
+    t = te;
+  } else {
+    t = rlast - s0;
+    Y = S.at(t, 1);
+    for (--t; t > te; --t) Y = S.at(t, 1) - S.at(t, 0) * Y;
+  }
+  if (t == te - 1 && I.ypp) I.ypp[n - 1] = to_f64(Y);
+  const bool evaluate = (m > 0 && s0 <= n - 2);
+  const Grid G = make_grid(x, n, m);
+  const long long klo = evaluate ? first_query(G, x, s0) : 0;
+  long long k = evaluate ? ((e0 <= n - 2) ? first_query(G, x, e0) - 1 : m - 1) : -1;
+  if (t < 0) return;
+  // current row t: y''_t, y''_{t+1}, knots and values, and the interval's binary32 width,
+  // reciprocal and values; the next row down is loaded one step ahead
+  float Yt1 = Y;
+  double xt1 = x[s0 + t + 1], xt = x[s0 + t];
+  double ytd1 = y[s0 + t + 1], ytd = y[s0 + t];
+  float Yt = S.at(t, 1) - S.at(t, 0) * Yt1;
+  if (I.ypp) I.ypp[s0 + t] = to_f64(Yt);
+  float fy1 = to_f32(ytd1), fy0 = to_f32(ytd);
+  float ba = dif32_near(xt1, xt), iba = rcp32(ba);
+  float c_n = 0.0f, d_n = 0.0f;
+  double x_n = 0.0, y_n = 0.0;
+  auto load_next = [&](long long row) {
+    if (row >= 0) {
+      if (row >= 8) {
+        prefetch_l1m(&S.at(row - 8, 0));
+        prefetch_l1m(x + s0 + row - 8); prefetch_l1m(y + s0 + row - 8);
+      }
+      c_n = S.at(row, 0); d_n = S.at(row, 1);
+      x_n = x[s0 + row]; y_n = y[s0 + row];
+    }
+  };
+  load_next(t - 1);
+  auto step_down = [&]() {
+    --t;
+    Yt1 = Yt; xt1 = xt; fy1 = fy0;
+    xt = x_n; ytd = y_n;
+    Yt = d_n - c_n * Yt1;
+    if (I.ypp) I.ypp[s0 + t] = to_f64(Yt);
+    load_next(t - 1);
+    fy0 = to_f32(ytd);
+    ba = dif32_near(xt1, xt);
+    iba = rcp32(ba);
+  };
+  long long kxt = dkey(xt);
+  double q = k >= klo ? G.at(k) : 0.0;  // the next query is formed one iteration ahead
+  for (; k >= klo; --k) {
+    const long long kq = dkey(q);
+    const double qn = k > klo ? G.at(k - 1) : 0.0;
+    while (t > 0 && kq <= kxt) {
+      step_down();
+      kxt = dkey(xt);
+    }
+    const float xa = dif32_near(q, xt);
+    I.yq[k] = to_f64(newint32(xa, ba - xa, fy0, fy1, Yt, Yt1, ba, iba));
+    if (I.jq) I.jq[k] = (int32_t)(s0 + t);
+    q = qn;
+  }
+  while (t > 0) step_down();
+}
+
+__device__ __forceinline__ void tile_correct_t(const FwdOutT &o, float delta, const ScrT &S) {
+  for (int k = 0; k < o.K; ++k) S.at(k, 1) = fmaf(S.m(k), delta, S.at(k, 1));
+}
+
+__global__ void __launch_bounds__(kThreadsT, 1)
+    mixed_tiled_kernel(const Inst *__restrict__ insts, int ninst, long long total_tiles,
+                       unsigned long long *__restrict__ counter, float *__restrict__ scratch, long long rows_cap) {
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  float *wbase = scratch + (size_t)warp * (rows_cap * 2 + kMRowsT) * 32;
+  const ScrT S{wbase, wbase + (size_t)rows_cap * 2 * 32, lane};
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(counter, 32ull);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((long long)base >= total_tiles) break;
+    const long long t = (long long)base + lane;
+    Inst I;
+    RowsT T;
+    T.s0 = T.e0 = 0;
+    T.succ = T.chain = false;
+    FwdOutT o;
+    o.rlast = -1;
+    o.A = o.B = 0.0f;
+    o.K = 0;
+    o.bad = 0;
+    if (t < total_tiles) {
+      const int i = find_inst(insts, ninst, t);
+      I = insts[i];
+      T = rows_of_t(I, t - I.tile_begin);
+      if (T.s0 < I.n) o = tile_forward_t(I, T, S);
+    }
+    float sa = o.A, sb = o.B;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const float pa = __shfl_up_sync(0xffffffffu, sa, off), pb = __shfl_up_sync(0xffffffffu, sb, off);
+      if (lane >= off) {
+        sa = fmaf(sb, pa, sa);
+        sb *= pb;
+      }
+    }
+    const float delta = __shfl_up_sync(0xffffffffu, sa, 1);
+    if (o.rlast >= 0 && T.chain) tile_correct_t(o, delta, S);
+    __syncwarp();
+    if (o.rlast >= 0) {
+      tile_bwd_eval_t(I, T, o.rlast, S);
+      if (o.bad) atomicOr(I.status, o.bad);
+    }
+    __syncwarp();
+  }
+}
+
+int tiled_mixed_overhang_rows() { return kOvT; }
+int tiled_mixed_lane0_short_rows() { return kLane0ShortT; }
+
+size_t scratch_bytes_tiled_mixed(long long threads, int tile_rows) {
+  const long long warps = (threads + 31) / 32;
+  return (size_t)warps * (((size_t)tile_rows + kOvT) * 2 + kMRowsT) * 32 * sizeof(float);
+}
+
+cudaError_t launch_tiled_mixed(const Inst *d_insts, int ninst, long long total_tiles, float *scratch, int tile_rows,
+                               long long threads, unsigned long long *counter, cudaStream_t stream) {
+  mixed_tiled_kernel<<<(unsigned)(threads / kThreadsT), kThreadsT, 0, stream>>>(d_insts, ninst, total_tiles, counter,
+                                                                                 scratch, (long long)tile_rows + kOvT);
+  return cudaGetLastError();
 }
 
 }  // namespace spl

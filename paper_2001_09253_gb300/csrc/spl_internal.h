@@ -34,6 +34,14 @@ cudaError_t launch_serve(const ServeArgs &args, int sm_count, cudaStream_t strea
 int serve_tile_threads();
 int mixed_threads_per_sm();  // threads of one mixed-kernel CTA (one CTA per SM)
 
+// Tiled binary32 fit + evaluation without refinement (spl_fused_mixed.cu, mixed_tiled_kernel):
+// grouped tiles as the FP64 kernel's, per-warp scratch of scratch_bytes_tiled_mixed bytes.
+int tiled_mixed_overhang_rows();
+int tiled_mixed_lane0_short_rows();
+size_t scratch_bytes_tiled_mixed(long long threads, int tile_rows);
+cudaError_t launch_tiled_mixed(const Inst *d_insts, int ninst, long long total_tiles, float *scratch, int tile_rows,
+                               long long threads, unsigned long long *counter, cudaStream_t stream);
+
 // Separate evaluation (spl_eval.cu): queries q_begin .. q_begin+mq-1 of each instance, explicit
 // (Inst::xq) or on the uniform grid, with the y'' in Inst::ypp; variant = spl_eval_variant.
 cudaError_t launch_eval(const Inst *d_insts, int ninst, long long total_q, int variant, int sm_count,

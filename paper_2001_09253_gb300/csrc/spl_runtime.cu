@@ -192,14 +192,17 @@ long long threads_for(const spl_ctx *c, int precision, long long total_tiles) {
 // Tile length so that one instance of total_points fills every thread of one wave; never
 // shorter than a few halos.  FP64 tiles come in warp groups of 32L - overhang - lane0_short
 // rows, so L is chosen for the group count to match the warps.
-int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points) {
+int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points, bool tiled_mixed) {
   const long long per_sm = precision == SPL_PREC_F64 ? spl::f64_threads_per_sm() : spl::mixed_threads_per_sm();
   const long long target = (long long)c->sm_count * per_sm;
   long long L = (long long)((total_points + target - 1) / target);
-  if (precision == SPL_PREC_F64) {
+  if (precision == SPL_PREC_F64 || tiled_mixed) {
     const long long warps = std::max<long long>(target / 32, 1);
     const long long per_warp = (long long)((total_points + warps - 1) / warps);
-    L = (per_warp + spl::overhang_rows_f64() + spl::lane0_short_rows_f64() + 31) / 32;
+    const long long extra = precision == SPL_PREC_F64
+                                ? spl::overhang_rows_f64() + spl::lane0_short_rows_f64()
+                                : spl::tiled_mixed_overhang_rows() + spl::tiled_mixed_lane0_short_rows();
+    L = (per_warp + extra + 31) / 32;
   }
   L = std::max<long long>(L, 128);
   L = std::min<long long>(L, 1 << 20);
@@ -222,6 +225,7 @@ struct LaunchPlan {
   long long threads = 0;
   uint64_t ring_bytes = 0;
   bool fit = true;             // run the fit kernel(s)
+  bool tiled_mixed = false;    // binary32 without refinement: the tiled kernel
   bool separate_eval = false;  // evaluate with the separate kernel (explicit queries, stored y'')
   int eval_variant = 0;
   long long total_queries = 0;
@@ -256,18 +260,24 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
                    uint64_t *d_status_off, uint64_t *d_ring_off) {
   uint64_t total_points = 0;
   for (uint32_t i = 0; i < count; ++i) total_points += reqs[i].n;
-  const int L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points);
   lp.precision = p->precision;
   lp.refine_steps = p->precision == SPL_PREC_F64 ? 0 : p->refine_steps;
   lp.fit = reqs[0].ypp_in == nullptr;
   lp.separate_eval = p->query_mode == SPL_QUERY_EXPLICIT || !lp.fit;
+  lp.tiled_mixed = p->precision == SPL_PREC_F32_REFINE && lp.refine_steps == 0;
+  const int L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, lp.tiled_mixed);
   lp.eval_variant = p->eval_variant;
   lp.insts.resize(count);
-  // FP64 instances of 32 tiles or more use the grouped geometry: their tiles start on a warp
-  // boundary, and each warp's 32 tiles cover 32L - overhang - lane0_short rows (the FP64
-  // kernel's lanes take the rows past their tile from the next lane and, but for the first,
-  // their start state from the previous one)
-  const long long ov = p->precision == SPL_PREC_F64 ? spl::overhang_rows_f64() : 0;
+  // Instances of 32 tiles or more of the FP64 and tiled binary32 kernels use the grouped
+  // geometry: their tiles start on a warp boundary, and each warp's 32 tiles cover
+  // 32L - overhang - lane0_short rows (the lanes take the rows past their tile from the next
+  // lane and, but for the first, their start state from the previous one)
+  const long long ov = p->precision == SPL_PREC_F64 ? spl::overhang_rows_f64()
+                       : lp.tiled_mixed          ? spl::tiled_mixed_overhang_rows()
+                                                 : 0;
+  const long long l0s = p->precision == SPL_PREC_F64 ? spl::lane0_short_rows_f64()
+                        : lp.tiled_mixed          ? spl::tiled_mixed_lane0_short_rows()
+                                                  : 0;
   long long tiles = 0;
   for (uint32_t i = 0; i < count; ++i) {
     const spl_request &r = reqs[i];
@@ -278,8 +288,8 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
     I.yp1 = r.yp1; I.ypn = r.ypn;
     I.tile_rows = L;
     I.ntiles = ((long long)r.n + L - 1) / L;
-    if (ov > 0 && I.ntiles >= 32 && L > ov + spl::lane0_short_rows_f64()) {
-      const long long G = 32LL * L - ov - spl::lane0_short_rows_f64();
+    if (ov > 0 && I.ntiles >= 32 && L > ov + l0s) {
+      const long long G = 32LL * L - ov - l0s;
       tiles = (tiles + 31) / 32 * 32;
       I.ntiles = 32 * (((long long)r.n + G - 1) / G);
       I.pad = 1;
@@ -298,7 +308,10 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
   lp.total_tiles = tiles;
   lp.threads = threads_for(c, p->precision, tiles);
   lp.tile_rows = L;
-  lp.ring_bytes = (p->precision == SPL_PREC_F64 && lp.fit) ? spl::ring_bytes_f64(lp.threads, L) : 0;
+  lp.ring_bytes = !lp.fit                           ? 0
+                  : p->precision == SPL_PREC_F64   ? spl::ring_bytes_f64(lp.threads, L)
+                  : lp.tiled_mixed                 ? spl::scratch_bytes_tiled_mixed(lp.threads, L)
+                                                   : 0;
 
   // footprint check against the whole budget first
   uint64_t need = round_up(sizeof(Inst) * count, kAlign) + round_up(status_block_bytes(count), kAlign) +
@@ -399,8 +412,9 @@ cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, 
     e = spl::launch_fused_f64(insts, count, lp.total_tiles, reinterpret_cast<double *>(c->arena + d_ring_off),
                               lp.tile_rows, lp.threads, counters, st);
     if (launches) *launches += 1;
-  } else if (lp.refine_steps == 0) {
-    e = spl::launch_fused_mixed(insts, count, lp.total_tiles, lp.threads, counters, st, false);
+  } else if (lp.tiled_mixed) {
+    e = spl::launch_tiled_mixed(insts, count, lp.total_tiles, reinterpret_cast<float *>(c->arena + d_ring_off),
+                                lp.tile_rows, lp.threads, counters, st);
     if (launches) *launches += 1;
   } else {
     e = spl::launch_fused_mixed(insts, count, lp.total_tiles, lp.threads, counters, st, true);

@@ -11,6 +11,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import weakref
 
 import numpy as np
 
@@ -241,6 +242,7 @@ class Context:
         self.device = int(device)
         dev = torch.device("cuda", self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._servers = weakref.WeakSet()  # closed before the context (they use its arena)
         if arena is None:
             arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=dev)
         self.arena = arena
@@ -296,6 +298,8 @@ class Context:
 
     def close(self):
         if getattr(self, "handle", None):
+            for srv in list(getattr(self, "_servers", ())):
+                srv.close()
             self.lib.spl_destroy(self.handle)
             self.handle = None
 
@@ -318,6 +322,7 @@ class Server:
         h = ctypes.c_void_p()
         _check(self.lib.spl_serve_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)), "spl_serve_create")
         self.handle = h
+        ctx._servers.add(self)
         self._keep = {}
 
     def submit(self, x, y, yp1=NATURAL, ypn=NATURAL, m=None, ypp_out=None, yq_out=None, jq_out=None) -> int:

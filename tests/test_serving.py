@@ -44,11 +44,11 @@ def _outputs(p):
 
 
 def _reference(ctx, p):
-    """The same request through spl_submit with the same tiling (mixed, no refinement)."""
-    plan = ctx.plan(max_n=1 << 26, precision=spl.PREC_F32_REFINE, refine_steps=0, tile_rows=TILE)
+    """The same request served alone: a fresh server with nothing else in flight."""
+    srv = spl.Server(ctx, max_inflight=1, tile_rows=TILE, idle_timeout_ms=20)
     ypp, yq = _outputs(p)
-    t = ctx.submit(plan, p["xt"], p["yt"], p["bc"][0], p["bc"][1], p["m"], ypp, yq)
-    s, _ = ctx.wait(t)
+    s, _ = srv.wait(srv.submit(p["xt"], p["yt"], p["bc"][0], p["bc"][1], p["m"], ypp, yq))
+    srv.close()
     assert s == spl.OK
     return ypp.cpu().numpy(), yq.cpu().numpy()
 
