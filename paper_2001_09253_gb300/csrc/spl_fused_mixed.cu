@@ -772,10 +772,144 @@ __device__ FwdOutT tile_forward_t(const Inst &I, const RowsT &T, const ScrT &S) 
   return out;
 }
 
-__device__ void tile_bwd_eval_t(const Inst &I, const RowsT &T, long long rlast, const ScrT &S) {
-  const long long n = I.n, m = I.m;
+// Forward sweep of the refinement's correction system A delta = r, r = d - A Z (the residual of
+// the stored binary32 Z in double-float arithmetic from exact double-float widths and value
+// differences), with the binary32 matrix of the first pass; the tile's start as in
+// tile_forward_t (halo, or chained with the same sensitivities: the matrix is the same).
+struct FwdRT {
+  double xn, yn;  // x_{r+1}, y_{r+1}
+  double xa, ya;  // x_{r+2}, y_{r+2}
+  F2 h, s;        // h_r, s_r
+  float zr, zn, za;  // Z_r, Z_{r+1}, Z_{r+2}
+  float cp, dp;
+};
+
+__device__ FwdOutT tile_forward_rt(const Inst &I, const RowsT &T, const ScrT &S) {
+  const long long n = I.n;
   const double *__restrict__ x = I.x;
   const double *__restrict__ y = I.y;
+  const float *__restrict__ z = I.z;
+  const long long s0 = T.s0, e0 = T.e0;
+  const bool nat0 = is_natural(I.yp1), nat1 = is_natural(I.ypn);
+  long long r;
+  float cp_start = 0.0f;
+  if (T.chain) {
+    const long long i0 = max(s0 - 1 - kHaloCT, 0LL);
+    float c = (i0 == 0 && !nat0) ? 0.5f : 0.0f;
+    double xb = x[i0 + 1];
+    float hp = dif32_near(xb, x[i0]);
+    for (long long i = i0 + 1; i <= s0 - 1; ++i) {
+      const double xc = x[i + 1];
+      const float hi = dif32_near(xc, xb);
+      c = hi * rcp32(2.0f * (hp + hi) - hp * c);
+      hp = hi;
+      xb = xc;
+    }
+    cp_start = c;
+    r = s0 - 1;
+  } else {
+    r = max(s0 - kLane0ShortT, 0LL);
+  }
+  FwdRT F;
+  {
+    const double x0 = x[r], x1 = x[r + 1], y0 = y[r], y1 = y[r + 1];
+    const float z0 = z[r], z1 = z[r + 1];
+    F.xa = F.ya = 0.0;
+    F.za = 0.0f;
+    if (r + 2 < n) { F.xa = x[r + 2]; F.ya = y[r + 2]; F.za = z[r + 2]; }
+    const F2 h = dif2(x1, x0);
+    const float ih = rcp32(h.hi);
+    const F2 sl = df_div(dif2(y1, y0), h, ih);
+    F.xn = x1; F.yn = y1; F.h = h; F.s = sl; F.zr = z0; F.zn = z1;
+    if (T.chain) {
+      F.cp = cp_start;
+      F.dp = 0.0f;
+    } else if (r == 0 && !nat0) {
+      // clamped first row: 6(s_0 - y'_0) - (2 h_0 Z_0 + h_0 Z_1), divided by b = 2 h_0
+      const F2 d = df_mul_f(df_add(sl, df_neg(f2_of(I.yp1))), 6.0f);
+      const F2 az = df_add(df_mul_f(h, 2.0f * z0), df_mul_f(h, z1));
+      const F2 res = df_add(d, df_neg(az));
+      F.cp = 0.5f;
+      F.dp = (res.hi + res.lo) * 0.5f * ih;
+    } else if (r == 0) {
+      F.cp = 0.0f;
+      F.dp = -z0;  // natural first row: y''_0 = 0
+    } else {
+      F.cp = 0.0f;
+      F.dp = 0.0f;
+    }
+    if (r >= s0) { S.at(0, 0) = F.cp; S.at(0, 1) = F.dp; }
+  }
+  FwdOutT out;
+  out.A = out.B = 0.0f;
+  out.bad = 0;
+  float M = 1.0f;
+  int K = 0;
+  bool track = T.chain;
+  const long long rlast = T.succ ? e0 - 1 : min(e0 + kOvT, n) - 1;
+  while (r < rlast) {
+    const long long j = r + 1;
+    const float hf = F.h.hi;
+    float cpj, dpj, iden;
+    if (j <= n - 2) {
+      const double x2 = F.xa, y2 = F.ya;
+      const float z2 = F.za;
+      if (j + 2 < n) { F.xa = x[j + 2]; F.ya = y[j + 2]; F.za = z[j + 2]; }
+      if (j + 2 + kPrefetchM < n) {
+        prefetch_l2m(x + j + 2 + kPrefetchM); prefetch_l2m(y + j + 2 + kPrefetchM);
+        prefetch_l2m(z + j + 2 + kPrefetchM);
+      }
+      const F2 hj = dif2(x2, F.xn);
+      const float ihj = rcp32(hj.hi);
+      const F2 sj = df_div(dif2(y2, F.yn), hj, ihj);
+      const F2 d = df_mul_f(df_add(sj, df_neg(F.s)), 6.0f);
+      const F2 az = df_add(df_add(df_mul_f(F.h, F.zr), df_mul_f(df_add(F.h, hj), 2.0f * F.zn)), df_mul_f(hj, z2));
+      const F2 res = df_add(d, df_neg(az));
+      iden = rcp32(2.0f * (hf + hj.hi) - hf * F.cp);
+      cpj = hj.hi * iden;
+      dpj = ((res.hi + res.lo) - hf * F.dp) * iden;
+      F.xn = x2; F.yn = y2; F.h = hj; F.s = sj; F.zr = F.zn; F.zn = z2;
+    } else {  // last row
+      cpj = 0.0f;
+      iden = rcp32(2.0f * hf - hf * F.cp);
+      if (nat1) {
+        dpj = -F.zn;  // y''_{n-1} = 0
+      } else {
+        const F2 d = df_mul_f(df_add(f2_of(I.ypn), df_neg(F.s)), 6.0f);
+        const F2 az = df_add(df_mul_f(F.h, F.zr), df_mul_f(F.h, 2.0f * F.zn));
+        const F2 res = df_add(d, df_neg(az));
+        dpj = ((res.hi + res.lo) - hf * F.dp) * iden;
+      }
+    }
+    F.cp = cpj; F.dp = dpj;
+    r = j;
+    if (j >= s0) { S.at(j - s0, 0) = cpj; S.at(j - s0, 1) = dpj; }
+    if (track) {
+      M *= (j == n - 1 && nat1) ? 0.0f : -hf * iden;
+      S.m(K++) = M;
+      if (!(fabsf(M) >= kMStopT) || K == kMRowsT) track = false;
+    }
+    if (j == e0 - 1) {
+      out.A = dpj;
+      out.B = track ? M : 0.0f;
+    }
+  }
+  out.rlast = rlast;
+  out.K = K;
+  return out;
+}
+
+// Back substitution from the tile's top, fused with the evaluation.  kMode 0: the recurrence
+// gives y''; output y'' and S(x_k).  kMode 1 (first pass of the refined path): output y'' in
+// binary32 to the scratch I.z, no evaluation.  kMode 2 (refinement): the recurrence gives the
+// correction delta of the stored binary32 Z; y'' = Z + delta is output (the sum in binary64) and
+// evaluated.
+template <int kMode>
+__device__ void tile_bwd_eval_t(const Inst &I, const RowsT &T, long long rlast, const ScrT &S) {
+  const long long n = I.n, m = kMode == 1 ? 0 : I.m;
+  const double *__restrict__ x = I.x;
+  const double *__restrict__ y = I.y;
+  const float *__restrict__ z = I.z;
   const long long s0 = T.s0, e0 = T.e0;
   const long long te = e0 - 1 - s0;
   float Y;
@@ -791,19 +925,45 @@ __device__ void tile_bwd_eval_t(const Inst &I, const RowsT &T, long long rlast, 
     Y = S.at(t, 1);
     for (--t; t > te; --t) Y = S.at(t, 1) - S.at(t, 0) * Y;
   }
-  if (t == te - 1 && I.ypp) I.ypp[n - 1] = to_f64(Y);
+  // a row's outputs from its recurrence value v; returns the row's binary32 y''
+  auto out_row = [&](long long row, float v) -> float {
+    if (kMode == 1) {
+      I.z[row] = v;
+      return v;
+    }
+    if (kMode == 2) {
+      const float zr = z[row];
+      if (I.ypp) I.ypp[row] = to_f64(zr) + to_f64(v);
+      return zr + v;
+    }
+    if (I.ypp) I.ypp[row] = to_f64(v);
+    return v;
+  };
+  if (t == te - 1) out_row(n - 1, Y);
+  if (t < 0) return;
+  if (kMode == 1) {  // no evaluation: the back substitution alone, loads one row ahead
+    float c = S.at(t, 0), d = S.at(t, 1);
+    for (; t >= 0; --t) {
+      const float cc = c, dd = d;
+      if (t > 0) { c = S.at(t - 1, 0); d = S.at(t - 1, 1); }
+      Y = dd - cc * Y;
+      out_row(s0 + t, Y);
+    }
+    return;
+  }
   const bool evaluate = (m > 0 && s0 <= n - 2);
   const Grid G = make_grid(x, n, m);
   const long long klo = evaluate ? first_query(G, x, s0) : 0;
   long long k = evaluate ? ((e0 <= n - 2) ? first_query(G, x, e0) - 1 : m - 1) : -1;
-  if (t < 0) return;
-  // current row t: y''_t, y''_{t+1}, knots and values, and the interval's binary32 width,
-  // reciprocal and values; the next row down is loaded one step ahead
+  // current row t: recurrence values (Yt, Yt1) and binary32 y'' (Pt, Pt1) of rows t and t+1,
+  // knots and values, and the interval's binary32 width, reciprocal and values; the next row
+  // down is loaded one step ahead
   float Yt1 = Y;
+  float Pt1 = kMode == 2 ? z[s0 + t + 1] + Y : Y;
   double xt1 = x[s0 + t + 1], xt = x[s0 + t];
   double ytd1 = y[s0 + t + 1], ytd = y[s0 + t];
   float Yt = S.at(t, 1) - S.at(t, 0) * Yt1;
-  if (I.ypp) I.ypp[s0 + t] = to_f64(Yt);
+  float Pt = out_row(s0 + t, Yt);
   float fy1 = to_f32(ytd1), fy0 = to_f32(ytd);
   float ba = dif32_near(xt1, xt), iba = rcp32(ba);
   float c_n = 0.0f, d_n = 0.0f;
@@ -821,10 +981,10 @@ __device__ void tile_bwd_eval_t(const Inst &I, const RowsT &T, long long rlast, 
   load_next(t - 1);
   auto step_down = [&]() {
     --t;
-    Yt1 = Yt; xt1 = xt; fy1 = fy0;
+    Yt1 = Yt; Pt1 = Pt; xt1 = xt; fy1 = fy0;
     xt = x_n; ytd = y_n;
     Yt = d_n - c_n * Yt1;
-    if (I.ypp) I.ypp[s0 + t] = to_f64(Yt);
+    Pt = out_row(s0 + t, Yt);
     load_next(t - 1);
     fy0 = to_f32(ytd);
     ba = dif32_near(xt1, xt);
@@ -840,7 +1000,7 @@ __device__ void tile_bwd_eval_t(const Inst &I, const RowsT &T, long long rlast, 
       kxt = dkey(xt);
     }
     const float xa = dif32_near(q, xt);
-    I.yq[k] = to_f64(newint32(xa, ba - xa, fy0, fy1, Yt, Yt1, ba, iba));
+    I.yq[k] = to_f64(newint32(xa, ba - xa, fy0, fy1, Pt, Pt1, ba, iba));
     if (I.jq) I.jq[k] = (int32_t)(s0 + t);
     q = qn;
   }
@@ -851,6 +1011,7 @@ __device__ __forceinline__ void tile_correct_t(const FwdOutT &o, float delta, co
   for (int k = 0; k < o.K; ++k) S.at(k, 1) = fmaf(S.m(k), delta, S.at(k, 1));
 }
 
+template <int kMode>  // 0: fit + eval, 1: fit only (refined path), 2: refine + eval
 __global__ void __launch_bounds__(kThreadsT, 1)
     mixed_tiled_kernel(const Inst *__restrict__ insts, int ninst, long long total_tiles,
                        unsigned long long *__restrict__ counter, float *__restrict__ scratch, long long rows_cap) {
@@ -877,7 +1038,7 @@ __global__ void __launch_bounds__(kThreadsT, 1)
       const int i = find_inst(insts, ninst, t);
       I = insts[i];
       T = rows_of_t(I, t - I.tile_begin);
-      if (T.s0 < I.n) o = tile_forward_t(I, T, S);
+      if (T.s0 < I.n) o = kMode == 2 ? tile_forward_rt(I, T, S) : tile_forward_t(I, T, S);
     }
     float sa = o.A, sb = o.B;
 #pragma unroll
@@ -892,7 +1053,7 @@ __global__ void __launch_bounds__(kThreadsT, 1)
     if (o.rlast >= 0 && T.chain) tile_correct_t(o, delta, S);
     __syncwarp();
     if (o.rlast >= 0) {
-      tile_bwd_eval_t(I, T, o.rlast, S);
+      tile_bwd_eval_t<kMode>(I, T, o.rlast, S);
       if (o.bad) atomicOr(I.status, o.bad);
     }
     __syncwarp();
@@ -908,9 +1069,14 @@ size_t scratch_bytes_tiled_mixed(long long threads, int tile_rows) {
 }
 
 cudaError_t launch_tiled_mixed(const Inst *d_insts, int ninst, long long total_tiles, float *scratch, int tile_rows,
-                               long long threads, unsigned long long *counter, cudaStream_t stream) {
-  mixed_tiled_kernel<<<(unsigned)(threads / kThreadsT), kThreadsT, 0, stream>>>(d_insts, ninst, total_tiles, counter,
-                                                                                 scratch, (long long)tile_rows + kOvT);
+                               long long threads, unsigned long long *counter, cudaStream_t stream, int mode) {
+  const unsigned grid = (unsigned)(threads / kThreadsT);
+  const long long rows_cap = (long long)tile_rows + kOvT;
+  switch (mode) {
+    case 1: mixed_tiled_kernel<1><<<grid, kThreadsT, 0, stream>>>(d_insts, ninst, total_tiles, counter, scratch, rows_cap); break;
+    case 2: mixed_tiled_kernel<2><<<grid, kThreadsT, 0, stream>>>(d_insts, ninst, total_tiles, counter, scratch, rows_cap); break;
+    default: mixed_tiled_kernel<0><<<grid, kThreadsT, 0, stream>>>(d_insts, ninst, total_tiles, counter, scratch, rows_cap); break;
+  }
   return cudaGetLastError();
 }
 

@@ -39,8 +39,10 @@ int mixed_threads_per_sm();  // threads of one mixed-kernel CTA (one CTA per SM)
 int tiled_mixed_overhang_rows();
 int tiled_mixed_lane0_short_rows();
 size_t scratch_bytes_tiled_mixed(long long threads, int tile_rows);
+// mode 0: fit + eval; 1: fit only into Inst::z (binary32), the refined path's first pass; 2:
+// refinement of Inst::z + eval.
 cudaError_t launch_tiled_mixed(const Inst *d_insts, int ninst, long long total_tiles, float *scratch, int tile_rows,
-                               long long threads, unsigned long long *counter, cudaStream_t stream);
+                               long long threads, unsigned long long *counter, cudaStream_t stream, int mode);
 
 // Separate evaluation (spl_eval.cu): queries q_begin .. q_begin+mq-1 of each instance, explicit
 // (Inst::xq) or on the uniform grid, with the y'' in Inst::ypp; variant = spl_eval_variant.

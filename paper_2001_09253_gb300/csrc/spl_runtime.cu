@@ -225,7 +225,7 @@ struct LaunchPlan {
   long long threads = 0;
   uint64_t ring_bytes = 0;
   bool fit = true;             // run the fit kernel(s)
-  bool tiled_mixed = false;    // binary32 without refinement: the tiled kernel
+  bool tiled_mixed = false;    // binary32 paths: the tiled kernel (with refinement: two launches)
   bool separate_eval = false;  // evaluate with the separate kernel (explicit queries, stored y'')
   int eval_variant = 0;
   long long total_queries = 0;
@@ -264,8 +264,24 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
   lp.refine_steps = p->precision == SPL_PREC_F64 ? 0 : p->refine_steps;
   lp.fit = reqs[0].ypp_in == nullptr;
   lp.separate_eval = p->query_mode == SPL_QUERY_EXPLICIT || !lp.fit;
-  lp.tiled_mixed = p->precision == SPL_PREC_F32_REFINE && lp.refine_steps == 0;
-  const int L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, lp.tiled_mixed);
+  // binary32 paths: the tiled kernel when most of the launch's points sit in instances its grouped
+  // geometry serves with little padding (32-tile groups), the shared-memory ring kernels otherwise
+  // (many small instances, where every tile runs its own halo either way)
+  lp.tiled_mixed = false;
+  int L;
+  if (p->precision == SPL_PREC_F32_REFINE) {
+    const int Lt = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, true);
+    const long long G = 32LL * Lt - spl::tiled_mixed_overhang_rows() - spl::tiled_mixed_lane0_short_rows();
+    uint64_t grouped_points = 0;
+    for (uint32_t i = 0; i < count && G > 0; ++i) {
+      const long long n = (long long)reqs[i].n, plain = (n + Lt - 1) / Lt, grouped = 32 * ((n + G - 1) / G);
+      if (plain >= 32 && 8 * grouped <= 9 * plain) grouped_points += reqs[i].n;
+    }
+    lp.tiled_mixed = 2 * grouped_points >= total_points;
+    L = lp.tiled_mixed ? Lt : (p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, false));
+  } else {
+    L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, false);
+  }
   lp.eval_variant = p->eval_variant;
   lp.insts.resize(count);
   // Instances of 32 tiles or more of the FP64 and tiled binary32 kernels use the grouped
@@ -288,7 +304,8 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
     I.yp1 = r.yp1; I.ypn = r.ypn;
     I.tile_rows = L;
     I.ntiles = ((long long)r.n + L - 1) / L;
-    if (ov > 0 && I.ntiles >= 32 && L > ov + l0s) {
+    if (ov > 0 && I.ntiles >= 32 && L > ov + l0s &&
+        8 * 32 * (((long long)r.n + 32LL * L - ov - l0s - 1) / (32LL * L - ov - l0s)) <= 9 * I.ntiles) {
       const long long G = 32LL * L - ov - l0s;
       tiles = (tiles + 31) / 32 * 32;
       I.ntiles = 32 * (((long long)r.n + G - 1) / G);
@@ -413,8 +430,18 @@ cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, 
                               lp.tile_rows, lp.threads, counters, st);
     if (launches) *launches += 1;
   } else if (lp.tiled_mixed) {
-    e = spl::launch_tiled_mixed(insts, count, lp.total_tiles, reinterpret_cast<float *>(c->arena + d_ring_off),
-                                lp.tile_rows, lp.threads, counters, st);
+    float *scr = reinterpret_cast<float *>(c->arena + d_ring_off);
+    if (lp.refine_steps == 0) {
+      e = spl::launch_tiled_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, lp.threads, counters, st, 0);
+      if (launches) *launches += 1;
+    } else {
+      e = spl::launch_tiled_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, lp.threads, counters, st, 1);
+      if (e == cudaSuccess)
+        e = spl::launch_tiled_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, lp.threads, counters + 1, st, 2);
+      if (launches) *launches += 2;
+    }
+  } else if (lp.refine_steps == 0) {
+    e = spl::launch_fused_mixed(insts, count, lp.total_tiles, lp.threads, counters, st, false);
     if (launches) *launches += 1;
   } else {
     e = spl::launch_fused_mixed(insts, count, lp.total_tiles, lp.threads, counters, st, true);
