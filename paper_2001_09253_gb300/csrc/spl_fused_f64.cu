@@ -6,32 +6,29 @@
 // the uniform grid of "Curve Interpolation".
 //
 // Parallel decomposition (GB300 design, not in the paper).  The serial Thomas sweep is cut
-// into tiles of L knots.  Every tile is solved independently by one thread, in three passes
-// over per-thread global scratch (lane-interleaved, so warp accesses are coalesced when the
-// lanes move together):
-//   1. forward elimination, started some rows before the tile from the guess c' = d' = 0.
-//      With b = 2(a + c) and c' <= 1/2, row i passes on the error of d' multiplied by at most
-//      a_i / (1.5 a_i + 2 c_i) (< 2/3): the halo is grown backwards from the tile until the
-//      product of these bounds, computed on the integer/FP32 pipes from the knot widths, is
-//      below 2^-110 (at least 16 rows, so that c' has converged too, at most 192 rows, where
-//      even the worst case is below 2^-112).  The target is far below binary64 resolution
-//      because d' at the halo start may exceed the solution inside the tile by many orders of
-//      magnitude (knot gaps spread over many decades).  c', d' and 1/h of the tile's rows and
-//      of kHaloB rows past its end go to the scratch;
-//   2. back substitution from kHaloB rows past the tile, from the guess y'' = d', once over
-//      the whole tile; its error is multiplied by c'_i <= c_i / (1.5 a_i + 2 c_i) < 1/2 per
-//      row (typically ~0.27, ~1e-27 after 48 rows; 3.6e-15 in the worst case).  y'' replaces
-//      d' in the scratch;
-//   3. evaluation of the queries whose interval lies in the tile, walking the uniform grid
-//      and the knots together (the monotone sweep of "Quality Checks"), with the fit's 1/h_j.
+// into tiles of L knots, each solved by one thread in two passes over per-warp scratch in
+// global memory (lane-interleaved, so warp accesses are coalesced when the lanes move
+// together):
+//   1. forward elimination of the tile's rows (and of the rows past it that start the back
+//      substitution, when the next lane does not hold them), storing c', d' and 1/h.  Its start:
+//      a halo grown backwards from the tile from the guess c' = d' = 0 until the product of the
+//      per-row bounds a_i / (1.5 a_i + 2 c_i) (< 2/3, from b = 2(a + c) and c' <= 1/2) is below
+//      2^-110, or, for a chained tile, the exact c' and a linear correction of d' (see TileRows);
+//      2^-110 is far below binary64 resolution because d' at the halo start may exceed the
+//      solution inside the tile by many orders of magnitude (knot gaps spread over many
+//      decades);
+//   2. back substitution from 48 rows past the tile, from the guess y'' = d' (its error is
+//      multiplied by c'_i <= c_i / (1.5 a_i + 2 c_i) < 1/2 per row: typically ~0.27, ~1e-27
+//      after 48 rows; 3.6e-15 in the worst case), fused with the evaluation of the queries
+//      whose interval lies in the tile, walking the uniform grid and the knots down together
+//      (the monotone sweep of "Quality Checks", reversed), with the fit's 1/h_j.
 //
-// GB300 notes: FP64 runs at ~1.7 lanes/clk/SM here and one warp per SM sub-partition cannot
-// keep the pipe busy through its own dependency chains, so the kernel runs two CTAs of four
-// warps per SM (two warps per sub-partition).  Scratch instead of a shared-memory ring frees
-// the shared memory for that and removes the per-segment halo recomputation; the back
-// substitution's loads do not depend on the recurrence and are issued four rows ahead.
-// Comparisons run on integer keys, divisions as a MUFU seed + 3 DFMAs, and the next row's
-// width, reciprocal and slope are computed while the current row's elimination is in flight.
+// GB300 notes: FP64 runs at ~1.7 lanes/clk/SM here and a few warps per SM sub-partition cannot
+// keep the pipe busy through their own dependency chains; one CTA of 14 warps per SM measured
+// best (13, 15 and 16 warps are slower: more tiles also means more per-tile work).  Global
+// scratch leaves the shared memory unused.  Comparisons run on integer keys, divisions as a
+// MUFU seed + 3 DFMAs, and the next row's width, reciprocal and slope are computed while the
+// current row's elimination is in flight.
 #include <algorithm>
 
 #include "spl_device.cuh"
@@ -40,8 +37,8 @@
 
 namespace spl {
 
-constexpr int kThreads = 128;           // four warps per CTA
-constexpr int kCtasPerSm = 2;           // two warps per SM sub-partition
+constexpr int kThreads = 448;           // 14 warps per CTA
+constexpr int kCtasPerSm = 1;
 constexpr int kHaloB = 48;              // back-substitution start past the tile end
 constexpr int kHaloFMax = 192;          // forward-elimination halo, worst case: (2/3)^192
 constexpr int kHaloFMin = 16;

@@ -182,8 +182,9 @@ spl_status check_request(const spl_plan *plan, const spl_request *r) {
 }
 
 // Launch geometry: persistent CTAs, one thread per tile, tiles fetched dynamically.  The FP64
-// kernel runs 256 threads per SM (two warps per SM sub-partition keep the FP64 pipe busy);
-// the mixed kernels 512 (four warps per sub-partition hide the L2 latency of their loads).
+// kernel runs 448 threads per SM (its measured best between FP64-pipe latency hiding and the
+// per-tile work more tiles bring); the mixed kernels 512 (four warps per sub-partition hide
+// the latency of their loads).
 long long threads_for(const spl_ctx *c, int precision, long long total_tiles) {
   return precision == SPL_PREC_F64 ? spl::threads_f64(c->sm_count, total_tiles)
                                    : spl::threads_mixed(c->sm_count, total_tiles);
