@@ -1061,6 +1061,12 @@ __global__ void __launch_bounds__(kThreadsT, 1)
 }
 
 int tiled_mixed_overhang_rows() { return kOvT; }
+int tiled_mixed_threads_per_sm() { return kThreadsT; }
+
+long long threads_tiled_mixed(int sm_count, long long total_tiles) {
+  long long blocks = std::min<long long>((total_tiles + kThreadsT - 1) / kThreadsT, (long long)sm_count);
+  return std::max<long long>(blocks, 1) * kThreadsT;
+}
 int tiled_mixed_lane0_short_rows() { return kLane0ShortT; }
 
 size_t scratch_bytes_tiled_mixed(long long threads, int tile_rows) {

@@ -37,6 +37,8 @@ int mixed_threads_per_sm();  // threads of one mixed-kernel CTA (one CTA per SM)
 // Tiled binary32 fit + evaluation without refinement (spl_fused_mixed.cu, mixed_tiled_kernel):
 // grouped tiles as the FP64 kernel's, per-warp scratch of scratch_bytes_tiled_mixed bytes.
 int tiled_mixed_overhang_rows();
+int tiled_mixed_threads_per_sm();  // one CTA per SM
+long long threads_tiled_mixed(int sm_count, long long total_tiles);
 int tiled_mixed_lane0_short_rows();
 size_t scratch_bytes_tiled_mixed(long long threads, int tile_rows);
 // mode 0: fit + eval; 1: fit only into Inst::z (binary32), the refined path's first pass; 2:

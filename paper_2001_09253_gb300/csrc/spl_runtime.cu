@@ -185,8 +185,9 @@ spl_status check_request(const spl_plan *plan, const spl_request *r) {
 // kernel runs 448 threads per SM (its measured best between FP64-pipe latency hiding and the
 // per-tile work more tiles bring); the mixed kernels 512 (four warps per sub-partition hide
 // the latency of their loads).
-long long threads_for(const spl_ctx *c, int precision, long long total_tiles) {
+long long threads_for(const spl_ctx *c, int precision, long long total_tiles, bool tiled_mixed) {
   return precision == SPL_PREC_F64 ? spl::threads_f64(c->sm_count, total_tiles)
+         : tiled_mixed             ? spl::threads_tiled_mixed(c->sm_count, total_tiles)
                                    : spl::threads_mixed(c->sm_count, total_tiles);
 }
 
@@ -194,7 +195,9 @@ long long threads_for(const spl_ctx *c, int precision, long long total_tiles) {
 // shorter than a few halos.  FP64 tiles come in warp groups of 32L - overhang - lane0_short
 // rows, so L is chosen for the group count to match the warps.
 int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points, bool tiled_mixed) {
-  const long long per_sm = precision == SPL_PREC_F64 ? spl::f64_threads_per_sm() : spl::mixed_threads_per_sm();
+  const long long per_sm = precision == SPL_PREC_F64 ? spl::f64_threads_per_sm()
+                           : tiled_mixed             ? spl::tiled_mixed_threads_per_sm()
+                                                     : spl::mixed_threads_per_sm();
   const long long target = (long long)c->sm_count * per_sm;
   long long L = (long long)((total_points + target - 1) / target);
   if (precision == SPL_PREC_F64 || tiled_mixed) {
@@ -324,7 +327,7 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
     }
   }
   lp.total_tiles = tiles;
-  lp.threads = threads_for(c, p->precision, tiles);
+  lp.threads = threads_for(c, p->precision, tiles, lp.tiled_mixed);
   lp.tile_rows = L;
   lp.ring_bytes = !lp.fit                           ? 0
                   : p->precision == SPL_PREC_F64   ? spl::ring_bytes_f64(lp.threads, L)
