@@ -1,0 +1,93 @@
+"""GPU parity of the grouped, chained tile decomposition (FP64 kernel and tiled binary32
+kernel) on inputs sized so that their tiles form several 32-tile warp groups with a ragged last
+group: every lane but the first of a group starts from the exact c' and a corrected d', every
+lane but the last takes its back-substitution start from the next lane's rows.
+
+Group sizes for the forced tile lengths: FP64, L = 200 -> a group covers 32 L - 48 - 56 = 6296
+rows; binary32, L = 150 -> 32 L - 24 - 48 = 4728 rows.  The sizes below give 7 and 9 groups
+whose padding stays under the 1/8 the runtime allows, so the grouped geometry is used."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2001_09253_gb300 import spl, synth
+from parity_util import TOL_F64, TOL_MIXED, check_instance, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+NAT = spl.NATURAL
+N64, L64 = 6296 * 7 - 1000, 200
+N32, L32 = 4728 * 9 - 500, 150
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = spl.Context(device=0, arena_bytes=2 << 30, max_slots=64)
+    yield c
+    c.close()
+
+
+def test_group_sizes_are_grouped():
+    """The sizes above meet the runtime's grouping rule (32-tile groups, padding <= 1/8)."""
+    for n, L, extra in ((N64, L64, 48 + 56), (N32, L32, 24 + 48)):
+        plain = -(-n // L)
+        groups = -(-n // (32 * L - extra))
+        assert plain >= 32 and 8 * 32 * groups <= 9 * plain and groups >= 5
+
+
+@pytest.mark.parametrize("bc", [(NAT, NAT), (-1.0, 1.0), (NAT, 0.25)])
+def test_fp64_grouped_chained(ctx, bc):
+    x, y = synth.curve(71, N64)
+    plan = ctx.plan(N64, spl.PREC_F64, tile_rows=L64)
+    for m in (N64, 3 * N64 + 7, 1001):
+        check_instance(ctx, plan, x, y, bc[0], bc[1], m)
+
+
+def test_fp64_grouped_adversarial(ctx):
+    for seed in (1, 2):
+        x, y = synth.curve_adversarial(seed, N64, decades=8)
+        plan = ctx.plan(N64, spl.PREC_F64, tile_rows=L64)
+        check_instance(ctx, plan, x, y, NAT, NAT, N64 + 5)
+        check_instance(ctx, plan, x, y, 0.5, -2.0, N64 // 3)
+
+
+@pytest.mark.parametrize("refine", [0, 1])
+@pytest.mark.parametrize("bc", [(NAT, NAT), (-1.0, 1.0)])
+def test_mixed_grouped_chained(ctx, refine, bc):
+    x, y = synth.curve(72, N32)
+    plan = ctx.plan(N32, spl.PREC_F32_REFINE, refine_steps=refine, tile_rows=L32)
+    for m in (N32, 2 * N32 + 3):
+        check_instance(ctx, plan, x, y, bc[0], bc[1], m, tol=TOL_MIXED)
+
+
+@pytest.mark.parametrize("refine", [0, 1])
+def test_mixed_grouped_adversarial(ctx, refine):
+    x, y = synth.curve_adversarial(3, N32, decades=6)
+    plan = ctx.plan(N32, spl.PREC_F32_REFINE, refine_steps=refine, tile_rows=L32)
+    ref = oracle.fit_eval(x, y, NAT, NAT, N32)
+    st, ypp, yq, jq = run_gpu(ctx, plan, x, y, NAT, NAT, N32)
+    assert st == 0
+    assert np.array_equal(jq.astype(np.int64), ref["jq"])
+    from parity_util import ypp_error, yq_error
+    assert ypp_error(ypp, ref["ypp"]) <= TOL_MIXED
+    assert yq_error(x, y, ref["ypp"], ref["jq"], yq, ref["yq"]) <= TOL_MIXED
+    if refine:  # the refinement brings y'' to FP64 accuracy
+        assert ypp_error(ypp, ref["ypp"]) <= 1e-8
+
+
+@pytest.mark.parametrize("precision,n,L", [(spl.PREC_F64, N64, L64), (spl.PREC_F32_REFINE, N32, L32)])
+def test_errors_inside_a_chained_tile(ctx, precision, n, L):
+    """Input errors in the middle of a chained lane's tile (group 2, lane 5) are reported."""
+    x, y = synth.curve(73, n)
+    plan = ctx.plan(n, precision, tile_rows=L)
+    extra = 48 + 56 if precision == spl.PREC_F64 else 24 + 48
+    G = 32 * L - extra
+    row = 2 * G + 5 * L - (56 if precision == spl.PREC_F64 else 48) + L // 2
+    bad_y = y.copy()
+    bad_y[row] = np.nan
+    st, _, _, _ = run_gpu(ctx, plan, x, bad_y, NAT, NAT, n)
+    assert st == spl.ERR_NONFINITE
+    bad_x = x.copy()
+    bad_x[row] = bad_x[row - 1]
+    st, _, _, _ = run_gpu(ctx, plan, bad_x, y, NAT, NAT, n)
+    assert st == spl.ERR_NOT_INCREASING
