@@ -90,13 +90,6 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-// Width of interval i in binary32 for the decay bounds (never used as a value of the method);
-// negative when the integer route does not apply.
-__device__ __forceinline__ float width32(const double *x, long long i) {
-  float v;
-  return diff_same_f32(x[i + 1], x[i], &v) ? v : -1.0f;
-}
-
 // Start row of the forward halo of a tile beginning at s0 (see the header comment).  Rows are
 // scanned eight at a time with independent loads; the halo may end up a few rows longer than
 // the bound requires.
@@ -469,8 +462,6 @@ int f64_threads_per_sm() { return kThreads * kCtasPerSm; }
 int overhang_rows_f64() { return kHaloB; }
 
 int lane0_short_rows_f64() { return kLane0Short; }
-
-int halo_rows_f64() { return kHaloFMax + kHaloB; }
 
 long long threads_f64(int sm_count, long long total_tiles) {
   long long blocks =

@@ -71,13 +71,6 @@ __device__ __forceinline__ float dif32_near(double b, double a) {
   return sub_f64_f32(b, a);
 }
 
-// arbitrary operands
-__device__ __forceinline__ float dif32(double b, double a) {
-  float v;
-  if (diff_f32(b, a, &v)) return v;
-  return sub_f64_f32(b, a);
-}
-
 __device__ __forceinline__ F2 dif2(double b, double a) {
   F2 v;
   if (diff_f2(b, a, &v)) return v;
@@ -581,8 +574,6 @@ cudaError_t launch_serve(const ServeArgs &args, int sm_count, cudaStream_t strea
   return cudaLaunchCooperativeKernel((const void *)serve_kernel, dim3((unsigned)sm_count), dim3(kThreadsM), params,
                                      kSmemM, stream);
 }
-
-int serve_tile_threads() { return kThreadsM; }
 
 int mixed_threads_per_sm() { return kThreadsM; }
 

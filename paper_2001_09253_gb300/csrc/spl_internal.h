@@ -13,7 +13,6 @@ namespace spl {
 // launch; `counter` (8 bytes of device memory) must be zero when the kernel starts.
 size_t ring_bytes_f64(long long threads, int tile_rows);
 long long threads_f64(int sm_count, long long total_tiles);
-int halo_rows_f64();
 int overhang_rows_f64();  // rows past a tile that start its back substitution
 int lane0_short_rows_f64();  // rows the first tile of an FP64 warp group gives up for its halo
 int f64_threads_per_sm();  // resident threads of the FP64 kernel per SM
@@ -31,7 +30,6 @@ cudaError_t launch_refine_mixed(const Inst *d_insts, int ninst, long long total_
 
 // Persistent serving loop (spl_fused_mixed.cu): a cooperative launch of one CTA per SM.
 cudaError_t launch_serve(const ServeArgs &args, int sm_count, cudaStream_t stream);
-int serve_tile_threads();
 int mixed_threads_per_sm();  // threads of one mixed-kernel CTA (one CTA per SM)
 
 // Tiled binary32 fit + evaluation without refinement (spl_fused_mixed.cu, mixed_tiled_kernel):

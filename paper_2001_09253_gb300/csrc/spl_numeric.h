@@ -121,56 +121,6 @@ SPL_HD bool diff_f32(double b, double a, float *out) {
   return true;
 }
 
-// b - a in binary64 when the difference is exact and the integer route covers it: a or b
-// zero, or two normal numbers of the same sign whose exponents differ by at most one with
-// the smaller magnitude at least half the larger (Sterbenz), which holds for neighbouring
-// knots and for a query and its bracketing knots.  The exact difference is unique, so the
-// result is bit-identical to the FP64 subtraction.  Returns false otherwise (and for
-// subnormal, infinite or NaN operands or a subnormal result): subtract in FP64 then.
-SPL_HD bool diff_exact64(double b, double a, double *out) {
-  const uint64_t ub = bits64(b), ua = bits64(a);
-  const uint64_t mag_b = ub & 0x7FFFFFFFFFFFFFFFull, mag_a = ua & 0x7FFFFFFFFFFFFFFFull;
-  if (mag_a == 0) {
-    if (mag_b == 0) return false;
-    if ((mag_b >> 52) == 0x7FF) return false;
-    *out = b;
-    return true;
-  }
-  if (mag_b == 0) {
-    if ((mag_a >> 52) == 0x7FF) return false;
-    *out = from_bits64(ua ^ 0x8000000000000000ull);
-    return true;
-  }
-  if ((ub ^ ua) >> 63) return false;  // opposite signs: a rounded sum
-  const bool b_big = mag_b >= mag_a;
-  const uint64_t big = b_big ? mag_b : mag_a, small = b_big ? mag_a : mag_b;
-  const int eB = (int)(big >> 52), eS = (int)(small >> 52);
-  if (eS == 0 || eB == 0x7FF) return false;
-  const uint64_t MB = (big & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
-  const uint64_t MS = (small & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
-  uint64_t D;
-  int e0;
-  if (eB == eS) {
-    D = MB - MS;
-    e0 = eB;
-  } else if (eB == eS + 1 && MB <= MS) {
-    D = 2 * MB - MS;
-    e0 = eS;
-  } else {
-    return false;
-  }
-  if (D == 0) {
-    *out = 0.0;
-    return true;
-  }
-  const int sh = clz64(D) - 11;  // leading one to bit 52
-  const int E = e0 - sh;
-  if (E <= 0) return false;
-  const uint64_t sign = ((ub >> 63) ^ (b_big ? 0u : 1u)) & 1u;  // sign(b) * sign(|b| - |a|)
-  *out = from_bits64((sign << 63) | ((uint64_t)E << 52) | ((D << sh) & 0xFFFFFFFFFFFFFull));
-  return true;
-}
-
 // b - a rounded to nearest-even binary32 for the common case of two binary64 numbers with
 // the same sign and exponent field (neighbouring knots, a query and the knot below it): the
 // encodings then differ by the exact difference in units of the shared ulp, so one integer
