@@ -91,3 +91,17 @@ def test_errors_inside_a_chained_tile(ctx, precision, n, L):
     bad_x[row] = bad_x[row - 1]
     st, _, _, _ = run_gpu(ctx, plan, bad_x, y, NAT, NAT, n)
     assert st == spl.ERR_NOT_INCREASING
+
+
+@pytest.mark.parametrize("precision,L,extra,tol", [(spl.PREC_F64, 128, 48 + 56, TOL_F64),
+                                                   (spl.PREC_F32_REFINE, 96, 24 + 48, TOL_MIXED)])
+def test_group_boundaries_sweep(ctx, precision, L, extra, tol):
+    """Sizes around whole groups (exactly k groups, one row more or less, a lone row past a
+    group, the last lane's tile cut short), seeded, both end conditions."""
+    G = 32 * L - extra
+    sizes = sorted({k * G + d for k in (1, 2, 3) for d in (-1, 0, 1, 2, 17, -L + 1, L - 1)})
+    plan = ctx.plan(4 * G, precision, tile_rows=L)
+    for i, n in enumerate(sizes):
+        x, y = synth.curve(80 + i, n)
+        bc = (NAT, NAT) if i % 2 else (0.75, -1.25)
+        check_instance(ctx, plan, x, y, bc[0], bc[1], n + (i % 3), tol=tol)
