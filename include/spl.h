@@ -79,7 +79,7 @@ typedef enum spl_query_mode {
   SPL_QUERY_UNIFORM = 0,    /* m uniform queries on [x_0, x_{n-1}] (section "Curve Interpolation") */
   SPL_QUERY_EXPLICIT = 1    /* m caller-given positions xq[m], any order, each bracketed by
                                bisection (the interval search of section "Quality Checks" for an
-                               unsorted query; SPL_PREC_F64 plans only) */
+                               unsorted query) */
 } spl_query_mode;
 
 /* Form of the evaluation (plan option; used when the queries are evaluated by the separate
@@ -89,7 +89,9 @@ typedef enum spl_query_mode {
  *   NOINV  the sum divided by (x_{j+1}-x_j) at the end;
  *   VOL    ORIG with inv_ba kept in a volatile local (a memory round trip pins the division
  *          before the cubic, the paper's scheduling trick).
- * All three agree to rounding; the fused uniform-grid kernels always use ORIG. */
+ * All three agree to rounding; the fused uniform-grid kernels always use ORIG.  The evaluation
+ * kernel runs them in binary64 for SPL_PREC_F64 plans and in binary32 (exact differences of the
+ * binary64 positions, rounded once) for SPL_PREC_F32_REFINE plans. */
 typedef enum spl_eval_variant {
   SPL_EVAL_ORIG = 0,
   SPL_EVAL_NOINV = 1,
@@ -129,7 +131,7 @@ typedef struct spl_ctx_desc {
  *                 values are SPL_ERR_INVALID_ARG.
  *   tile_rows     knots per tile of the chunked solve; 0 picks it from the device and n.
  *                 Exposed so tests can force many small tiles; values below 16 are refused.
- *   query_mode    spl_query_mode; SPL_QUERY_EXPLICIT needs precision SPL_PREC_F64.
+ *   query_mode    spl_query_mode.
  *   eval_variant  spl_eval_variant of the separate evaluation kernel. */
 typedef struct spl_plan_desc {
   uint64_t max_n;
@@ -154,8 +156,8 @@ typedef struct spl_plan_desc {
  *                below x_0 or above x_{n-1} is extrapolated by the end cubic).  Must be NULL
  *                in uniform mode.  A non-finite position completes with SPL_ERR_NONFINITE.
  *   ypp_in       NULL: fit, then evaluate.  Otherwise y''[n] of an earlier fit of the same
- *                x, y (SPL_PREC_F64 plans only): the fit is skipped and only the evaluation
- *                runs ("fit once, evaluate many"); ypp_out and the end slopes are ignored.
+ *                x, y: the fit is skipped and only the evaluation runs ("fit once, evaluate
+ *                many"), in the plan's precision; ypp_out and the end slopes are ignored.
  *                Every request of one spl_submit_batch call must agree on NULL or not. */
 typedef struct spl_request {
   uint64_t n;

@@ -13,6 +13,7 @@
 
 #include "spl_device.cuh"
 #include "spl_internal.h"
+#include "spl_numeric.h"
 
 namespace spl {
 
@@ -54,7 +55,39 @@ __device__ __forceinline__ double newint_variant(double q, double xj, double xj1
   return sum * inv_ba;
 }
 
+// The binary32 form (mixed-precision plans): the differences of binary64 positions are formed
+// exactly and rounded once (one FP64 subtraction for operands of one sign and exponent field,
+// which is exact; a binary32 rounding of the FP64 difference otherwise), values and y'' are
+// rounded to binary32, and the cubic runs in binary32 with the variant's division.
+__device__ __forceinline__ float near_diff32(double b, double a) {
+  const unsigned hb = (unsigned)(bits64(b) >> 32), ha = (unsigned)(bits64(a) >> 32);
+  if (((hb ^ ha) >> 20) == 0u) return (float)(b - a);
+  float v;
+  if (diff_f32(b, a, &v)) return v;
+  return (float)(b - a);
+}
+
 template <int kVariant>
+__device__ __forceinline__ double newint_variant32(double q, double xj, double xj1, double yj, double yj1,
+                                                   double ppj, double ppj1) {
+  const float ba = near_diff32(xj1, xj);
+  const float xa = near_diff32(q, xj);
+  const float bx = ba - xa;
+  float inv_ba = 0.0f;
+  volatile float inv_pinned;
+  if (kVariant == 0) inv_ba = 1.0f / ba;
+  if (kVariant == 2) inv_pinned = 1.0f / ba;
+  const float ba2 = ba * ba;
+  const float lower = xa * (float)yj1 + bx * (float)yj;
+  const float C = (xa * xa - ba2) * xa * (float)ppj1;
+  const float D = (bx * bx - ba2) * bx * (float)ppj;
+  const float sum = lower + (1.0f / 6.0f) * (C + D);
+  if (kVariant == 1) return (double)(sum / ba);
+  if (kVariant == 2) return (double)(sum * inv_pinned);
+  return (double)(sum * inv_ba);
+}
+
+template <int kVariant, bool kF32>
 __global__ void __launch_bounds__(kThreadsE) eval_kernel(const Inst *__restrict__ insts, int ninst,
                                                          long long total_q) {
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -86,21 +119,25 @@ __global__ void __launch_bounds__(kThreadsE) eval_kernel(const Inst *__restrict_
     const long long j = bracket_bisect(x, n, dkey(q));
     const double *__restrict__ y = I.y;
     const double *__restrict__ ypp = I.ypp;
-    I.yq[k] = newint_variant<kVariant>(q, x[j], x[j + 1], y[j], y[j + 1], ypp[j], ypp[j + 1]);
+    I.yq[k] = kF32 ? newint_variant32<kVariant>(q, x[j], x[j + 1], y[j], y[j + 1], ypp[j], ypp[j + 1])
+                   : newint_variant<kVariant>(q, x[j], x[j + 1], y[j], y[j + 1], ypp[j], ypp[j + 1]);
     if (I.jq) I.jq[k] = (int32_t)j;
   }
 }
 
-cudaError_t launch_eval(const Inst *d_insts, int ninst, long long total_q, int variant, int sm_count,
+cudaError_t launch_eval(const Inst *d_insts, int ninst, long long total_q, int variant, bool f32, int sm_count,
                         cudaStream_t stream) {
   if (total_q <= 0) return cudaSuccess;
   const long long blocks =
       std::min<long long>((total_q + kThreadsE - 1) / kThreadsE, (long long)sm_count * kBlocksPerSmE);
   const unsigned grid = (unsigned)std::max<long long>(blocks, 1);
-  switch (variant) {
-    case 1: eval_kernel<1><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q); break;
-    case 2: eval_kernel<2><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q); break;
-    default: eval_kernel<0><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q); break;
+  switch (variant * 2 + (f32 ? 1 : 0)) {
+    case 2: eval_kernel<1, false><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q); break;
+    case 3: eval_kernel<1, true><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q); break;
+    case 4: eval_kernel<2, false><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q); break;
+    case 5: eval_kernel<2, true><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q); break;
+    case 1: eval_kernel<0, true><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q); break;
+    default: eval_kernel<0, false><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q); break;
   }
   return cudaGetLastError();
 }

@@ -177,7 +177,6 @@ spl_status check_request(const spl_plan *plan, const spl_request *r) {
   } else if (r->xq) {
     return SPL_ERR_INVALID_ARG;
   }
-  if (r->ypp_in && plan->precision != SPL_PREC_F64) return SPL_ERR_INVALID_ARG;
   return SPL_OK;
 }
 
@@ -453,7 +452,8 @@ cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, 
     if (launches) *launches += 2;
   }
   if (e == cudaSuccess && lp.separate_eval && lp.total_queries > 0) {
-    e = spl::launch_eval(insts, count, lp.total_queries, lp.eval_variant, c->sm_count, st);
+    e = spl::launch_eval(insts, count, lp.total_queries, lp.eval_variant, lp.precision != SPL_PREC_F64, c->sm_count,
+                         st);
     if (launches) *launches += 1;
   }
   return e;
@@ -623,7 +623,6 @@ spl_status spl_plan_create(spl_ctx *c, const spl_plan_desc *d, spl_plan **out) {
   if (d->precision == SPL_PREC_F64 && d->refine_steps != 0) return SPL_ERR_INVALID_ARG;
   if (d->tile_rows != 0 && d->tile_rows < 16) return SPL_ERR_INVALID_ARG;
   if (d->query_mode != SPL_QUERY_UNIFORM && d->query_mode != SPL_QUERY_EXPLICIT) return SPL_ERR_INVALID_ARG;
-  if (d->query_mode == SPL_QUERY_EXPLICIT && d->precision != SPL_PREC_F64) return SPL_ERR_INVALID_ARG;
   if (d->eval_variant < SPL_EVAL_ORIG || d->eval_variant > SPL_EVAL_VOL) return SPL_ERR_INVALID_ARG;
   spl_plan *p = new (std::nothrow) spl_plan();
   if (!p) return SPL_ERR_CUDA;

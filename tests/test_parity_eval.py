@@ -195,9 +195,8 @@ def test_explicit_errors(ctx):
     dev = torch.device("cuda", ctx.device)
     x, y = synth.curve(24, 500)
     xt, yt = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
-    # explicit mode needs the FP64 precision; unknown modes and variants are refused
-    for kw in ({"precision": spl.PREC_F32_REFINE, "query_mode": spl.QUERY_EXPLICIT}, {"query_mode": 2},
-               {"eval_variant": 3}, {"eval_variant": -1}):
+    # unknown modes and variants are refused
+    for kw in ({"query_mode": 2}, {"eval_variant": 3}, {"eval_variant": -1}):
         with pytest.raises(spl.SplError) as ei:
             ctx.plan(500, **kw)
         assert ei.value.status == spl.ERR_INVALID_ARG
@@ -209,10 +208,6 @@ def test_explicit_errors(ctx):
         ctx.submit(uni, xt, yt, NAT, NAT, 10, None, yq, None, xq=q)
     with pytest.raises(spl.SplError):  # explicit plan without positions
         ctx.submit(exp, xt, yt, NAT, NAT, 10, None, yq, None)
-    mixed = ctx.plan(500, spl.PREC_F32_REFINE)
-    with pytest.raises(spl.SplError):  # stored y'' with the mixed path
-        ctx.submit(mixed, xt, yt, NAT, NAT, 10, None, yq, None, ypp_in=torch.zeros(500, dtype=torch.float64,
-                                                                                 device=dev))
     # a non-finite query position completes with SPL_ERR_NONFINITE
     bad = q.clone()
     bad[3] = float("nan")
@@ -254,3 +249,25 @@ def test_explicit_large_sampled(ctx):
     yref = oracle.evaluate(xh, yh, ref["ypp"], xq[pick], jref[pick])
     e = yq_error(xh, yh, ref["ypp"], jref[pick], yq.cpu().numpy()[pick], yref)
     assert e <= TOL_F64
+
+
+@pytest.mark.parametrize("refine", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_mixed_explicit_queries_and_stored_fit(ctx, refine, variant):
+    """Binary32 plans: explicit unsorted queries after a binary32 fit (refined or not), and
+    evaluation from a stored y'': brackets bit-exact, values within the mixed tolerance."""
+    from paper_2001_09253_gb300 import spl
+    from parity_util import TOL_MIXED
+    rng = np.random.default_rng(30 + 3 * refine + variant)
+    x, y = synth.curve(26, 6000)
+    xq = _queries(x, 8000, rng)
+    ref = oracle.fit_eval(x, y, NAT, NAT, 0)
+    plan = ctx.plan(len(x), spl.PREC_F32_REFINE, refine_steps=refine, query_mode=spl.QUERY_EXPLICIT,
+                    eval_variant=variant)
+    st, ypp, yq, jq = _run(ctx, plan, x, y, xq)
+    assert st == 0
+    assert ypp_error(ypp, ref["ypp"]) <= (1e-8 if refine else TOL_MIXED)
+    _check(x, y, ref["ypp"], xq, yq, jq, tol=TOL_MIXED)
+    st, _, yq2, jq2 = _run(ctx, plan, x, y, xq, ypp_in=ypp, want_ypp=False)
+    assert st == 0
+    assert np.array_equal(yq2, yq) and np.array_equal(jq2, jq)
