@@ -193,7 +193,10 @@ long long threads_for(const spl_ctx *c, int precision, long long total_tiles, bo
 // Tile length so that one instance of total_points fills every thread of one wave; never
 // shorter than a few halos.  FP64 tiles come in warp groups of 32L - overhang - lane0_short
 // rows, so L is chosen for the group count to match the warps.
-int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points, bool tiled_mixed) {
+int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points, bool tiled_mixed, uint32_t count) {
+  // several instances: short tiles, fetched dynamically, balance instances of uneven sizes
+  // (one wave of long tiles waits on the longest; 4,096 log-uniform instances run ~1.4x faster)
+  if (count > 1) return 128;
   const long long per_sm = precision == SPL_PREC_F64 ? spl::f64_threads_per_sm()
                            : tiled_mixed             ? spl::tiled_mixed_threads_per_sm()
                                                      : spl::mixed_threads_per_sm();
@@ -273,7 +276,7 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
   lp.tiled_mixed = false;
   int L;
   if (p->precision == SPL_PREC_F32_REFINE) {
-    const int Lt = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, true);
+    const int Lt = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, true, count);
     const long long G = 32LL * Lt - spl::tiled_mixed_overhang_rows() - spl::tiled_mixed_lane0_short_rows();
     uint64_t grouped_points = 0;
     for (uint32_t i = 0; i < count && G > 0; ++i) {
@@ -281,9 +284,9 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
       if (plain >= 32 && 8 * grouped <= 9 * plain) grouped_points += reqs[i].n;
     }
     lp.tiled_mixed = 2 * grouped_points >= total_points;
-    L = lp.tiled_mixed ? Lt : (p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, false));
+    L = lp.tiled_mixed ? Lt : (p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, false, count));
   } else {
-    L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, false);
+    L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, false, count);
   }
   lp.eval_variant = p->eval_variant;
   lp.insts.resize(count);
