@@ -243,7 +243,7 @@ class Runner:
         self.K, self.W = max(args.steps, 1), max(args.warmup, 3)
         self.n = int(args.n)
         self.window = 16  # launches in flight: enough to keep the device busy
-        ring = 320 << 20  # per-launch scratch bound (FP64 tile scratch or binary32 y'' of a refined launch)
+        ring = 512 << 20  # per-launch scratch bound (FP64 tile scratch ~330 MB at n = 1e7, binary32 scratch less)
         arena = (min(self.window, self.K) + 2) * (ring + 4 * self.n)
         if not args.no_e2e:
             arena += 10 * (32 * self.n + ring)  # host-buffer leg: staged inputs/outputs, 8 in flight

@@ -464,16 +464,17 @@ int overhang_rows_f64() { return kHaloB; }
 int lane0_short_rows_f64() { return kLane0Short; }
 
 long long threads_f64(int sm_count, long long total_tiles) {
-  long long blocks =
-      std::min<long long>((total_tiles + kThreads - 1) / kThreads, (long long)kCtasPerSm * sm_count);
-  return std::max<long long>(blocks, 1) * kThreads;
+  int blocks, bt;
+  spread_grid(sm_count * kCtasPerSm, total_tiles, kThreads, &blocks, &bt);
+  return (long long)blocks * bt;
 }
 
 cudaError_t launch_fused_f64(const Inst *d_insts, int ninst, long long total_tiles, double *scratch,
-                             int tile_rows, long long threads, unsigned long long *counter, cudaStream_t stream) {
-  const long long grid = threads / kThreads;
-  fused_f64_kernel<<<(unsigned)grid, kThreads, 0, stream>>>(d_insts, ninst, total_tiles, counter, scratch,
-                                                            (long long)tile_rows + kHaloB);
+                             int tile_rows, int sm_count, unsigned long long *counter, cudaStream_t stream) {
+  int blocks, bt;
+  spread_grid(sm_count * kCtasPerSm, total_tiles, kThreads, &blocks, &bt);
+  fused_f64_kernel<<<(unsigned)blocks, (unsigned)bt, 0, stream>>>(d_insts, ninst, total_tiles, counter, scratch,
+                                                                  (long long)tile_rows + kHaloB);
   return cudaGetLastError();
 }
 

@@ -578,29 +578,33 @@ cudaError_t launch_serve(const ServeArgs &args, int sm_count, cudaStream_t strea
 int mixed_threads_per_sm() { return kThreadsM; }
 
 long long threads_mixed(int sm_count, long long total_tiles) {
-  long long blocks = std::min<long long>((total_tiles + kThreadsM - 1) / kThreadsM, (long long)sm_count);
-  return std::max<long long>(blocks, 1) * kThreadsM;
+  int blocks, bt;
+  spread_grid(sm_count, total_tiles, kThreadsM, &blocks, &bt);
+  return (long long)blocks * bt;
 }
 
+// The ring is laid out for kThreadsM threads; a smaller CTA (few tiles spread over the SMs)
+// uses the first blockDim.x columns of it.
 template <int kMode>
-static cudaError_t launch_mode(const Inst *d_insts, int ninst, long long total_tiles, long long threads,
+static cudaError_t launch_mode(const Inst *d_insts, int ninst, long long total_tiles, int sm_count,
                                unsigned long long *counter, cudaStream_t stream) {
   cudaError_t e = cudaFuncSetAttribute(mixed_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemM);
   if (e != cudaSuccess) return e;
-  mixed_kernel<kMode><<<(unsigned)(threads / kThreadsM), kThreadsM, kSmemM, stream>>>(d_insts, ninst, total_tiles,
-                                                                                        counter);
+  int blocks, bt;
+  spread_grid(sm_count, total_tiles, kThreadsM, &blocks, &bt);
+  mixed_kernel<kMode><<<(unsigned)blocks, (unsigned)bt, kSmemM, stream>>>(d_insts, ninst, total_tiles, counter);
   return cudaGetLastError();
 }
 
-cudaError_t launch_fused_mixed(const Inst *d_insts, int ninst, long long total_tiles, long long threads,
+cudaError_t launch_fused_mixed(const Inst *d_insts, int ninst, long long total_tiles, int sm_count,
                                unsigned long long *counter, cudaStream_t stream, bool fit_only) {
-  return fit_only ? launch_mode<1>(d_insts, ninst, total_tiles, threads, counter, stream)
-                  : launch_mode<0>(d_insts, ninst, total_tiles, threads, counter, stream);
+  return fit_only ? launch_mode<1>(d_insts, ninst, total_tiles, sm_count, counter, stream)
+                  : launch_mode<0>(d_insts, ninst, total_tiles, sm_count, counter, stream);
 }
 
-cudaError_t launch_refine_mixed(const Inst *d_insts, int ninst, long long total_tiles, long long threads,
+cudaError_t launch_refine_mixed(const Inst *d_insts, int ninst, long long total_tiles, int sm_count,
                                 unsigned long long *counter, cudaStream_t stream) {
-  return launch_mode<2>(d_insts, ninst, total_tiles, threads, counter, stream);
+  return launch_mode<2>(d_insts, ninst, total_tiles, sm_count, counter, stream);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1055,8 +1059,9 @@ int tiled_mixed_overhang_rows() { return kOvT; }
 int tiled_mixed_threads_per_sm() { return kThreadsT; }
 
 long long threads_tiled_mixed(int sm_count, long long total_tiles) {
-  long long blocks = std::min<long long>((total_tiles + kThreadsT - 1) / kThreadsT, (long long)sm_count);
-  return std::max<long long>(blocks, 1) * kThreadsT;
+  int blocks, bt;
+  spread_grid(sm_count, total_tiles, kThreadsT, &blocks, &bt);
+  return (long long)blocks * bt;
 }
 int tiled_mixed_lane0_short_rows() { return kLane0ShortT; }
 
@@ -1066,13 +1071,15 @@ size_t scratch_bytes_tiled_mixed(long long threads, int tile_rows) {
 }
 
 cudaError_t launch_tiled_mixed(const Inst *d_insts, int ninst, long long total_tiles, float *scratch, int tile_rows,
-                               long long threads, unsigned long long *counter, cudaStream_t stream, int mode) {
-  const unsigned grid = (unsigned)(threads / kThreadsT);
+                               int sm_count, unsigned long long *counter, cudaStream_t stream, int mode) {
+  int blocks, bt;
+  spread_grid(sm_count, total_tiles, kThreadsT, &blocks, &bt);
+  const unsigned grid = (unsigned)blocks, block = (unsigned)bt;
   const long long rows_cap = (long long)tile_rows + kOvT;
   switch (mode) {
-    case 1: mixed_tiled_kernel<1><<<grid, kThreadsT, 0, stream>>>(d_insts, ninst, total_tiles, counter, scratch, rows_cap); break;
-    case 2: mixed_tiled_kernel<2><<<grid, kThreadsT, 0, stream>>>(d_insts, ninst, total_tiles, counter, scratch, rows_cap); break;
-    default: mixed_tiled_kernel<0><<<grid, kThreadsT, 0, stream>>>(d_insts, ninst, total_tiles, counter, scratch, rows_cap); break;
+    case 1: mixed_tiled_kernel<1><<<grid, block, 0, stream>>>(d_insts, ninst, total_tiles, counter, scratch, rows_cap); break;
+    case 2: mixed_tiled_kernel<2><<<grid, block, 0, stream>>>(d_insts, ninst, total_tiles, counter, scratch, rows_cap); break;
+    default: mixed_tiled_kernel<0><<<grid, block, 0, stream>>>(d_insts, ninst, total_tiles, counter, scratch, rows_cap); break;
   }
   return cudaGetLastError();
 }

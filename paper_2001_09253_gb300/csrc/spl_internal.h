@@ -8,7 +8,20 @@
 
 namespace spl {
 
-// FP64 fused fit + evaluation (spl_fused_f64.cu).  `threads` comes from threads_f64; `scratch`
+// Persistent-grid geometry: at most one CTA of max_threads per SM; when the tiles would not fill
+// that, the CTAs shrink (to whole warps) so that the tiles spread over all SMs instead of
+// crowding a few.
+inline void spread_grid(int sm_count, long long tiles, int max_threads, int *blocks, int *block_threads) {
+  const long long per_sm = (tiles + sm_count - 1) / sm_count;
+  long long bt = (per_sm + 31) / 32 * 32;
+  bt = bt < 32 ? 32 : (bt > max_threads ? max_threads : bt);
+  long long b = (tiles + bt - 1) / bt;
+  b = b < 1 ? 1 : (b > sm_count ? sm_count : b);
+  *blocks = (int)b;
+  *block_threads = (int)bt;
+}
+
+// FP64 fused fit + evaluation (spl_fused_f64.cu).  `threads` (threads_f64) sizes the scratch; `scratch`
 // must hold ring_bytes_f64(threads, tile_rows) bytes, tile_rows being the longest tile of the
 // launch; `counter` (8 bytes of device memory) must be zero when the kernel starts.
 size_t ring_bytes_f64(long long threads, int tile_rows);
@@ -17,15 +30,15 @@ int overhang_rows_f64();  // rows past a tile that start its back substitution
 int lane0_short_rows_f64();  // rows the first tile of an FP64 warp group gives up for its halo
 int f64_threads_per_sm();  // resident threads of the FP64 kernel per SM
 cudaError_t launch_fused_f64(const Inst *d_insts, int ninst, long long total_tiles, double *scratch,
-                             int tile_rows, long long threads, unsigned long long *counter, cudaStream_t stream);
+                             int tile_rows, int sm_count, unsigned long long *counter, cudaStream_t stream);
 
 // Mixed-precision fused fit + evaluation (spl_fused_mixed.cu).
 long long threads_mixed(int sm_count, long long total_tiles);
 // fit_only: first pass of the refined path (y'' in binary32 to each Inst::z, no queries).
-cudaError_t launch_fused_mixed(const Inst *d_insts, int ninst, long long total_tiles, long long threads,
+cudaError_t launch_fused_mixed(const Inst *d_insts, int ninst, long long total_tiles, int sm_count,
                                unsigned long long *counter, cudaStream_t stream, bool fit_only);
 // Second pass of the refined path: one refinement step of y'' and the evaluation.
-cudaError_t launch_refine_mixed(const Inst *d_insts, int ninst, long long total_tiles, long long threads,
+cudaError_t launch_refine_mixed(const Inst *d_insts, int ninst, long long total_tiles, int sm_count,
                                 unsigned long long *counter, cudaStream_t stream);
 
 // Persistent serving loop (spl_fused_mixed.cu): a cooperative launch of one CTA per SM.
@@ -42,7 +55,7 @@ size_t scratch_bytes_tiled_mixed(long long threads, int tile_rows);
 // mode 0: fit + eval; 1: fit only into Inst::z (binary32), the refined path's first pass; 2:
 // refinement of Inst::z + eval.
 cudaError_t launch_tiled_mixed(const Inst *d_insts, int ninst, long long total_tiles, float *scratch, int tile_rows,
-                               long long threads, unsigned long long *counter, cudaStream_t stream, int mode);
+                               int sm_count, unsigned long long *counter, cudaStream_t stream, int mode);
 
 // Separate evaluation (spl_eval.cu): queries q_begin .. q_begin+mq-1 of each instance, explicit
 // (Inst::xq) or on the uniform grid, with the y'' in Inst::ypp; variant = spl_eval_variant; f32:

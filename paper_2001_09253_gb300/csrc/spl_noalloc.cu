@@ -86,9 +86,8 @@ extern "C" spl_status spl_fit_eval_noalloc(const double *x, const double *y, uin
   unsigned long long *counters = reinterpret_cast<unsigned long long *>(base + kStatusOff + 16);
   noalloc_prepare<<<1, 1, 0, st>>>(I, d_inst, I.status, counters);
   cudaError_t e = cudaGetLastError();
-  const long long threads = spl::threads_mixed(sms, I.ntiles);
-  if (e == cudaSuccess) e = spl::launch_fused_mixed(d_inst, 1, I.ntiles, threads, counters, st, true);
-  if (e == cudaSuccess) e = spl::launch_refine_mixed(d_inst, 1, I.ntiles, threads, counters + 1, st);
+  if (e == cudaSuccess) e = spl::launch_fused_mixed(d_inst, 1, I.ntiles, sms, counters, st, true);
+  if (e == cudaSuccess) e = spl::launch_refine_mixed(d_inst, 1, I.ntiles, sms, counters + 1, st);
   if (e != cudaSuccess) return SPL_ERR_CUDA;
   if (status_out) {
     unsigned bits = 0;

@@ -433,25 +433,25 @@ cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, 
     // stored y'': evaluation only
   } else if (lp.precision == SPL_PREC_F64) {
     e = spl::launch_fused_f64(insts, count, lp.total_tiles, reinterpret_cast<double *>(c->arena + d_ring_off),
-                              lp.tile_rows, lp.threads, counters, st);
+                              lp.tile_rows, c->sm_count, counters, st);
     if (launches) *launches += 1;
   } else if (lp.tiled_mixed) {
     float *scr = reinterpret_cast<float *>(c->arena + d_ring_off);
     if (lp.refine_steps == 0) {
-      e = spl::launch_tiled_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, lp.threads, counters, st, 0);
+      e = spl::launch_tiled_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, c->sm_count, counters, st, 0);
       if (launches) *launches += 1;
     } else {
-      e = spl::launch_tiled_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, lp.threads, counters, st, 1);
+      e = spl::launch_tiled_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, c->sm_count, counters, st, 1);
       if (e == cudaSuccess)
-        e = spl::launch_tiled_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, lp.threads, counters + 1, st, 2);
+        e = spl::launch_tiled_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, c->sm_count, counters + 1, st, 2);
       if (launches) *launches += 2;
     }
   } else if (lp.refine_steps == 0) {
-    e = spl::launch_fused_mixed(insts, count, lp.total_tiles, lp.threads, counters, st, false);
+    e = spl::launch_fused_mixed(insts, count, lp.total_tiles, c->sm_count, counters, st, false);
     if (launches) *launches += 1;
   } else {
-    e = spl::launch_fused_mixed(insts, count, lp.total_tiles, lp.threads, counters, st, true);
-    if (e == cudaSuccess) e = spl::launch_refine_mixed(insts, count, lp.total_tiles, lp.threads, counters + 1, st);
+    e = spl::launch_fused_mixed(insts, count, lp.total_tiles, c->sm_count, counters, st, true);
+    if (e == cudaSuccess) e = spl::launch_refine_mixed(insts, count, lp.total_tiles, c->sm_count, counters + 1, st);
     if (launches) *launches += 2;
   }
   if (e == cudaSuccess && lp.separate_eval && lp.total_queries > 0) {
