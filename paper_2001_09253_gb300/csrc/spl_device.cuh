@@ -71,6 +71,15 @@ __device__ __forceinline__ long long dkey(double v) {
   return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
 }
 
+// True for one element of each kPfBlock-byte aligned block of a stream walked one element at a time
+// (in either direction): a software prefetch per block instead of one per element, since every
+// prefetch instruction of a lane is a memory request of its own.
+constexpr unsigned kPfBlock = 32;
+template <typename T>
+__device__ __forceinline__ bool first_in_block(const T *p) {
+  return ((unsigned)(size_t)p & (kPfBlock - 1u)) < (unsigned)sizeof(T);
+}
+
 __device__ __forceinline__ bool finite64(double v) {
   return ((unsigned long long)__double_as_longlong(v) & 0x7FF0000000000000ULL) != 0x7FF0000000000000ULL;
 }

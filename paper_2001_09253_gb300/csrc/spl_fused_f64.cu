@@ -214,7 +214,10 @@ __device__ FwdOut tile_forward(const Inst &I, const TileRows &T, const Scratch64
     if (j <= n - 2) {
       const double x2 = F.xl, y2 = F.yl;
       if (j + 2 < n) {
-        if (j + 18 < n) { prefetch_l1(x + j + 18); prefetch_l1(y + j + 18); }
+        if (j + 18 < n) {
+          if (first_in_block(x + j + 18)) prefetch_l1(x + j + 18);
+          if (first_in_block(y + j + 18)) prefetch_l1(y + j + 18);
+        }
         F.xl = x[j + 2];
         F.yl = y[j + 2];
       }
@@ -367,7 +370,8 @@ __device__ void tile_backward_eval(const Inst &I, const TileRows &T, long long r
     if (row >= 0) {
       if (row >= 8) {
         prefetch_l1(&S.at(row - 8, 0)); prefetch_l1(&S.at(row - 8, 1)); prefetch_l1(&S.at(row - 8, 2));
-        prefetch_l1(x + s0 + row - 8); prefetch_l1(y + s0 + row - 8);
+        if (first_in_block(x + s0 + row - 8)) prefetch_l1(x + s0 + row - 8);
+        if (first_in_block(y + s0 + row - 8)) prefetch_l1(y + s0 + row - 8);
       }
       c_n = S.at(row, 0); d_n = S.at(row, 1); ih_n = S.at(row, 2);
       x_n = x[s0 + row]; y_n = y[s0 + row];

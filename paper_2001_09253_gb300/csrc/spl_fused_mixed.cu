@@ -230,7 +230,10 @@ __device__ void tile_mixed(const Inst &I, long long tile, const RingM &ring) {
         const double x2 = F.xa, y2 = F.ya;
         F.xa = F.xb; F.ya = F.yb;
         if (j + 3 < n) { F.xb = x[j + 3]; F.yb = y[j + 3]; }
-        if (j + 3 + kPrefetchM < n) { prefetch_l2m(x + j + 3 + kPrefetchM); prefetch_l2m(y + j + 3 + kPrefetchM); }
+        if (j + 3 + kPrefetchM < n) {
+          if (first_in_block(x + j + 3 + kPrefetchM)) prefetch_l2m(x + j + 3 + kPrefetchM);
+          if (first_in_block(y + j + 3 + kPrefetchM)) prefetch_l2m(y + j + 3 + kPrefetchM);
+        }
         if (owned) bad |= row_check(F.xn, F.yn, true, x2);
         const float hj = dif32_near(x2, F.xn);
         const float ihj = rcp32(hj);
@@ -345,8 +348,9 @@ __device__ void tile_refine(const Inst &I, long long tile, const RingM &ring) {
         const float z2 = F.za;
         if (j + 2 < n) { F.xa = x[j + 2]; F.ya = y[j + 2]; F.za = z[j + 2]; }
         if (j + 2 + kPrefetchM < n) {
-          prefetch_l2m(x + j + 2 + kPrefetchM); prefetch_l2m(y + j + 2 + kPrefetchM);
-          prefetch_l2m(z + j + 2 + kPrefetchM);
+          if (first_in_block(x + j + 2 + kPrefetchM)) prefetch_l2m(x + j + 2 + kPrefetchM);
+          if (first_in_block(y + j + 2 + kPrefetchM)) prefetch_l2m(y + j + 2 + kPrefetchM);
+          if (first_in_block(z + j + 2 + kPrefetchM)) prefetch_l2m(z + j + 2 + kPrefetchM);
         }
         const F2 hj = dif2(x2, F.xn);
         const float ihj = rcp32(hj.hi);
@@ -733,7 +737,10 @@ __device__ FwdOutT tile_forward_t(const Inst &I, const RowsT &T, const ScrT &S) 
       const double x2 = F.xa, y2 = F.ya;
       F.xa = F.xb; F.ya = F.yb;
       if (j + 3 < n) { F.xb = x[j + 3]; F.yb = y[j + 3]; }
-      if (j + 3 + kPrefetchM < n) { prefetch_l2m(x + j + 3 + kPrefetchM); prefetch_l2m(y + j + 3 + kPrefetchM); }
+      if (j + 3 + kPrefetchM < n) {
+        if (first_in_block(x + j + 3 + kPrefetchM)) prefetch_l2m(x + j + 3 + kPrefetchM);
+        if (first_in_block(y + j + 3 + kPrefetchM)) prefetch_l2m(y + j + 3 + kPrefetchM);
+      }
       if (owned) bad |= row_check(F.xn, F.yn, true, x2);
       const float hj = dif32_near(x2, F.xn);
       const float ihj = rcp32(hj);
@@ -851,8 +858,9 @@ __device__ FwdOutT tile_forward_rt(const Inst &I, const RowsT &T, const ScrT &S)
       const float z2 = F.za;
       if (j + 2 < n) { F.xa = x[j + 2]; F.ya = y[j + 2]; F.za = z[j + 2]; }
       if (j + 2 + kPrefetchM < n) {
-        prefetch_l2m(x + j + 2 + kPrefetchM); prefetch_l2m(y + j + 2 + kPrefetchM);
-        prefetch_l2m(z + j + 2 + kPrefetchM);
+        if (first_in_block(x + j + 2 + kPrefetchM)) prefetch_l2m(x + j + 2 + kPrefetchM);
+        if (first_in_block(y + j + 2 + kPrefetchM)) prefetch_l2m(y + j + 2 + kPrefetchM);
+        if (first_in_block(z + j + 2 + kPrefetchM)) prefetch_l2m(z + j + 2 + kPrefetchM);
       }
       const F2 hj = dif2(x2, F.xn);
       const float ihj = rcp32(hj.hi);
@@ -967,7 +975,8 @@ __device__ void tile_bwd_eval_t(const Inst &I, const RowsT &T, long long rlast, 
     if (row >= 0) {
       if (row >= 8) {
         prefetch_l1m(&S.at(row - 8, 0));
-        prefetch_l1m(x + s0 + row - 8); prefetch_l1m(y + s0 + row - 8);
+        if (first_in_block(x + s0 + row - 8)) prefetch_l1m(x + s0 + row - 8);
+        if (first_in_block(y + s0 + row - 8)) prefetch_l1m(y + s0 + row - 8);
       }
       c_n = S.at(row, 0); d_n = S.at(row, 1);
       x_n = x[s0 + row]; y_n = y[s0 + row];
