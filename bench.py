@@ -383,17 +383,24 @@ class Runner:
         b.close()
         return res, (sizes, off, X, Y, P, Q)
 
-    def _timed_submit(self, plan, m, yq, jq=None, xq=None, ypp_in=None, x=None, y=None, ypp_out=None):
-        """One request bracketed by CUDA events on the context's stream; returns device ms."""
+    def _timed_submit(self, plan, m, yq, jq=None, xq=None, ypp_in=None, x=None, y=None, ypp_out=None,
+                      detail=False):
+        """One request bracketed by CUDA events on the context's stream; returns device ms (with
+        detail: also the library's own device time of the request, from its first copy to its
+        last operation, and the host wall time of submit + wait)."""
         torch, spl = self.torch, self.spl
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0 = time.perf_counter()
         e0.record(self.stream)
         t = self.ctx.submit(plan, self.x if x is None else x, self.y if y is None else y, spl.NATURAL,
                             spl.NATURAL, m, ypp_out, yq, jq, xq=xq, ypp_in=ypp_in)
         e1.record(self.stream)
-        s, _ = self.ctx.wait(t, 120.0)
+        s, res = self.ctx.wait(t, 120.0)
         assert s == spl.OK, spl.status_str(s)
         e1.synchronize()
+        wall = (time.perf_counter() - w0) * 1e3
+        if detail:
+            return e0.elapsed_time(e1), float(res.device_ms), wall
         return e0.elapsed_time(e1)
 
     def eval_variants(self, reps=None):
@@ -459,6 +466,7 @@ class Runner:
         yq = torch.empty(nmax, dtype=torch.float64, device=self.dev)
         names = ["fit+eval (fused)", "eval orig", "eval noinv", "eval vol"]
         ns = {k: [] for k in names}
+        wall = {k: [] for k in names}
         for i, n in enumerate(sizes):
             n = int(n)
             with torch.cuda.stream(self.stream):
@@ -469,10 +477,12 @@ class Runner:
             xs, ys = X[:n], Y[:n]
             for k in rng.permutation(4):
                 if k == 0:
-                    ms = self._timed_submit(fused, n, yq[:n], x=xs, y=ys, ypp_out=ypp[:n])
+                    _, ms, wl = self._timed_submit(fused, n, yq[:n], x=xs, y=ys, ypp_out=ypp[:n], detail=True)
                 else:
-                    ms = self._timed_submit(evals[k - 1], n, yq[:n], ypp_in=ypp[:n], x=xs, y=ys)
+                    _, ms, wl = self._timed_submit(evals[k - 1], n, yq[:n], ypp_in=ypp[:n], x=xs, y=ys,
+                                                   detail=True)
                 ns[names[k]].append(ms * 1e6 / n)
+                wall[names[k]].append(wl * 1e6 / n)
         sizes_f = sizes.astype(np.float64)
 
         def dist(v, mask=None):
@@ -489,10 +499,15 @@ class Runner:
 
         bins = {"n<1e3": sizes_f < 1e3, "1e3<=n<1e5": (sizes_f >= 1e3) & (sizes_f < 1e5), "n>=1e5": sizes_f >= 1e5}
         out = {k: {"all": dist(v), **{b: dist(v, msk) for b, msk in bins.items()}} for k, v in ns.items()}
+        out_wall = {k: {b: dist(v, msk) for b, msk in bins.items()} for k, v in wall.items()}
         return {"workload": "the paper's size schedule n = round((r (1024 - 2) + 2)^2), r on 524,288 even "
                             "points, shuffled; %d seeded draws (n from %d to %d), one new curve per draw, "
                             "routines in shuffled order" % (draws, int(sizes.min()), nmax),
-                "unit": "ns per point", "routines": out}
+                "unit": "ns per point",
+                "timing": "device: the library's CUDA events around one request (descriptor copy, status "
+                          "reset, kernels, status copy back); wall: host clock around the Python submit and "
+                          "wait (includes the binding's marshalling and the completion poll)",
+                "routines": out, "wall": out_wall}
 
 
 def serving(r, pool_count=512, seed=3, lo=1e2, hi=1e6, rate=20000.0, warm_s=1.0, run_s=8.0):

@@ -197,6 +197,16 @@ int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points, bool 
   // several instances: short tiles, fetched dynamically, balance instances of uneven sizes
   // (one wave of long tiles waits on the longest; 4,096 log-uniform instances run ~1.4x faster)
   if (count > 1) return 128;
+  // One instance too small to keep the GPU's FP64 (or binary32) pipes busy with long tiles:
+  // its time is then one tile's serial dependency chain (halo, tile, back-substitution start,
+  // one thread), so short tiles spread it over more warps.  Measured on GB300 for n = 1e3..1e5:
+  // 16-row tiles halve the FP64 time (0.36-0.41 -> 0.17 ms) and cut the binary32 time 3x; past
+  // a few 1e5 points (FP64) the halo work that every short tile repeats outweighs the shorter
+  // chain, and from ~1e6 the grouped long tiles below win.
+  const uint64_t upto16 = (uint64_t)c->sm_count * (precision == SPL_PREC_F64 ? 2000ull : 13000ull);
+  const uint64_t upto32 = (uint64_t)c->sm_count * (precision == SPL_PREC_F64 ? 8000ull : 0ull);
+  if (total_points <= upto16) return 16;
+  if (total_points <= upto32) return 32;
   const long long per_sm = precision == SPL_PREC_F64 ? spl::f64_threads_per_sm()
                            : tiled_mixed             ? spl::tiled_mixed_threads_per_sm()
                                                      : spl::mixed_threads_per_sm();
@@ -731,14 +741,16 @@ spl_status spl_poll(spl_ctx *c, uint64_t ticket, spl_result *res) {
 }
 
 spl_status spl_wait(spl_ctx *c, uint64_t ticket, uint64_t timeout_ns, spl_result *res) {
+  // Polls with yields for the first 2 ms (a sleep overshoots by tens of microseconds, which a
+  // request of a few hundred microseconds would see), then sleeps between polls.
   const double t0 = now_ms();
   const double limit = (double)timeout_ns * 1e-6;
-  int spins = 0;
   for (;;) {
     spl_status s = spl_poll(c, ticket, res);
     if (s != SPL_PENDING) return s;
-    if (now_ms() - t0 >= limit) return SPL_ERR_TIMEOUT;
-    if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    const double waited = now_ms() - t0;
+    if (waited >= limit) return SPL_ERR_TIMEOUT;
+    if (waited > 2.0) std::this_thread::sleep_for(std::chrono::microseconds(20));
     else std::this_thread::yield();
   }
 }
@@ -822,13 +834,13 @@ spl_status spl_batch_wait(spl_batch *b, uint64_t timeout_ns, int32_t *statuses) 
   if (!b->launched) return SPL_ERR_STATE;
   const double t0 = now_ms();
   const double limit = (double)timeout_ns * 1e-6;
-  int spins = 0;
-  for (;;) {
+  for (;;) {  // the polling of spl_wait
     cudaError_t q = cudaEventQuery(b->ev_done);
     if (q == cudaSuccess) break;
     if (q != cudaErrorNotReady) return SPL_ERR_CUDA;
-    if (now_ms() - t0 >= limit) return SPL_ERR_TIMEOUT;
-    if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    const double waited = now_ms() - t0;
+    if (waited >= limit) return SPL_ERR_TIMEOUT;
+    if (waited > 2.0) std::this_thread::sleep_for(std::chrono::microseconds(20));
     else std::this_thread::yield();
   }
   spl_status worst = SPL_OK;
