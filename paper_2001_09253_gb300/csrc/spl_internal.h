@@ -57,6 +57,16 @@ size_t scratch_bytes_tiled_mixed(long long threads, int tile_rows);
 cudaError_t launch_tiled_mixed(const Inst *d_insts, int ninst, long long total_tiles, float *scratch, int tile_rows,
                                int sm_count, unsigned long long *counter, cudaStream_t stream, int mode);
 
+// Warp-cooperative binary32 fit + evaluation without refinement (spl_mixed_scan.cu): one warp per
+// tile of scan_mixed_tile_rows rows (a multiple of 32), per-warp scratch of
+// scratch_bytes_scan_mixed bytes.
+int scan_mixed_threads_per_sm();
+int scan_mixed_tile_rows(long long total_points, int sm_count, int count);
+long long threads_scan_mixed(int sm_count, long long total_tiles);
+size_t scratch_bytes_scan_mixed(long long threads, int tile_rows);
+cudaError_t launch_scan_mixed(const Inst *d_insts, int ninst, long long total_tiles, float *scratch, int tile_rows,
+                              int sm_count, unsigned long long *counter, cudaStream_t stream, int mode);
+
 // Separate evaluation (spl_eval.cu): queries q_begin .. q_begin+mq-1 of each instance, explicit
 // (Inst::xq) or on the uniform grid, with the y'' in Inst::ypp; variant = spl_eval_variant; f32:
 // the binary32 form of the mixed-precision plans.

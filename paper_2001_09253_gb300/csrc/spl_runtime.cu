@@ -242,6 +242,7 @@ struct LaunchPlan {
   uint64_t ring_bytes = 0;
   bool fit = true;             // run the fit kernel(s)
   bool tiled_mixed = false;    // binary32 paths: the tiled kernel (with refinement: two launches)
+  bool scan_mixed = false;     // binary32 without refinement: the warp-cooperative kernel
   bool separate_eval = false;  // evaluate with the separate kernel (explicit queries, stored y'')
   int eval_variant = 0;
   long long total_queries = 0;
@@ -295,6 +296,13 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
     }
     lp.tiled_mixed = 2 * grouped_points >= total_points;
     L = lp.tiled_mixed ? Lt : (p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, false, count));
+    // these launches go to the warp-cooperative kernel (its own tiles: multiples of 32 rows,
+    // about two per resident warp)
+    if (lp.tiled_mixed) {
+      lp.tiled_mixed = false;
+      lp.scan_mixed = true;
+      L = p->tile_rows > 0 ? (p->tile_rows + 31) / 32 * 32 : spl::scan_mixed_tile_rows((long long)total_points, c->sm_count, (int)count);
+    }
   } else {
     L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, false, count);
   }
@@ -339,11 +347,12 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
     }
   }
   lp.total_tiles = tiles;
-  lp.threads = threads_for(c, p->precision, tiles, lp.tiled_mixed);
+  lp.threads = lp.scan_mixed ? spl::threads_scan_mixed(c->sm_count, tiles) : threads_for(c, p->precision, tiles, lp.tiled_mixed);
   lp.tile_rows = L;
   lp.ring_bytes = !lp.fit                           ? 0
                   : p->precision == SPL_PREC_F64   ? spl::ring_bytes_f64(lp.threads, L)
                   : lp.tiled_mixed                 ? spl::scratch_bytes_tiled_mixed(lp.threads, L)
+                  : lp.scan_mixed                  ? spl::scratch_bytes_scan_mixed(lp.threads, L)
                                                    : 0;
 
   // footprint check against the whole budget first
@@ -445,6 +454,17 @@ cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, 
     e = spl::launch_fused_f64(insts, count, lp.total_tiles, reinterpret_cast<double *>(c->arena + d_ring_off),
                               lp.tile_rows, c->sm_count, counters, st);
     if (launches) *launches += 1;
+  } else if (lp.scan_mixed) {
+    float *scr = reinterpret_cast<float *>(c->arena + d_ring_off);
+    if (lp.refine_steps == 0) {
+      e = spl::launch_scan_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, c->sm_count, counters, st, 0);
+      if (launches) *launches += 1;
+    } else {
+      e = spl::launch_scan_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, c->sm_count, counters, st, 1);
+      if (e == cudaSuccess)
+        e = spl::launch_scan_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, c->sm_count, counters + 1, st, 2);
+      if (launches) *launches += 2;
+    }
   } else if (lp.tiled_mixed) {
     float *scr = reinterpret_cast<float *>(c->arena + d_ring_off);
     if (lp.refine_steps == 0) {

@@ -145,6 +145,44 @@ def test_small_same_binade_difference(lib):
     assert not lib.t_diff_small_f32(1e300, 1e300 * (1 - 1e-15), ctypes.byref(o))
 
 
+def test_near_difference_split_fma(lib):
+    """The same-binade route with the split ulp count and one FMA: exact rounding of b - a for
+    both signs and both orders, up to 2^39 ulps apart; wider gaps and other binades refused."""
+    lib.t_diff_near_f32.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_float)]
+    lib.t_diff_near_f32.restype = ctypes.c_int
+    rng = np.random.default_rng(9)
+    hits = 0
+    for _ in range(8000):
+        a = rng.normal() * 10.0 ** rng.integers(-20, 20)
+        b = a + abs(a) * rng.random() * 10.0 ** rng.integers(-16, -3) * (1 if rng.random() < 0.5 else -1)
+        if rng.random() < 0.1:
+            b = a
+        out = ctypes.c_float()
+        if not lib.t_diff_near_f32(float(b), float(a), ctypes.byref(out)):
+            continue
+        hits += 1
+        exact = Fraction(float(b)) - Fraction(float(a))
+        assert out.value == rn32(exact), (a, b)
+        if exact == 0:
+            assert math.copysign(1.0, out.value) == 1.0
+    assert hits > 4000
+    # the split boundary: D = 2^39 - 1 accepted, 2^39 refused; ties of the single rounding
+    one = 1.0
+    ulp = 2.0 ** -52
+    o = ctypes.c_float()
+    b = one + (2 ** 39 - 1) * ulp
+    assert lib.t_diff_near_f32(b, one, ctypes.byref(o)) and o.value == rn32(Fraction(b) - 1)
+    assert not lib.t_diff_near_f32(one + 2 ** 39 * ulp, one, ctypes.byref(o))
+    for d in ((1 << 24) + 1, (1 << 24) + 3, (1 << 30) + (1 << 6), (1 << 30) + (3 << 6), (1 << 38) + (1 << 14)):
+        b = one + d * ulp
+        assert lib.t_diff_near_f32(b, one, ctypes.byref(o)) and o.value == rn32(Fraction(b) - 1), d
+        assert lib.t_diff_near_f32(one, b, ctypes.byref(o)) and o.value == rn32(1 - Fraction(b)), d
+        assert lib.t_diff_near_f32(-b, -one, ctypes.byref(o)) and o.value == rn32(Fraction(-b) + 1), d
+    assert not lib.t_diff_near_f32(2.0, 1.9, ctypes.byref(o))
+    assert not lib.t_diff_near_f32(1e300, 1e300 * (1 - 1e-15), ctypes.byref(o))
+    assert not lib.t_diff_near_f32(1e-300, 1.5e-300, ctypes.byref(o))
+
+
 def test_diff_far_apart_and_signs(lib):
     rng = np.random.default_rng(1)
     for _ in range(2000):
