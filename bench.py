@@ -53,8 +53,8 @@ TOL = {"f64": 1e-12, "mixed": 1e-5}
 CSRC = os.path.join(ROOT, "paper_2001_09253_gb300", "csrc")
 PROFILES = {
     "f64": (os.path.join(ROOT, "profiles", "fused_f64_n1e7.md"), ["spl_fused_f64.cu", "spl_device.cuh"]),
-    "mixed": (os.path.join(ROOT, "profiles", "fused_mixed_n1e7.md"),
-              ["spl_fused_mixed.cu", "spl_device.cuh", "spl_numeric.h"]),
+    "mixed": (os.path.join(ROOT, "profiles", "mixed_scan_n1e7.md"),
+              ["spl_mixed_scan.cu", "spl_mixed_math.cuh", "spl_device.cuh", "spl_numeric.h"]),
 }
 
 

@@ -45,21 +45,10 @@ cudaError_t launch_refine_mixed(const Inst *d_insts, int ninst, long long total_
 cudaError_t launch_serve(const ServeArgs &args, int sm_count, cudaStream_t stream);
 int mixed_threads_per_sm();  // threads of one mixed-kernel CTA (one CTA per SM)
 
-// Tiled binary32 fit + evaluation without refinement (spl_fused_mixed.cu, mixed_tiled_kernel):
-// grouped tiles as the FP64 kernel's, per-warp scratch of scratch_bytes_tiled_mixed bytes.
-int tiled_mixed_overhang_rows();
-int tiled_mixed_threads_per_sm();  // one CTA per SM
-long long threads_tiled_mixed(int sm_count, long long total_tiles);
-int tiled_mixed_lane0_short_rows();
-size_t scratch_bytes_tiled_mixed(long long threads, int tile_rows);
-// mode 0: fit + eval; 1: fit only into Inst::z (binary32), the refined path's first pass; 2:
-// refinement of Inst::z + eval.
-cudaError_t launch_tiled_mixed(const Inst *d_insts, int ninst, long long total_tiles, float *scratch, int tile_rows,
-                               int sm_count, unsigned long long *counter, cudaStream_t stream, int mode);
-
-// Warp-cooperative binary32 fit + evaluation without refinement (spl_mixed_scan.cu): one warp per
-// tile of scan_mixed_tile_rows rows (a multiple of 32), per-warp scratch of
-// scratch_bytes_scan_mixed bytes.
+// Warp-cooperative binary32 fit + evaluation (spl_mixed_scan.cu): one warp per tile of
+// scan_mixed_tile_rows rows (a multiple of 32), per-warp scratch of scratch_bytes_scan_mixed
+// bytes.  mode 0: fit + eval; 1: fit only into Inst::z (binary32), the refined path's first
+// pass; 2: refinement of Inst::z + eval.
 int scan_mixed_threads_per_sm();
 int scan_mixed_tile_rows(long long total_points, int sm_count, int count);
 long long threads_scan_mixed(int sm_count, long long total_tiles);

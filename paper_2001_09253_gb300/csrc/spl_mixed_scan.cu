@@ -1,6 +1,6 @@
 // Warp-cooperative binary32 fit + evaluation ("scan" form of the mixed-precision path).
 //
-// The same system and arithmetic as the tiled binary32 kernel (tridiagonal system of eq.
+// The same system and arithmetic as the binary32 ring kernel (spl_fused_mixed.cu: tridiagonal system of eq.
 // (init_val) with the end rows of "Start and End Derivatives", Thomas recurrences of
 // "Implementation", the one-division form of "Fast Interpolation" on the grid of "Curve
 // Interpolation"; binary32 arithmetic on exact, once-rounded differences of the binary64

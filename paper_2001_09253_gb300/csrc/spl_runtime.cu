@@ -180,20 +180,21 @@ spl_status check_request(const spl_plan *plan, const spl_request *r) {
   return SPL_OK;
 }
 
-// Launch geometry: persistent CTAs, one thread per tile, tiles fetched dynamically.  The FP64
-// kernel runs 448 threads per SM (its measured best between FP64-pipe latency hiding and the
-// per-tile work more tiles bring); the mixed kernels 512 (four warps per sub-partition hide
-// the latency of their loads).
-long long threads_for(const spl_ctx *c, int precision, long long total_tiles, bool tiled_mixed) {
+// Launch geometry: persistent CTAs, tiles fetched dynamically.  The FP64 kernel runs 448
+// threads per SM, one tile per thread (its measured best between FP64-pipe latency hiding and
+// the per-tile work more tiles bring); the binary32 ring kernel 512, one tile per thread; the
+// warp-cooperative binary32 kernel 1024, one tile per warp.
+long long threads_for(const spl_ctx *c, int precision, long long total_tiles, bool scan_mixed) {
   return precision == SPL_PREC_F64 ? spl::threads_f64(c->sm_count, total_tiles)
-         : tiled_mixed             ? spl::threads_tiled_mixed(c->sm_count, total_tiles)
+         : scan_mixed              ? spl::threads_scan_mixed(c->sm_count, total_tiles)
                                    : spl::threads_mixed(c->sm_count, total_tiles);
 }
 
-// Tile length so that one instance of total_points fills every thread of one wave; never
-// shorter than a few halos.  FP64 tiles come in warp groups of 32L - overhang - lane0_short
-// rows, so L is chosen for the group count to match the warps.
-int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points, bool tiled_mixed, uint32_t count) {
+// Tile length (one tile per thread) for the FP64 and binary32 ring kernels, so that one instance
+// of total_points fills every thread of one wave; never shorter than a few halos.  FP64 tiles
+// come in warp groups of 32L - overhang - lane0_short rows, so L is chosen for the group count to
+// match the warps.
+int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points, uint32_t count) {
   // several instances: short tiles, fetched dynamically, balance instances of uneven sizes
   // (one wave of long tiles waits on the longest; 4,096 log-uniform instances run ~1.4x faster)
   if (count > 1) return 128;
@@ -207,23 +208,23 @@ int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points, bool 
   const uint64_t upto32 = (uint64_t)c->sm_count * (precision == SPL_PREC_F64 ? 8000ull : 0ull);
   if (total_points <= upto16) return 16;
   if (total_points <= upto32) return 32;
-  const long long per_sm = precision == SPL_PREC_F64 ? spl::f64_threads_per_sm()
-                           : tiled_mixed             ? spl::tiled_mixed_threads_per_sm()
-                                                     : spl::mixed_threads_per_sm();
+  const long long per_sm = precision == SPL_PREC_F64 ? spl::f64_threads_per_sm() : spl::mixed_threads_per_sm();
   const long long target = (long long)c->sm_count * per_sm;
   long long L = (long long)((total_points + target - 1) / target);
-  if (precision == SPL_PREC_F64 || tiled_mixed) {
+  if (precision == SPL_PREC_F64) {
     const long long warps = std::max<long long>(target / 32, 1);
     const long long per_warp = (long long)((total_points + warps - 1) / warps);
-    const long long extra = precision == SPL_PREC_F64
-                                ? spl::overhang_rows_f64() + spl::lane0_short_rows_f64()
-                                : spl::tiled_mixed_overhang_rows() + spl::tiled_mixed_lane0_short_rows();
-    L = (per_warp + extra + 31) / 32;
+    L = (per_warp + spl::overhang_rows_f64() + spl::lane0_short_rows_f64() + 31) / 32;
   }
   L = std::max<long long>(L, 128);
   L = std::min<long long>(L, 1 << 20);
   return (int)L;
 }
+
+// Binary32 launches go to the warp-cooperative kernel when at least half of their points lie in
+// instances of this many rows or more; to the ring kernel (one thread per tile) otherwise: many
+// small instances, of which one warp each would leave most lanes without rows.
+constexpr uint64_t kScanMinRows = 1024;
 
 struct Staged {
   std::vector<Block> dev;
@@ -241,8 +242,7 @@ struct LaunchPlan {
   long long threads = 0;
   uint64_t ring_bytes = 0;
   bool fit = true;             // run the fit kernel(s)
-  bool tiled_mixed = false;    // binary32 paths: the tiled kernel (with refinement: two launches)
-  bool scan_mixed = false;     // binary32 without refinement: the warp-cooperative kernel
+  bool scan_mixed = false;     // binary32: the warp-cooperative kernel (with refinement: two launches)
   bool separate_eval = false;  // evaluate with the separate kernel (explicit queries, stored y'')
   int eval_variant = 0;
   long long total_queries = 0;
@@ -281,43 +281,29 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
   lp.refine_steps = p->precision == SPL_PREC_F64 ? 0 : p->refine_steps;
   lp.fit = reqs[0].ypp_in == nullptr;
   lp.separate_eval = p->query_mode == SPL_QUERY_EXPLICIT || !lp.fit;
-  // binary32 paths: the tiled kernel when most of the launch's points sit in instances its grouped
-  // geometry serves with little padding (32-tile groups), the shared-memory ring kernels otherwise
-  // (many small instances, where every tile runs its own halo either way)
-  lp.tiled_mixed = false;
+  lp.scan_mixed = false;
   int L;
   if (p->precision == SPL_PREC_F32_REFINE) {
-    const int Lt = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, true, count);
-    const long long G = 32LL * Lt - spl::tiled_mixed_overhang_rows() - spl::tiled_mixed_lane0_short_rows();
-    uint64_t grouped_points = 0;
-    for (uint32_t i = 0; i < count && G > 0; ++i) {
-      const long long n = (long long)reqs[i].n, plain = (n + Lt - 1) / Lt, grouped = 32 * ((n + G - 1) / G);
-      if (plain >= 32 && 8 * grouped <= 9 * plain) grouped_points += reqs[i].n;
-    }
-    lp.tiled_mixed = 2 * grouped_points >= total_points;
-    L = lp.tiled_mixed ? Lt : (p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, false, count));
-    // these launches go to the warp-cooperative kernel (its own tiles: multiples of 32 rows,
-    // about two per resident warp)
-    if (lp.tiled_mixed) {
-      lp.tiled_mixed = false;
-      lp.scan_mixed = true;
-      L = p->tile_rows > 0 ? (p->tile_rows + 31) / 32 * 32 : spl::scan_mixed_tile_rows((long long)total_points, c->sm_count, (int)count);
-    }
+    uint64_t big = 0;
+    for (uint32_t i = 0; i < count; ++i)
+      if (reqs[i].n >= kScanMinRows) big += reqs[i].n;
+    lp.scan_mixed = 2 * big >= total_points;
+    if (lp.scan_mixed)  // tiles of whole 32-row chunks
+      L = p->tile_rows > 0 ? (p->tile_rows + 31) / 32 * 32
+                           : spl::scan_mixed_tile_rows((long long)total_points, c->sm_count, (int)count);
+    else
+      L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, count);
   } else {
-    L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, false, count);
+    L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, count);
   }
   lp.eval_variant = p->eval_variant;
   lp.insts.resize(count);
-  // Instances of 32 tiles or more of the FP64 and tiled binary32 kernels use the grouped
-  // geometry: their tiles start on a warp boundary, and each warp's 32 tiles cover
-  // 32L - overhang - lane0_short rows (the lanes take the rows past their tile from the next
-  // lane and, but for the first, their start state from the previous one)
-  const long long ov = p->precision == SPL_PREC_F64 ? spl::overhang_rows_f64()
-                       : lp.tiled_mixed          ? spl::tiled_mixed_overhang_rows()
-                                                 : 0;
-  const long long l0s = p->precision == SPL_PREC_F64 ? spl::lane0_short_rows_f64()
-                        : lp.tiled_mixed          ? spl::tiled_mixed_lane0_short_rows()
-                                                  : 0;
+  // Instances of 32 tiles or more of the FP64 kernel use the grouped geometry: their tiles
+  // start on a warp boundary, and each warp's 32 tiles cover 32L - overhang - lane0_short rows
+  // (the lanes take the rows past their tile from the next lane and, but for the first, their
+  // start state from the previous one)
+  const long long ov = p->precision == SPL_PREC_F64 ? spl::overhang_rows_f64() : 0;
+  const long long l0s = p->precision == SPL_PREC_F64 ? spl::lane0_short_rows_f64() : 0;
   long long tiles = 0;
   for (uint32_t i = 0; i < count; ++i) {
     const spl_request &r = reqs[i];
@@ -347,11 +333,10 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
     }
   }
   lp.total_tiles = tiles;
-  lp.threads = lp.scan_mixed ? spl::threads_scan_mixed(c->sm_count, tiles) : threads_for(c, p->precision, tiles, lp.tiled_mixed);
+  lp.threads = threads_for(c, p->precision, tiles, lp.scan_mixed);
   lp.tile_rows = L;
   lp.ring_bytes = !lp.fit                           ? 0
                   : p->precision == SPL_PREC_F64   ? spl::ring_bytes_f64(lp.threads, L)
-                  : lp.tiled_mixed                 ? spl::scratch_bytes_tiled_mixed(lp.threads, L)
                   : lp.scan_mixed                  ? spl::scratch_bytes_scan_mixed(lp.threads, L)
                                                    : 0;
 
@@ -463,17 +448,6 @@ cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, 
       e = spl::launch_scan_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, c->sm_count, counters, st, 1);
       if (e == cudaSuccess)
         e = spl::launch_scan_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, c->sm_count, counters + 1, st, 2);
-      if (launches) *launches += 2;
-    }
-  } else if (lp.tiled_mixed) {
-    float *scr = reinterpret_cast<float *>(c->arena + d_ring_off);
-    if (lp.refine_steps == 0) {
-      e = spl::launch_tiled_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, c->sm_count, counters, st, 0);
-      if (launches) *launches += 1;
-    } else {
-      e = spl::launch_tiled_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, c->sm_count, counters, st, 1);
-      if (e == cudaSuccess)
-        e = spl::launch_tiled_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, c->sm_count, counters + 1, st, 2);
       if (launches) *launches += 2;
     }
   } else if (lp.refine_steps == 0) {

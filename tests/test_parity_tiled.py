@@ -1,23 +1,27 @@
-"""GPU parity of the grouped, chained tile decomposition (FP64 kernel and tiled binary32
-kernel) on inputs sized so that their tiles form several 32-tile warp groups with a ragged last
-group: every lane but the first of a group starts from the exact c' and a corrected d', every
-lane but the last takes its back-substitution start from the next lane's rows.
+"""GPU parity of the two tile decompositions of long instances.
 
-Group sizes for the forced tile lengths: FP64, L = 200 -> a group covers 32 L - 48 - 56 = 6296
-rows; binary32, L = 150 -> 32 L - 24 - 48 = 4728 rows.  The sizes below give 7 and 9 groups
-whose padding stays under the 1/8 the runtime allows, so the grouped geometry is used."""
+FP64 kernel, grouped and chained tiles: every lane but the first of a warp group starts from
+the exact c' and a corrected d', every lane but the last takes its back-substitution start from
+the next lane's rows.  Group size for the forced tile length L = 200: 32 L - 48 - 56 = 6296
+rows; the size below gives 7 groups, the last one ragged, with padding under the 1/8 the runtime
+allows, so the grouped geometry is used.
+
+Binary32 warp-cooperative kernel: a warp solves one tile 32 rows at a time (warp scans for the
+recurrences, lane-parallel queries); tiles of L rows (a multiple of 32) start their forward sweep
+64 rows early and their back substitution 32 rows past their end.  The sizes below give many
+tiles with a ragged last tile and ragged last chunk."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2001_09253_gb300 import spl, synth
-from parity_util import TOL_F64, TOL_MIXED, check_instance, run_gpu
+from parity_util import TOL_F64, TOL_MIXED, check_instance, run_gpu, ypp_error, yq_error
 
 pytestmark = pytest.mark.gpu
 
 NAT = spl.NATURAL
 N64, L64 = 6296 * 7 - 1000, 200
-N32, L32 = 4728 * 9 - 500, 150
+N32, L32 = 256 * 37 + 19, 256
 
 
 @pytest.fixture(scope="module")
@@ -28,11 +32,10 @@ def ctx():
 
 
 def test_group_sizes_are_grouped():
-    """The sizes above meet the runtime's grouping rule (32-tile groups, padding <= 1/8)."""
-    for n, L, extra in ((N64, L64, 48 + 56), (N32, L32, 24 + 48)):
-        plain = -(-n // L)
-        groups = -(-n // (32 * L - extra))
-        assert plain >= 32 and 8 * 32 * groups <= 9 * plain and groups >= 5
+    """The FP64 size above meets the runtime's grouping rule (32-tile groups, padding <= 1/8)."""
+    plain = -(-N64 // L64)
+    groups = -(-N64 // (32 * L64 - 48 - 56))
+    assert plain >= 32 and 8 * 32 * groups <= 9 * plain and groups >= 5
 
 
 @pytest.mark.parametrize("bc", [(NAT, NAT), (-1.0, 1.0), (NAT, 0.25)])
@@ -52,37 +55,34 @@ def test_fp64_grouped_adversarial(ctx):
 
 
 @pytest.mark.parametrize("refine", [0, 1])
-@pytest.mark.parametrize("bc", [(NAT, NAT), (-1.0, 1.0)])
-def test_mixed_grouped_chained(ctx, refine, bc):
+@pytest.mark.parametrize("bc", [(NAT, NAT), (-1.0, 1.0), (NAT, 0.25)])
+def test_mixed_warp_tiles(ctx, refine, bc):
     x, y = synth.curve(72, N32)
     plan = ctx.plan(N32, spl.PREC_F32_REFINE, refine_steps=refine, tile_rows=L32)
-    for m in (N32, 2 * N32 + 3):
+    for m in (N32, 2 * N32 + 3, 77, 2):
         check_instance(ctx, plan, x, y, bc[0], bc[1], m, tol=TOL_MIXED)
 
 
 @pytest.mark.parametrize("refine", [0, 1])
-def test_mixed_grouped_adversarial(ctx, refine):
+def test_mixed_warp_tiles_adversarial(ctx, refine):
     x, y = synth.curve_adversarial(3, N32, decades=6)
     plan = ctx.plan(N32, spl.PREC_F32_REFINE, refine_steps=refine, tile_rows=L32)
     ref = oracle.fit_eval(x, y, NAT, NAT, N32)
     st, ypp, yq, jq = run_gpu(ctx, plan, x, y, NAT, NAT, N32)
     assert st == 0
     assert np.array_equal(jq.astype(np.int64), ref["jq"])
-    from parity_util import ypp_error, yq_error
     assert ypp_error(ypp, ref["ypp"]) <= TOL_MIXED
     assert yq_error(x, y, ref["ypp"], ref["jq"], yq, ref["yq"]) <= TOL_MIXED
     if refine:  # the refinement brings y'' to FP64 accuracy
         assert ypp_error(ypp, ref["ypp"]) <= 1e-8
 
 
-@pytest.mark.parametrize("precision,n,L", [(spl.PREC_F64, N64, L64), (spl.PREC_F32_REFINE, N32, L32)])
-def test_errors_inside_a_chained_tile(ctx, precision, n, L):
-    """Input errors in the middle of a chained lane's tile (group 2, lane 5) are reported."""
+@pytest.mark.parametrize("precision,n,L,row", [(spl.PREC_F64, N64, L64, 2 * (32 * L64 - 104) + 5 * L64 - 56 + L64 // 2),
+                                               (spl.PREC_F32_REFINE, N32, L32, 5 * L32 + 77)])
+def test_errors_inside_a_tile(ctx, precision, n, L, row):
+    """Input errors in the middle of a tile (FP64: group 2, lane 5; binary32: tile 5) are reported."""
     x, y = synth.curve(73, n)
     plan = ctx.plan(n, precision, tile_rows=L)
-    extra = 48 + 56 if precision == spl.PREC_F64 else 24 + 48
-    G = 32 * L - extra
-    row = 2 * G + 5 * L - (56 if precision == spl.PREC_F64 else 48) + L // 2
     bad_y = y.copy()
     bad_y[row] = np.nan
     st, _, _, _ = run_gpu(ctx, plan, x, bad_y, NAT, NAT, n)
@@ -93,15 +93,28 @@ def test_errors_inside_a_chained_tile(ctx, precision, n, L):
     assert st == spl.ERR_NOT_INCREASING
 
 
-@pytest.mark.parametrize("precision,L,extra,tol", [(spl.PREC_F64, 128, 48 + 56, TOL_F64),
-                                                   (spl.PREC_F32_REFINE, 96, 24 + 48, TOL_MIXED)])
-def test_group_boundaries_sweep(ctx, precision, L, extra, tol):
-    """Sizes around whole groups (exactly k groups, one row more or less, a lone row past a
+def test_fp64_group_boundaries_sweep(ctx):
+    """Sizes around whole FP64 groups (exactly k groups, one row more or less, a lone row past a
     group, the last lane's tile cut short), seeded, both end conditions."""
-    G = 32 * L - extra
+    L = 128
+    G = 32 * L - 104
     sizes = sorted({k * G + d for k in (1, 2, 3) for d in (-1, 0, 1, 2, 17, -L + 1, L - 1)})
-    plan = ctx.plan(4 * G, precision, tile_rows=L)
+    plan = ctx.plan(4 * G, spl.PREC_F64, tile_rows=L)
     for i, n in enumerate(sizes):
         x, y = synth.curve(80 + i, n)
         bc = (NAT, NAT) if i % 2 else (0.75, -1.25)
-        check_instance(ctx, plan, x, y, bc[0], bc[1], n + (i % 3), tol=tol)
+        check_instance(ctx, plan, x, y, bc[0], bc[1], n + (i % 3), tol=TOL_F64)
+
+
+@pytest.mark.parametrize("refine", [0, 1])
+def test_mixed_tile_boundaries_sweep(ctx, refine):
+    """Sizes around whole binary32 tiles and chunks (k tiles exactly, one row more or less, a lone
+    row or chunk past a tile, a tile one row short of its last chunk), seeded, both end
+    conditions."""
+    L = 96
+    sizes = sorted({k * L + d for k in (12, 13, 33) for d in (-1, 0, 1, 2, 17, 31, 32, 33, -L + 1, L - 1)})
+    plan = ctx.plan(34 * L, spl.PREC_F32_REFINE, refine_steps=refine, tile_rows=L)
+    for i, n in enumerate(sizes):
+        x, y = synth.curve(90 + i, n)
+        bc = (NAT, NAT) if i % 2 else (0.75, -1.25)
+        check_instance(ctx, plan, x, y, bc[0], bc[1], n + (i % 3), tol=TOL_MIXED)
