@@ -242,17 +242,21 @@ spl_status spl_generate_curve(uint64_t seed, uint64_t instance, uint64_t n, doub
  *
  * A server owns a persistent kernel (one CTA per SM, cooperative launch) on its own stream:
  * a scheduler warp takes requests from a ring in mapped host memory and publishes their tiles;
- * worker warps solve published tiles (binary32 solve and cubic, exact binary64 differences and
- * query positions: the mixed path without refinement) while further requests arrive, so the
+ * worker warps solve published tiles, one tile per warp (binary32 solve and cubic, exact binary64
+ * differences and query positions: the mixed path without refinement, tiles of tile_rows rows
+ * rounded up to a multiple of 32) while further requests arrive, so the
  * work of requests that arrive while others run overlaps on the device.  A request is admitted
  * when a slot is free, its tiles fit the tile map and its footprint (16 n + 8 m bytes, plus
  * 8 n for y'' and 4 m for indices when requested) fits in budget_bytes; otherwise it waits in
  * a host FIFO and is admitted by a later submit/poll/wait.  The device loop exits after
  * idle_timeout_ms without work (and after 30 s in any case); the next admission relaunches it.
- * Requests use device memory (SPL_MEM_DEVICE); results equal those of a single-instance
- * submission bit for bit, whatever else is in flight.
+ * Requests use device memory (SPL_MEM_DEVICE), and their arrays must hold their final contents
+ * when the request is submitted (no GPU work still writing them on another stream): a running
+ * loop may read the inputs and write the outputs at once.  Results equal those of a
+ * single-request server, bit for bit, whatever else is in flight.
  *   max_inflight     requests resident on the device at once (slots), 1..65536.
- *   tile_rows        knots per tile (0 = 256), >= 16.
+ *   tile_rows        knots per tile (0 = 1024), >= 16; shorter tiles lower the latency of a request,
+ *                    longer ones raise the throughput (each tile repeats 96 rows of start-up).
  *   budget_bytes     HBM budget for the footprints of resident requests.
  *   max_tiles        tile-map capacity (0 = max(2^20, 64 max_inflight)).
  *   idle_timeout_ms  0 = 200.

@@ -56,6 +56,8 @@ struct ServeArgs {
   volatile unsigned *h_done;                             // per slot: status, seq
   unsigned long long idle_ns, deadline_ns;
   unsigned fault_flags;                                  // tests: bit 0, the scheduler leaves at once
+  float4 *scan_scratch;                                  // per worker warp: scan_rows_cap rows
+  long long scan_rows_cap;
 };
 
 // Natural end condition: section "Start and End Derivatives" (slope > 0.99e30).

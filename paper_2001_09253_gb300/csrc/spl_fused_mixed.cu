@@ -366,143 +366,6 @@ __global__ void __launch_bounds__(kThreadsM, 1) mixed_kernel(const Inst *__restr
   }
 }
 
-// ---------------------------------------------------------------------------------------
-// Persistent serving loop (continuous batching).  Warp 0 of CTA 0 is the scheduler: it reads
-// request entries that the host appends to a ring in mapped host memory, installs each in its
-// device slot, maps the request's tiles into the device tile map and publishes them by
-// advancing `published`.  Every other warp is a worker: it claims 32 consecutive tile tickets
-// at a time and, once a ticket is published, solves that tile of that request with the same
-// binary32 fit + evaluation as mixed_kernel<0>.  The lane finishing a request's last tile
-// writes the request's status and sequence number to mapped host memory.  All waits are
-// bounded: the scheduler leaves after `idle_ns` without work or at `deadline_ns`, and sets
-// `stop`; workers leave once stop is set and every published tile is claimed.  The host
-// relaunches the loop when new work arrives.  Launched cooperatively (one CTA per SM), so the
-// scheduler and the workers are co-resident.
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-
-__global__ void __launch_bounds__(kThreadsM, 1) serve_kernel(ServeArgs a) {
-  extern __shared__ float smem_ring_s[];
-  RingM ring{smem_ring_s, (int)threadIdx.x};
-  const int lane = threadIdx.x & 31;
-  const bool scheduler = (blockIdx.x == 0 && threadIdx.x < 32);
-  const unsigned long long t_start = globaltimer_ns();
-  volatile unsigned long long *published = a.published;
-  volatile unsigned *stop = a.stop;
-
-  if (scheduler && (a.fault_flags & 1u)) return;  // failure-detection tests: no work is published
-  if (scheduler) {
-    unsigned long long consumed = *a.consumed;
-    unsigned long long last_work = t_start;
-    unsigned sleep_ns = 64;
-    if (lane == 0) *a.h_alive = 1u;
-    for (;;) {
-      const unsigned long long tail = *a.h_tail;
-      if (consumed < tail) {
-        __threadfence_system();  // the entry was written before the tail: read it after
-        const ServeEntry *e = a.h_ring + (consumed % a.rcap);
-        // one 8-byte word of the entry per lane from mapped host memory, shared by shuffles
-        constexpr int kWords = (int)(sizeof(ServeEntry) / 8);
-        static_assert(kWords <= 32, "a serving entry must fit in one warp's loads");
-        const volatile unsigned long long *src = reinterpret_cast<const volatile unsigned long long *>(e);
-        const unsigned long long word = (lane < kWords) ? src[lane] : 0ull;
-        ServeEntry ent;
-        unsigned long long *dst = reinterpret_cast<unsigned long long *>(&ent);
-        for (int w = 0; w < kWords; ++w) dst[w] = __shfl_sync(0xffffffffu, word, w);
-        const unsigned slot = ent.slot;
-        if (lane == 0) {
-          ent.inst.status = a.slot_status + slot;
-          ent.inst.z = nullptr;
-          a.slot_inst[slot] = ent.inst;
-          a.slot_first[slot] = ent.first_tile;
-          a.slot_done[slot] = 0u;
-          a.slot_status[slot] = 0u;
-          a.slot_seq[slot] = ent.seq;
-        }
-        const unsigned long long nt = (unsigned long long)ent.inst.ntiles;
-        for (unsigned long long i = lane; i < nt; i += 32) a.tile_slot[(ent.first_tile + i) % a.tile_cap] = slot;
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) *published = ent.first_tile + nt;
-        ++consumed;
-        if (lane == 0) {
-          *a.consumed = consumed;
-          *a.h_consumed = consumed;
-          __threadfence_system();
-        }
-        last_work = globaltimer_ns();
-        sleep_ns = 64;
-        continue;
-      }
-      const unsigned long long now = globaltimer_ns();
-      if (*a.h_stop || now - last_work > a.idle_ns || now - t_start > a.deadline_ns) break;
-      __nanosleep(sleep_ns);
-      if (sleep_ns < 2048) sleep_ns <<= 1;
-    }
-    if (lane == 0) {
-      *stop = 1u;
-      __threadfence();
-    }
-    return;
-  }
-
-  // workers
-  for (;;) {
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(a.claimed, 32ull);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    const unsigned long long t = base + lane;
-    bool have = false;
-    unsigned sleep_ns = 64;
-    for (;;) {
-      if (*published > t) {
-        have = true;
-        break;
-      }
-      if (*stop) {
-        __threadfence();
-        have = *published > t;
-        break;
-      }
-      if (globaltimer_ns() - t_start > a.deadline_ns + 1000000000ull) {  // the scheduler stops first
-        atomicOr(a.err, 1u);
-        break;
-      }
-      __nanosleep(sleep_ns);
-      if (sleep_ns < 4096) sleep_ns <<= 1;
-    }
-    if (have) {
-      __threadfence();
-      const unsigned slot = a.tile_slot[t % a.tile_cap];
-      const Inst I = a.slot_inst[slot];
-      tile_mixed<false>(I, (long long)(t - a.slot_first[slot]), ring);
-      __threadfence();
-      const unsigned done = atomicAdd(a.slot_done + slot, 1u) + 1u;
-      if (done == (unsigned)I.ntiles) {
-        __threadfence();
-        const unsigned st = *(volatile unsigned *)(a.slot_status + slot);
-        a.h_done[2 * slot] = st;
-        __threadfence_system();
-        a.h_done[2 * slot + 1] = a.slot_seq[slot];
-        __threadfence_system();
-      }
-    }
-    if (__all_sync(0xffffffffu, !have)) break;
-  }
-}
-
-cudaError_t launch_serve(const ServeArgs &args, int sm_count, cudaStream_t stream) {
-  cudaError_t e = cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemM);
-  if (e != cudaSuccess) return e;
-  ServeArgs copy = args;
-  void *params[] = {&copy};
-  return cudaLaunchCooperativeKernel((const void *)serve_kernel, dim3((unsigned)sm_count), dim3(kThreadsM), params,
-                                     kSmemM, stream);
-}
-
 int mixed_threads_per_sm() { return kThreadsM; }
 
 long long threads_mixed(int sm_count, long long total_tiles) {

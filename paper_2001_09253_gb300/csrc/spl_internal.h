@@ -41,8 +41,13 @@ cudaError_t launch_fused_mixed(const Inst *d_insts, int ninst, long long total_t
 cudaError_t launch_refine_mixed(const Inst *d_insts, int ninst, long long total_tiles, int sm_count,
                                 unsigned long long *counter, cudaStream_t stream);
 
-// Persistent serving loop (spl_fused_mixed.cu): a cooperative launch of one CTA per SM.
+// Persistent serving loop (spl_mixed_scan.cu): a cooperative launch of one CTA per SM; its
+// workers solve tiles of serve_tile_rows(tile_rows) rows with the warp-cooperative kernel's
+// solver, in ServeArgs::scan_scratch (serve_scratch_bytes bytes, serve_rows_cap rows per warp).
 cudaError_t launch_serve(const ServeArgs &args, int sm_count, cudaStream_t stream);
+int serve_tile_rows(int tile_rows);
+long long serve_rows_cap(int tile_rows);
+size_t serve_scratch_bytes(int sm_count, int tile_rows);
 int mixed_threads_per_sm();  // threads of one mixed-kernel CTA (one CTA per SM)
 
 // Warp-cooperative binary32 fit + evaluation (spl_mixed_scan.cu): one warp per tile of

@@ -225,7 +225,8 @@ spl_status spl_serve_create(spl_ctx *c, const spl_serve_desc *d, spl_server **ou
   if (!s) return SPL_ERR_CUDA;
   s->ctx = c;
   s->d = *d;
-  if (!s->d.tile_rows) s->d.tile_rows = 256;
+  if (!s->d.tile_rows) s->d.tile_rows = 1024;
+  s->d.tile_rows = (uint32_t)spl::serve_tile_rows((int)std::min<uint32_t>(s->d.tile_rows, 1u << 20));
   if (!s->d.idle_timeout_ms) s->d.idle_timeout_ms = 200;
   s->device = spl_ctx_device(c);
   s->sms = spl_ctx_sms(c);
@@ -241,6 +242,14 @@ spl_status spl_serve_create(spl_ctx *c, const spl_serve_desc *d, spl_server **ou
   if (!spl_ctx_arena_alloc(c, total, &off)) return SPL_ERR_BUDGET;
   s->blocks.push_back({off, total});
   char *base = spl_ctx_arena_base(c) + off;
+  // the workers' scratch (one slice per warp of the launch)
+  const uint64_t scratch = up256(spl::serve_scratch_bytes(s->sms, (int)s->d.tile_rows));
+  uint64_t soff = 0;
+  if (!spl_ctx_arena_alloc(c, scratch, &soff)) {
+    release_server(s.get());
+    return SPL_ERR_BUDGET;
+  }
+  s->blocks.push_back({soff, scratch});
   ServeArgs &a = s->args;
   a.published = reinterpret_cast<unsigned long long *>(base);
   a.claimed = a.published + 1;
@@ -265,6 +274,8 @@ spl_status spl_serve_create(spl_ctx *c, const spl_serve_desc *d, spl_server **ou
   // a single launch never runs longer than the deadline; the host relaunches
   a.deadline_ns = (unsigned long long)(s->d.deadline_ms ? s->d.deadline_ms : 30000u) * 1000000ull;
   a.fault_flags = s->d.fault_flags;
+  a.scan_scratch = reinterpret_cast<float4 *>(spl_ctx_arena_base(c) + soff);
+  a.scan_rows_cap = spl::serve_rows_cap((int)s->d.tile_rows);
   // mapped host block: tail, stop, consumed, alive, done words, ring
   const uint64_t hbytes = 256 + up256(8ull * S) + sizeof(ServeEntry) * rcap;
   if (cudaHostAlloc(&s->hblock, hbytes, cudaHostAllocMapped) != cudaSuccess) {

@@ -313,7 +313,7 @@ class Context:
 class Server:
     """Continuous-batching server on a persistent device loop (spl_serve_*)."""
 
-    def __init__(self, ctx: Context, max_inflight: int = 1024, tile_rows: int = 256, budget_bytes: int = 1 << 34,
+    def __init__(self, ctx: Context, max_inflight: int = 1024, tile_rows: int = 0, budget_bytes: int = 1 << 34,
                  max_tiles: int = 0, idle_timeout_ms: int = 0, deadline_ms: int = 0, fault_flags: int = 0):
         self.ctx, self.lib = ctx, ctx.lib
         d = ServeDesc(max_inflight=int(max_inflight), tile_rows=int(tile_rows), budget_bytes=int(budget_bytes),
@@ -325,8 +325,15 @@ class Server:
         ctx._servers.add(self)
         self._keep = {}
 
-    def submit(self, x, y, yp1=NATURAL, ypn=NATURAL, m=None, ypp_out=None, yq_out=None, jq_out=None) -> int:
+    def submit(self, x, y, yp1=NATURAL, ypn=NATURAL, m=None, ypp_out=None, yq_out=None, jq_out=None,
+               sync=True) -> int:
+        """sync: first wait for the caller's current stream, since the running device loop may
+        pick the request up at once and pending writes to its arrays (their creation, a fill) must
+        land first; False when the caller has made the arrays ready itself."""
+        import torch
         r = make_request(x, y, yp1, ypn, m, ypp_out, yq_out, jq_out)
+        if sync:
+            torch.cuda.current_stream(x.device).synchronize()
         t = ctypes.c_uint64()
         _check(self.lib.spl_serve_submit(self.handle, ctypes.byref(r), ctypes.byref(t)), "spl_serve_submit")
         self._keep[t.value] = (x, y, ypp_out, yq_out, jq_out)

@@ -86,15 +86,18 @@ def test_alone_and_in_the_mix_are_identical(ctx):
 
 
 def test_admission_under_a_small_budget(ctx):
-    pool = _pool(40, 6, lo=1e4, hi=5e4)
+    import torch
+    # requests long enough (1e6..2e6 points) and submitted back to back (outputs made ready
+    # beforehand) so that later ones arrive while the budget is held by earlier ones
+    pool = _pool(16, 6, lo=1e6, hi=2e6)
     biggest = max(16 * p["n"] + 8 * p["n"] + 8 * p["m"] for p in pool)
     srv = spl.Server(ctx, max_inflight=64, tile_rows=TILE, budget_bytes=2 * biggest)
-    outs, tickets = [], []
+    outs = [_outputs(p) for p in pool]
+    torch.cuda.synchronize()
+    tickets = []
     waited = 0
-    for p in pool:
-        o = _outputs(p)
-        outs.append(o)
-        tickets.append(srv.submit(p["xt"], p["yt"], p["bc"][0], p["bc"][1], p["m"], o[0], o[1]))
+    for p, o in zip(pool, outs):
+        tickets.append(srv.submit(p["xt"], p["yt"], p["bc"][0], p["bc"][1], p["m"], o[0], o[1], sync=False))
         waited = max(waited, srv.stats()["waiting"])
     assert waited > 0  # some requests had to wait for memory
     for t in tickets:
