@@ -118,3 +118,16 @@ def test_mixed_tile_boundaries_sweep(ctx, refine):
         x, y = synth.curve(90 + i, n)
         bc = (NAT, NAT) if i % 2 else (0.75, -1.25)
         check_instance(ctx, plan, x, y, bc[0], bc[1], n + (i % 3), tol=TOL_MIXED)
+
+
+@pytest.mark.parametrize("refine", [0, 1])
+@pytest.mark.parametrize("n", [1024, 1057, 1311])
+def test_mixed_warp_tiles_query_counts(ctx, refine, n):
+    """The warp-cooperative kernel (instances of 1,024 rows or more) with few and many queries:
+    none, one (the grid's single point x_0), two, three, a third of n, more than twice n; both
+    end conditions, tiles of 96 rows."""
+    x, y = synth.curve(3000 + n, n)
+    plan = ctx.plan(n, spl.PREC_F32_REFINE, refine_steps=refine, tile_rows=96)
+    for m in sorted({0, 1, 2, 3, n // 3, 2 * n + 1}):
+        check_instance(ctx, plan, x, y, -1.0, 1.0, m, tol=TOL_MIXED)
+        check_instance(ctx, plan, x, y, NAT, NAT, m, tol=TOL_MIXED)
