@@ -109,6 +109,13 @@ __device__ __forceinline__ double quot64(double num, double den, double r) {
 }
 
 // Same seed and step for binary32 (MUFU rcp has ~1 ulp; one second-order step suffices).
+// The MUFU binary32 reciprocal alone (~1 ulp).
+__device__ __forceinline__ float rcp_approx32(float d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  return r;
+}
+
 __device__ __forceinline__ float rcp32(float d) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));

@@ -170,12 +170,14 @@ __device__ void scan_tile(const Inst &I, long long tile, float4 *__restrict__ W,
     // The map contracts errors in c'_{j-1} by at most h_j h_{j-1} / (1.5 h_{j-1} + 2 h_j)^2 <= 1/12,
     // so after kRelaxS sweeps every lane is within 12^-8 / 2 (< 2^-29) of the sequential value; lane 0
     // starts from the carried c'_{R-1}.
-    float cj = c * rcp32(b - a * (lane == 0 ? cp : 0.0f)), iden = 0.0f;
+    // The sweeps before the last use the MUFU reciprocal alone (~1 ulp): they only move the
+    // guess, the last one forms the refined 1/den that the d' step uses.
+    float cj = c * rcp_approx32(b - a * (lane == 0 ? cp : 0.0f)), iden = 0.0f;
 #pragma unroll
     for (int it = 0; it < kRelaxS; ++it) {
       float cm = __shfl_up_sync(kFullS, cj, 1);
       if (lane == 0) cm = cp;
-      iden = rcp32(b - a * cm);
+      iden = it + 1 < kRelaxS ? rcp_approx32(b - a * cm) : rcp32(b - a * cm);
       cj = c * iden;
     }
     // d': scan of the affine maps t -> (-a/den) t + d/den, applied to d'_{R-1}
