@@ -131,6 +131,9 @@ typedef struct spl_ctx_desc {
  *                 values are SPL_ERR_INVALID_ARG.
  *   tile_rows     knots per tile of the chunked solve; 0 picks it from the device and n.
  *                 Exposed so tests can force many small tiles; values below 16 are refused.
+ *                 Binary32 launches whose points lie mostly in instances of 1,024 knots or
+ *                 more run the warp-cooperative kernel, whose tiles are whole 32-row chunks:
+ *                 there tile_rows is rounded up to a multiple of 32.
  *   query_mode    spl_query_mode.
  *   eval_variant  spl_eval_variant of the separate evaluation kernel. */
 typedef struct spl_plan_desc {
