@@ -41,6 +41,13 @@ __device__ __forceinline__ float dif32_alu(double b, double a) {
   return dif32_near(b, a);
 }
 
+// dif32_alu for b >= a (widths of increasing knots, a query above its bracketing knot).
+__device__ __forceinline__ float dif32_up(double b, double a) {
+  float v;
+  if (diff_up_f32(b, a, &v)) return v;
+  return dif32_near(b, a);
+}
+
 __device__ __forceinline__ F2 dif2(double b, double a) {
   F2 v;
   if (diff_f2(b, a, &v)) return v;

@@ -102,7 +102,7 @@ __device__ void scan_tile(const Inst &I, long long tile, float4 *__restrict__ W,
         hF = dif2(x1, x0);
         sF = df_div(dif2(y1, y0), hF, rcp32(hF.hi));
       } else {
-        hF.hi = dif32_alu(x1, x0);
+        hF.hi = dif32_up(x1, x0);
         sF.hi = quot32(dy32(y1, y0), hF.hi, rcp32(hF.hi));
       }
     }
@@ -289,7 +289,7 @@ __device__ void scan_tile(const Inst &I, long long tile, float4 *__restrict__ W,
           const float pl = __shfl_sync(kFullS, ypp, l), pl1 = __shfl_sync(kFullS, yp1, l);
           const float bl = __shfl_sync(kFullS, ba, l), ibl = __shfl_sync(kFullS, iba, l);
           if (in) {
-            const float xa = dif32_alu(q, xl);
+            const float xa = dif32_up(q, xl);
             I.yq[k] = to_f64(newint32(xa, bl - xa, fl, fl1, pl, pl1, bl, ibl));
             if (I.jq) I.jq[k] = (int32_t)(R + l);
           }

@@ -234,6 +234,22 @@ SPL_HD bool diff_near_f32(double b, double a, float *out) {
   return true;
 }
 
+// diff_near_f32 for b >= a (widths of increasing knots, a query above the knot that brackets
+// it): the ulp count is then non-negative whatever the operands' sign, so no sign handling;
+// b < a is refused like a wide gap.
+SPL_HD bool diff_up_f32(double b, double a, float *out) {
+  const uint64_t ub = bits64(b), ua = bits64(a);
+  const uint32_t hb = (uint32_t)(ub >> 52);
+  if (hb != (uint32_t)(ua >> 52)) return false;
+  const uint32_t e = hb & 0x7FFu;
+  if (e - 949u > 214u) return false;  // e in [949, 1163]: 2^(e-1075) and 2^(e-1075+39) normal
+  const uint64_t u = (hb & 0x800u) ? ua - ub : ub - ua;
+  if (u >> 39) return false;  // also b < a (u wraps to a huge count)
+  const float r = fma32(f32_of_small_uint((uint32_t)(u >> 16)), 65536.0f, f32_of_small_uint((uint32_t)u & 0xFFFFu));
+  *out = r * from_bits32((e - 1075u + 127u) << 23);
+  return true;
+}
+
 SPL_HD F2 df_add(F2 a, F2 b) {
   F2 s = two_sum(a.hi, b.hi);
   const float e = s.lo + (a.lo + b.lo);

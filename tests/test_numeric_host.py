@@ -183,6 +183,34 @@ def test_near_difference_split_fma(lib):
     assert not lib.t_diff_near_f32(1e-300, 1.5e-300, ctypes.byref(o))
 
 
+def test_ordered_difference(lib):
+    """diff_up_f32 (b >= a) equals diff_near_f32 wherever it accepts, accepts every ordered
+    same-binade pair up to 2^39 ulps apart, and refuses b < a."""
+    lib.t_diff_up_f32.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_float)]
+    lib.t_diff_up_f32.restype = ctypes.c_int
+    lib.t_diff_near_f32.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_float)]
+    lib.t_diff_near_f32.restype = ctypes.c_int
+    rng = np.random.default_rng(10)
+    hits = 0
+    for _ in range(6000):
+        a = rng.normal() * 10.0 ** rng.integers(-20, 20)
+        b = a + abs(a) * rng.random() * 10.0 ** rng.integers(-16, -3)
+        if rng.random() < 0.1:
+            b = a
+        o1, o2 = ctypes.c_float(), ctypes.c_float()
+        ok1 = lib.t_diff_up_f32(float(b), float(a), ctypes.byref(o1))
+        ok2 = lib.t_diff_near_f32(float(b), float(a), ctypes.byref(o2))
+        assert ok1 == ok2, (a, b)
+        if ok1:
+            hits += 1
+            assert o1.value == o2.value == rn32(Fraction(float(b)) - Fraction(float(a))), (a, b)
+    assert hits > 3000
+    o = ctypes.c_float()
+    assert not lib.t_diff_up_f32(1.0, 1.0 + 2.0 ** -40, ctypes.byref(o))      # b < a
+    assert not lib.t_diff_up_f32(-1.0 - 2.0 ** -40, -1.0, ctypes.byref(o))    # b < a, negative
+    assert lib.t_diff_up_f32(-1.0, -1.0 - 2.0 ** -40, ctypes.byref(o)) and o.value == 2.0 ** -40
+
+
 def test_diff_far_apart_and_signs(lib):
     rng = np.random.default_rng(1)
     for _ in range(2000):
