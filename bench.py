@@ -534,7 +534,7 @@ def serving(r, pool_count=512, seed=3, lo=1e2, hi=1e6, rate=20000.0, warm_s=1.0,
     for i, nn in enumerate(sizes):
         o, nn = int(off[i]), int(nn)
         reqs.append(spl.make_request(X[o:o + nn], Y[o:o + nn], spl.NATURAL, spl.NATURAL, nn, P[o:o + nn], Q[o:o + nn]))
-    srv = spl.Server(r.ctx, max_inflight=2048, tile_rows=1024, budget_bytes=150 * 10 ** 9)
+    srv = spl.Server(r.ctx, max_inflight=2048, tile_rows=0, budget_bytes=150 * 10 ** 9)
     st0 = srv.stats()
     # warm-up trace, then the measured trace (fresh Poisson draws, pool entries cycled)
     nw, nm = int(rate * warm_s), int(rate * run_s)

@@ -258,8 +258,9 @@ spl_status spl_generate_curve(uint64_t seed, uint64_t instance, uint64_t n, doub
  * loop may read the inputs and write the outputs at once.  Results equal those of a
  * single-request server, bit for bit, whatever else is in flight.
  *   max_inflight     requests resident on the device at once (slots), 1..65536.
- *   tile_rows        knots per tile (0 = 1024), >= 16; shorter tiles lower the latency of a request,
- *                    longer ones raise the throughput (each tile repeats 96 rows of start-up).
+ *   tile_rows        knots per tile, >= 16 (rounded up to a multiple of 32); shorter tiles lower the
+ *                    latency of a request, longer ones raise the throughput (each tile repeats 96
+ *                    rows of start-up).  0: per request, about 32 tiles each, 256..1024 rows.
  *   budget_bytes     HBM budget for the footprints of resident requests.
  *   max_tiles        tile-map capacity (0 = max(2^20, 64 max_inflight)).
  *   idle_timeout_ms  0 = 200.

@@ -38,6 +38,15 @@ double now_s() {
 
 uint64_t up256(uint64_t v) { return (v + 255) / 256 * 256; }
 
+// Per-request tile length of a server created with tile_rows = 0: about 32 tiles (warps) per
+// request, between 256 rows (a small request's latency: one short tile) and kServeTileMax (a
+// large one's throughput: each tile repeats 96 rows of start-up).
+constexpr int kServeTileMin = 256, kServeTileMax = 1024;
+int serve_tile_for(uint64_t n) {
+  const uint64_t L = (n + 32 * 32 - 1) / (32 * 32) * 32;
+  return (int)std::min<uint64_t>(std::max<uint64_t>(L, kServeTileMin), kServeTileMax);
+}
+
 struct Req {
   int state = 0;  // 0 waiting on the host, 1 resident on the device, 2 done
   Inst inst{};
@@ -225,8 +234,9 @@ spl_status spl_serve_create(spl_ctx *c, const spl_serve_desc *d, spl_server **ou
   if (!s) return SPL_ERR_CUDA;
   s->ctx = c;
   s->d = *d;
-  if (!s->d.tile_rows) s->d.tile_rows = 1024;
-  s->d.tile_rows = (uint32_t)spl::serve_tile_rows((int)std::min<uint32_t>(s->d.tile_rows, 1u << 20));
+  // tile_rows 0: per request (serve_tile_for); otherwise one length, a whole number of chunks
+  if (s->d.tile_rows) s->d.tile_rows = (uint32_t)spl::serve_tile_rows((int)std::min<uint32_t>(s->d.tile_rows, 1u << 20));
+  const int scratch_rows = s->d.tile_rows ? (int)s->d.tile_rows : kServeTileMax;
   if (!s->d.idle_timeout_ms) s->d.idle_timeout_ms = 200;
   s->device = spl_ctx_device(c);
   s->sms = spl_ctx_sms(c);
@@ -243,7 +253,7 @@ spl_status spl_serve_create(spl_ctx *c, const spl_serve_desc *d, spl_server **ou
   s->blocks.push_back({off, total});
   char *base = spl_ctx_arena_base(c) + off;
   // the workers' scratch (one slice per warp of the launch)
-  const uint64_t scratch = up256(spl::serve_scratch_bytes(s->sms, (int)s->d.tile_rows));
+  const uint64_t scratch = up256(spl::serve_scratch_bytes(s->sms, scratch_rows));
   uint64_t soff = 0;
   if (!spl_ctx_arena_alloc(c, scratch, &soff)) {
     release_server(s.get());
@@ -275,7 +285,7 @@ spl_status spl_serve_create(spl_ctx *c, const spl_serve_desc *d, spl_server **ou
   a.deadline_ns = (unsigned long long)(s->d.deadline_ms ? s->d.deadline_ms : 30000u) * 1000000ull;
   a.fault_flags = s->d.fault_flags;
   a.scan_scratch = reinterpret_cast<float4 *>(spl_ctx_arena_base(c) + soff);
-  a.scan_rows_cap = spl::serve_rows_cap((int)s->d.tile_rows);
+  a.scan_rows_cap = spl::serve_rows_cap(scratch_rows);
   // mapped host block: tail, stop, consumed, alive, done words, ring
   const uint64_t hbytes = 256 + up256(8ull * S) + sizeof(ServeEntry) * rcap;
   if (cudaHostAlloc(&s->hblock, hbytes, cudaHostAllocMapped) != cudaSuccess) {
@@ -327,7 +337,7 @@ spl_status spl_serve_submit(spl_server *s, const spl_request *r, uint64_t *ticke
   I.x = r->x; I.y = r->y; I.ypp = r->ypp_out; I.yq = r->yq_out; I.jq = r->jq_out;
   I.n = (long long)r->n; I.m = (long long)r->m;
   I.yp1 = r->yp1; I.ypn = r->ypn;
-  I.tile_rows = (int)s->d.tile_rows;
+  I.tile_rows = s->d.tile_rows ? (int)s->d.tile_rows : serve_tile_for(r->n);
   I.ntiles = ((long long)r->n + I.tile_rows - 1) / I.tile_rows;
   I.tile_begin = 0;
   q.ntiles = (uint64_t)I.ntiles;

@@ -43,9 +43,9 @@ def _outputs(p):
             torch.full((p["m"],), np.nan, dtype=torch.float64, device="cuda"))
 
 
-def _reference(ctx, p):
+def _reference(ctx, p, tile=TILE):
     """The same request served alone: a fresh server with nothing else in flight."""
-    srv = spl.Server(ctx, max_inflight=1, tile_rows=TILE, idle_timeout_ms=20)
+    srv = spl.Server(ctx, max_inflight=1, tile_rows=tile, idle_timeout_ms=20)
     ypp, yq = _outputs(p)
     s, _ = srv.wait(srv.submit(p["xt"], p["yt"], p["bc"][0], p["bc"][1], p["m"], ypp, yq))
     srv.close()
@@ -53,11 +53,12 @@ def _reference(ctx, p):
     return ypp.cpu().numpy(), yq.cpu().numpy()
 
 
-def test_alone_and_in_the_mix_are_identical(ctx):
+@pytest.mark.parametrize("tile", [TILE, 0])  # 0: tile length chosen per request
+def test_alone_and_in_the_mix_are_identical(ctx, tile):
     import torch
     pool = _pool(48, 5)
-    refs = [_reference(ctx, p) for p in pool]
-    srv = spl.Server(ctx, max_inflight=64, tile_rows=TILE, budget_bytes=1 << 34)
+    refs = [_reference(ctx, p, tile) for p in pool]
+    srv = spl.Server(ctx, max_inflight=64, tile_rows=tile, budget_bytes=1 << 34)
     # alone: one request at a time
     for p, ref in zip(pool, refs):
         ypp, yq = _outputs(p)
