@@ -32,16 +32,10 @@ __device__ __forceinline__ float dif32_near(double b, double a) {
   return sub_f64_f32(b, a);
 }
 
-// b - a rounded once to binary32 without FP64 instructions in the common case (the integer/FP32
-// route of diff_near_f32): for kernels that are throughput-bound with many warps in flight, where
-// the FP64 pipe (~1/64 of the FP32 rate) is the scarce unit; other pairs as dif32_near.
-__device__ __forceinline__ float dif32_alu(double b, double a) {
-  float v;
-  if (diff_near_f32(b, a, &v)) return v;
-  return dif32_near(b, a);
-}
-
-// dif32_alu for b >= a (widths of increasing knots, a query above its bracketing knot).
+// b - a rounded once to binary32 for b >= a (widths of increasing knots, a query above its
+// bracketing knot), without FP64 instructions in the common case (the integer/FP32 route of
+// diff_up_f32): for kernels that are throughput-bound with many warps in flight, where the FP64
+// pipe (~1/64 of the FP32 rate) is the scarce unit; other pairs as dif32_near.
 __device__ __forceinline__ float dif32_up(double b, double a) {
   float v;
   if (diff_up_f32(b, a, &v)) return v;

@@ -207,36 +207,18 @@ SPL_HD float fma32(float a, float b, float c) {
 #endif
 }
 
-// b - a rounded to nearest-even binary32 on the integer and FP32 pipes, for two binary64
-// numbers with the same sign and exponent field whose difference is below 2^39 units of their
-// shared ulp (neighbouring knots, a query and its bracketing knots): the ulp count D splits as
-// D = Dh 2^16 + Dl with Dh < 2^23 and Dl < 2^16; each part is exact in binary32 (the encoding of
-// 2^23 + part, minus 2^23), and one FMA forms Dh 2^16 + Dl with a single rounding.  The scale
-// 2^(e-1075) is a power of two within binary32's normal range, so the final product is exact.
-// Returns false otherwise (the caller then takes a wider route).
 SPL_HD float f32_of_small_uint(uint32_t v) {  // v < 2^23, exactly
   return from_bits32(0x4B000000u | v) - 8388608.0f;
 }
 
-SPL_HD bool diff_near_f32(double b, double a, float *out) {
-  const uint64_t ub = bits64(b), ua = bits64(a);
-  const uint32_t hb = (uint32_t)(ub >> 52);
-  if (hb != (uint32_t)(ua >> 52)) return false;
-  const uint32_t e = hb & 0x7FFu;
-  if (e < 949u || e > 1163u) return false;  // 2^(e-1075) and 2^(e-1075+39) within the normal range
-  const int64_t D = (hb & 0x800u) ? (int64_t)(ua - ub) : (int64_t)(ub - ua);
-  const uint32_t neg = D < 0 ? 0x80000000u : 0u;
-  const uint64_t u = D < 0 ? (uint64_t)(-D) : (uint64_t)D;
-  if (u >> 39) return false;
-  const float r = fma32(f32_of_small_uint((uint32_t)(u >> 16)), 65536.0f, f32_of_small_uint((uint32_t)u & 0xFFFFu));
-  const float scale = from_bits32((e - 1075u + 127u) << 23);
-  *out = from_bits32(bits32(r * scale) | neg);
-  return true;
-}
-
-// diff_near_f32 for b >= a (widths of increasing knots, a query above the knot that brackets
-// it): the ulp count is then non-negative whatever the operands' sign, so no sign handling;
-// b < a is refused like a wide gap.
+// b - a rounded to nearest-even binary32 on the integer and FP32 pipes, for b >= a with the same
+// sign and exponent field and a difference below 2^39 units of their shared ulp (widths of
+// increasing knots, a query above the knot that brackets it): the ulp count D (non-negative
+// whatever the operands' sign) splits as D = Dh 2^16 + Dl with Dh < 2^23 and Dl < 2^16; each part
+// is exact in binary32 (the encoding of 2^23 + part, minus 2^23), and one FMA forms Dh 2^16 + Dl
+// with a single rounding.  The scale 2^(e-1075) is a power of two within binary32's normal
+// range, so the final product is exact.  Returns false otherwise, b < a included (the caller then
+// takes a wider route).
 SPL_HD bool diff_up_f32(double b, double a, float *out) {
   const uint64_t ub = bits64(b), ua = bits64(a);
   const uint32_t hb = (uint32_t)(ub >> 52);

@@ -39,6 +39,5 @@ int t_diff_same_f32(double b, double a, float *out) { return spl::diff_same_f32(
 
 extern "C" {
 int t_diff_small_f32(double b, double a, float *out) { return spl::diff_small_f32(b, a, out) ? 1 : 0; }
-int t_diff_near_f32(double b, double a, float *out) { return spl::diff_near_f32(b, a, out) ? 1 : 0; }
 int t_diff_up_f32(double b, double a, float *out) { return spl::diff_up_f32(b, a, out) ? 1 : 0; }
 }

@@ -145,20 +145,21 @@ def test_small_same_binade_difference(lib):
     assert not lib.t_diff_small_f32(1e300, 1e300 * (1 - 1e-15), ctypes.byref(o))
 
 
-def test_near_difference_split_fma(lib):
-    """The same-binade route with the split ulp count and one FMA: exact rounding of b - a for
-    both signs and both orders, up to 2^39 ulps apart; wider gaps and other binades refused."""
-    lib.t_diff_near_f32.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_float)]
-    lib.t_diff_near_f32.restype = ctypes.c_int
+def test_ordered_difference_split_fma(lib):
+    """The ordered same-binade route (b >= a) with the split ulp count and one FMA: exact
+    rounding of b - a for positive and negative operands, up to 2^39 ulps apart; b < a, wider
+    gaps and other binades refused."""
+    lib.t_diff_up_f32.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_float)]
+    lib.t_diff_up_f32.restype = ctypes.c_int
     rng = np.random.default_rng(9)
     hits = 0
     for _ in range(8000):
         a = rng.normal() * 10.0 ** rng.integers(-20, 20)
-        b = a + abs(a) * rng.random() * 10.0 ** rng.integers(-16, -3) * (1 if rng.random() < 0.5 else -1)
+        b = a + abs(a) * rng.random() * 10.0 ** rng.integers(-16, -3)
         if rng.random() < 0.1:
             b = a
         out = ctypes.c_float()
-        if not lib.t_diff_near_f32(float(b), float(a), ctypes.byref(out)):
+        if not lib.t_diff_up_f32(float(b), float(a), ctypes.byref(out)):
             continue
         hits += 1
         exact = Fraction(float(b)) - Fraction(float(a))
@@ -171,44 +172,17 @@ def test_near_difference_split_fma(lib):
     ulp = 2.0 ** -52
     o = ctypes.c_float()
     b = one + (2 ** 39 - 1) * ulp
-    assert lib.t_diff_near_f32(b, one, ctypes.byref(o)) and o.value == rn32(Fraction(b) - 1)
-    assert not lib.t_diff_near_f32(one + 2 ** 39 * ulp, one, ctypes.byref(o))
+    assert lib.t_diff_up_f32(b, one, ctypes.byref(o)) and o.value == rn32(Fraction(b) - 1)
+    assert not lib.t_diff_up_f32(one + 2 ** 39 * ulp, one, ctypes.byref(o))
     for d in ((1 << 24) + 1, (1 << 24) + 3, (1 << 30) + (1 << 6), (1 << 30) + (3 << 6), (1 << 38) + (1 << 14)):
         b = one + d * ulp
-        assert lib.t_diff_near_f32(b, one, ctypes.byref(o)) and o.value == rn32(Fraction(b) - 1), d
-        assert lib.t_diff_near_f32(one, b, ctypes.byref(o)) and o.value == rn32(1 - Fraction(b)), d
-        assert lib.t_diff_near_f32(-b, -one, ctypes.byref(o)) and o.value == rn32(Fraction(-b) + 1), d
-    assert not lib.t_diff_near_f32(2.0, 1.9, ctypes.byref(o))
-    assert not lib.t_diff_near_f32(1e300, 1e300 * (1 - 1e-15), ctypes.byref(o))
-    assert not lib.t_diff_near_f32(1e-300, 1.5e-300, ctypes.byref(o))
-
-
-def test_ordered_difference(lib):
-    """diff_up_f32 (b >= a) equals diff_near_f32 wherever it accepts, accepts every ordered
-    same-binade pair up to 2^39 ulps apart, and refuses b < a."""
-    lib.t_diff_up_f32.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_float)]
-    lib.t_diff_up_f32.restype = ctypes.c_int
-    lib.t_diff_near_f32.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_float)]
-    lib.t_diff_near_f32.restype = ctypes.c_int
-    rng = np.random.default_rng(10)
-    hits = 0
-    for _ in range(6000):
-        a = rng.normal() * 10.0 ** rng.integers(-20, 20)
-        b = a + abs(a) * rng.random() * 10.0 ** rng.integers(-16, -3)
-        if rng.random() < 0.1:
-            b = a
-        o1, o2 = ctypes.c_float(), ctypes.c_float()
-        ok1 = lib.t_diff_up_f32(float(b), float(a), ctypes.byref(o1))
-        ok2 = lib.t_diff_near_f32(float(b), float(a), ctypes.byref(o2))
-        assert ok1 == ok2, (a, b)
-        if ok1:
-            hits += 1
-            assert o1.value == o2.value == rn32(Fraction(float(b)) - Fraction(float(a))), (a, b)
-    assert hits > 3000
-    o = ctypes.c_float()
-    assert not lib.t_diff_up_f32(1.0, 1.0 + 2.0 ** -40, ctypes.byref(o))      # b < a
-    assert not lib.t_diff_up_f32(-1.0 - 2.0 ** -40, -1.0, ctypes.byref(o))    # b < a, negative
-    assert lib.t_diff_up_f32(-1.0, -1.0 - 2.0 ** -40, ctypes.byref(o)) and o.value == 2.0 ** -40
+        assert lib.t_diff_up_f32(b, one, ctypes.byref(o)) and o.value == rn32(Fraction(b) - 1), d
+        assert lib.t_diff_up_f32(-one, -b, ctypes.byref(o)) and o.value == rn32(Fraction(b) - 1), d
+        assert not lib.t_diff_up_f32(one, b, ctypes.byref(o)), d           # b < a
+        assert not lib.t_diff_up_f32(-b, -one, ctypes.byref(o)), d         # b < a, negative
+    assert not lib.t_diff_up_f32(2.0, 1.9, ctypes.byref(o))
+    assert not lib.t_diff_up_f32(1e300, 1e300 * (1 - 1e-15), ctypes.byref(o))
+    assert not lib.t_diff_up_f32(1.5e-300, 1e-300, ctypes.byref(o))
 
 
 def test_diff_far_apart_and_signs(lib):
