@@ -1,14 +1,17 @@
-// Evaluation of a fitted spline at a batch of queries, one thread per query: explicit query
+// Evaluation of a fitted spline at a batch of queries, lane-parallel over queries: explicit query
 // positions in any order (or the uniform grid of section "Curve Interpolation"), each
-// bracketed by bisection, then one of the three forms of section "Fast Interpolation" that the
+// bracketed by bisection (or by galloping from the interval of the lane's previous query when
+// that lies below it), then one of the three forms of section "Fast Interpolation" that the
 // paper benchmarks (section "Curve Interpolation": newint orig / noinv / vol).
 //
 // Bracketing is the definition the monotone sweep of section "Quality Checks" implements for
 // sorted queries: the largest i in [0, n-2] with x_i < q, or 0 when there is none.  It runs on
 // the order-preserving integer keys of the binary64 values, so the index is bit-identical to a
 // binary64 comparison; a query equal to a knot takes the interval on its left.  Each probe is a
-// dependent load: sorted queries share their probe paths between neighbouring threads (cache
-// hits), unsorted ones pay about log2(n) latencies each, hidden by many threads per SM.
+// dependent load: launches on the uniform grid (ascending queries) run eval_runs_kernel, whose
+// lanes gallop a few knots from their previous query; launches with explicit positions run
+// eval_bisect_kernel, one query per thread paying about log2(n) latencies, hidden by many
+// threads per SM.
 #include <algorithm>
 
 #include "spl_device.cuh"
@@ -87,8 +90,109 @@ __device__ __forceinline__ double newint_variant32(double q, double xj, double x
   return (double)(sum * inv_ba);
 }
 
+// Bracket of q given a knot x_{j0} < q (the previous query's interval): galloping steps of 1, 2,
+// 4, ... knots from j0 (at most kGallopE of them; beyond, `far` is set and the rest of the
+// instance is bisected), then bisection of the last step; the same index as bracket_bisect.
+constexpr int kGallopE = 8;
+
+__device__ __forceinline__ long long bracket_from(const double *__restrict__ x, long long n, long long j0,
+                                                  long long kq, bool &far) {
+  long long lo = j0, hi, step = 1;  // x_lo < q throughout
+  far = false;
+  for (int s = 0;; ++s) {
+    hi = lo + step;
+    if (hi > n - 2) {
+      hi = n - 1;
+      break;
+    }
+    if (dkey(x[hi]) >= kq) break;
+    lo = hi;
+    step <<= 1;
+    if (s + 1 == kGallopE) {
+      hi = n - 1;
+      far = true;
+      break;
+    }
+  }
+  while (hi - lo > 1) {  // largest i in [lo, hi) with x_i < q
+    const long long mid = lo + ((hi - lo) >> 1);
+    if (dkey(x[mid]) < kq) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Each warp takes runs of 32 kRunE consecutive queries, lane l the queries run + l + 32 i: every
+// access of a step is contiguous across the warp, and a lane's successive queries lie 32 apart,
+// so sorted queries find their interval by galloping from the previous one (~2 log2 32 probes
+// near it instead of log2 n across the instance); a lane whose query lies below its previous one,
+// or far above it, bisects for the rest of the run, so any order gives the same brackets.
+constexpr int kRunE = 8;
+
 template <int kVariant, bool kF32>
-__global__ void __launch_bounds__(kThreadsE) eval_kernel(const Inst *__restrict__ insts, int ninst,
+__global__ void __launch_bounds__(kThreadsE) eval_runs_kernel(const Inst *__restrict__ insts, int ninst,
+                                                         long long total_q) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  constexpr long long kSpan = 32LL * kRunE;
+  int cur = -1;  // instance of the previous query of this lane, whose grid is cached
+  long long qb = 0, qe = 0;
+  Grid G{};
+  for (long long run = warp * kSpan; run < total_q; run += nwarps * kSpan) {
+    long long jprev = -1;  // interval of the lane's previous query in this run
+    bool gallop = true;    // the lane's queries have been ascending and close so far
+#pragma unroll 1
+    for (int i = 0; i < kRunE; ++i) {
+      const long long g = run + lane + 32LL * i;
+      if (g >= total_q) break;
+      if (cur < 0 || g < qb || g >= qe) {  // the instance owning query g: last with q_begin <= g
+        int lo = 0, hi = ninst - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (insts[mid].q_begin <= g) lo = mid; else hi = mid - 1;
+        }
+        cur = lo;
+        qb = insts[lo].q_begin;
+        qe = qb + insts[lo].mq;
+        G = insts[lo].xq ? Grid{} : make_grid(insts[lo].x, insts[lo].n, insts[lo].mq);
+        jprev = -1;
+      }
+      const Inst &I = insts[cur];
+      const long long n = I.n, k = g - qb;
+      const double *__restrict__ x = I.x;
+      double q;
+      if (I.xq) {
+        q = I.xq[k];
+        if (!finite64(q)) {
+          atomicOr(I.status, kStNonFinite);
+          continue;
+        }
+      } else {
+        q = G.at(k);
+      }
+      const long long kq = dkey(q);
+      long long j;
+      if (gallop && jprev >= 0 && dkey(x[jprev]) < kq) {
+        bool far;
+        j = bracket_from(x, n, jprev, kq, far);
+        if (far) gallop = false;
+      } else {
+        if (jprev >= 0) gallop = false;
+        j = bracket_bisect(x, n, kq);
+      }
+      jprev = j;
+      const double *__restrict__ y = I.y;
+      const double *__restrict__ ypp = I.ypp;
+      I.yq[k] = kF32 ? newint_variant32<kVariant>(q, x[j], x[j + 1], y[j], y[j + 1], ypp[j], ypp[j + 1])
+                     : newint_variant<kVariant>(q, x[j], x[j + 1], y[j], y[j + 1], ypp[j], ypp[j + 1]);
+      if (I.jq) I.jq[k] = (int32_t)j;
+    }
+  }
+}
+
+// Queries in any order (explicit positions): one query per thread, grid-stride, bisection.
+template <int kVariant, bool kF32>
+__global__ void __launch_bounds__(kThreadsE) eval_bisect_kernel(const Inst *__restrict__ insts, int ninst,
                                                          long long total_q) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   int cur = -1;  // instance whose grid is cached
@@ -125,20 +229,26 @@ __global__ void __launch_bounds__(kThreadsE) eval_kernel(const Inst *__restrict_
   }
 }
 
-cudaError_t launch_eval(const Inst *d_insts, int ninst, long long total_q, int variant, bool f32, int sm_count,
-                        cudaStream_t stream) {
+cudaError_t launch_eval(const Inst *d_insts, int ninst, long long total_q, int variant, bool f32, bool uniform,
+                        int sm_count, cudaStream_t stream) {
   if (total_q <= 0) return cudaSuccess;
-  const long long blocks =
-      std::min<long long>((total_q + kThreadsE - 1) / kThreadsE, (long long)sm_count * kBlocksPerSmE);
+  // uniform grids (ascending by construction): runs of queries per lane with galloping brackets;
+  // explicit positions (any order): one query per thread with bisection
+  const long long per_block = uniform ? (long long)kThreadsE * kRunE : (long long)kThreadsE;
+  const long long blocks = std::min<long long>((total_q + per_block - 1) / per_block, (long long)sm_count * kBlocksPerSmE);
   const unsigned grid = (unsigned)std::max<long long>(blocks, 1);
+#define SPL_EVAL_LAUNCH(V, F)                                                                         \
+  (uniform ? (eval_runs_kernel<V, F><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q), 0) \
+           : (eval_bisect_kernel<V, F><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q), 0))
   switch (variant * 2 + (f32 ? 1 : 0)) {
-    case 2: eval_kernel<1, false><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q); break;
-    case 3: eval_kernel<1, true><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q); break;
-    case 4: eval_kernel<2, false><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q); break;
-    case 5: eval_kernel<2, true><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q); break;
-    case 1: eval_kernel<0, true><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q); break;
-    default: eval_kernel<0, false><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q); break;
+    case 2: SPL_EVAL_LAUNCH(1, false); break;
+    case 3: SPL_EVAL_LAUNCH(1, true); break;
+    case 4: SPL_EVAL_LAUNCH(2, false); break;
+    case 5: SPL_EVAL_LAUNCH(2, true); break;
+    case 1: SPL_EVAL_LAUNCH(0, true); break;
+    default: SPL_EVAL_LAUNCH(0, false); break;
   }
+#undef SPL_EVAL_LAUNCH
   return cudaGetLastError();
 }
 

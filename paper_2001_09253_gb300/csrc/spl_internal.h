@@ -64,8 +64,9 @@ cudaError_t launch_scan_mixed(const Inst *d_insts, int ninst, long long total_ti
 // Separate evaluation (spl_eval.cu): queries q_begin .. q_begin+mq-1 of each instance, explicit
 // (Inst::xq) or on the uniform grid, with the y'' in Inst::ypp; variant = spl_eval_variant; f32:
 // the binary32 form of the mixed-precision plans.
-cudaError_t launch_eval(const Inst *d_insts, int ninst, long long total_q, int variant, bool f32, int sm_count,
-                        cudaStream_t stream);
+// uniform: no instance of the launch has explicit positions (the queries ascend).
+cudaError_t launch_eval(const Inst *d_insts, int ninst, long long total_q, int variant, bool f32, bool uniform,
+                        int sm_count, cudaStream_t stream);
 
 }  // namespace spl
 

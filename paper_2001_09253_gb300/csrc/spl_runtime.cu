@@ -459,8 +459,10 @@ cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, 
     if (launches) *launches += 2;
   }
   if (e == cudaSuccess && lp.separate_eval && lp.total_queries > 0) {
-    e = spl::launch_eval(insts, count, lp.total_queries, lp.eval_variant, lp.precision != SPL_PREC_F64, c->sm_count,
-                         st);
+    bool uniform = true;
+    for (const Inst &I : lp.insts) uniform = uniform && I.xq == nullptr;
+    e = spl::launch_eval(insts, count, lp.total_queries, lp.eval_variant, lp.precision != SPL_PREC_F64, uniform,
+                         c->sm_count, st);
     if (launches) *launches += 1;
   }
   return e;
