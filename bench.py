@@ -440,7 +440,7 @@ class Runner:
             out[label]["fastest"] = names[int(np.argmin([np.median(t) for t in times]))]
         res = {"workload": "evaluation only from a stored FP64 fit of the n = 1e7 curve (seed 1), M = 1e7 "
                            "queries: the uniform grid (sorted) and seeded uniform positions (unsorted), "
-                           "bisection bracketing", **out}
+                           "galloping brackets on the grid, bisection on unsorted positions", **out}
         return res, (pick, xq.cpu().numpy()[pick], samples)
 
     def n_schedule(self, draws=256, seed=5):
