@@ -271,3 +271,45 @@ def test_mixed_explicit_queries_and_stored_fit(ctx, refine, variant):
     st, _, yq2, jq2 = _run(ctx, plan, x, y, xq, ypp_in=ypp, want_ypp=False)
     assert st == 0
     assert np.array_equal(yq2, yq) and np.array_equal(jq2, jq)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_uniform_grid_batch_from_stored_fits(ctx, precision):
+    """Uniform grids evaluated from stored y'' for several instances in one launch: query counts
+    that end inside a warp's run of queries (so runs cross from one instance into the next),
+    an instance without queries, a single query, fewer and more queries than knots.  Brackets
+    bit-exact against the oracle's monotone sweep, values within the plan's tolerance of the
+    oracle's evaluation from the same y''."""
+    import torch
+    from paper_2001_09253_gb300 import spl
+    from parity_util import TOL_MIXED
+    dev = torch.device("cuda", ctx.device)
+    prec = spl.PREC_F64 if precision == "f64" else spl.PREC_F32_REFINE
+    tol = TOL_F64 if precision == "f64" else TOL_MIXED
+    plan = ctx.plan(20000, prec)
+    sizes = [(3, 1), (5, 300), (100, 0), (4097, 257), (777, 33), (64, 513), (20000, 5000), (1000, 2001)]
+    reqs, keep, cases = [], [], []
+    for i, (n, m) in enumerate(sizes):
+        x, y = synth.curve(40, n, instance=i)
+        yp1, ypn = (NAT, NAT) if i % 2 == 0 else (0.25 * i, -0.5)
+        ref = oracle.fit_eval(x, y, yp1, ypn, m)
+        xt, yt = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
+        pin = torch.from_numpy(np.ascontiguousarray(ref["ypp"])).to(dev)
+        yq = torch.full((max(m, 1),), np.nan, dtype=torch.float64, device=dev)
+        jq = torch.full((max(m, 1),), -7, dtype=torch.int32, device=dev)
+        reqs.append(spl.make_request(xt, yt, yp1, ypn, m, None, yq if m else None, jq if m else None,
+                                     ypp_in=pin))
+        keep += [xt, yt, pin, yq, jq]
+        cases.append((x, y, ref, yq, jq, m))
+    launches0 = ctx.stats()["kernel_launches"]
+    for t in ctx.submit_batch(plan, reqs, keep):
+        st, _ = ctx.wait(t, 60.0)
+        assert st == 0
+    assert ctx.stats()["kernel_launches"] - launches0 == 1  # one evaluation launch, no fit
+    for x, y, ref, yq, jq, m in cases:
+        if not m:
+            continue
+        j = jq.cpu().numpy()[:m].astype(np.int64)
+        assert np.array_equal(j, ref["jq"]), np.nonzero(j != ref["jq"])[0][:10]
+        e = yq_error(x, y, ref["ypp"], ref["jq"], yq.cpu().numpy()[:m], ref["yq"])
+        assert e <= tol, "S(x) error %.3e (n = %d, m = %d)" % (e, len(x), m)
