@@ -21,7 +21,10 @@
 namespace spl {
 
 constexpr int kThreadsE = 256;
-constexpr int kBlocksPerSmE = 8;
+// CTAs per SM: all resident at once within the register limit this imposes (51 per thread, no
+// spills), so a launch is one wave (8 CTAs at the 48-56 registers the kernels take unbounded
+// ran as a wave and a partial one: ~9 % slower on unsorted queries)
+constexpr int kBlocksPerSmE = 5;
 
 __device__ __forceinline__ long long bracket_bisect(const double *__restrict__ x, long long n, long long kq) {
   long long lo = 0, hi = n - 1;  // knots x_0..x_{n-2} below q: a count in [lo, hi]
@@ -129,7 +132,7 @@ __device__ __forceinline__ long long bracket_from(const double *__restrict__ x, 
 constexpr int kRunE = 8;
 
 template <int kVariant, bool kF32>
-__global__ void __launch_bounds__(kThreadsE) eval_runs_kernel(const Inst *__restrict__ insts, int ninst,
+__global__ void __launch_bounds__(kThreadsE, kBlocksPerSmE) eval_runs_kernel(const Inst *__restrict__ insts, int ninst,
                                                          long long total_q) {
   const int lane = threadIdx.x & 31;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(kThreadsE) eval_runs_kernel(const Inst *__rest
 
 // Queries in any order (explicit positions): one query per thread, grid-stride, bisection.
 template <int kVariant, bool kF32>
-__global__ void __launch_bounds__(kThreadsE) eval_bisect_kernel(const Inst *__restrict__ insts, int ninst,
+__global__ void __launch_bounds__(kThreadsE, kBlocksPerSmE) eval_bisect_kernel(const Inst *__restrict__ insts, int ninst,
                                                          long long total_q) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   int cur = -1;  // instance whose grid is cached
