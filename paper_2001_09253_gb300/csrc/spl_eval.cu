@@ -132,8 +132,8 @@ __device__ __forceinline__ long long bracket_from(const double *__restrict__ x, 
 constexpr int kRunE = 8;
 
 template <int kVariant, bool kF32>
-__global__ void __launch_bounds__(kThreadsE, kBlocksPerSmE) eval_runs_kernel(const Inst *__restrict__ insts, int ninst,
-                                                         long long total_q) {
+__global__ void __launch_bounds__(kThreadsE, kBlocksPerSmE)
+    eval_runs_kernel(const Inst *__restrict__ insts, int ninst, long long total_q) {
   const int lane = threadIdx.x & 31;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -195,8 +195,8 @@ __global__ void __launch_bounds__(kThreadsE, kBlocksPerSmE) eval_runs_kernel(con
 
 // Queries in any order (explicit positions): one query per thread, grid-stride, bisection.
 template <int kVariant, bool kF32>
-__global__ void __launch_bounds__(kThreadsE, kBlocksPerSmE) eval_bisect_kernel(const Inst *__restrict__ insts, int ninst,
-                                                         long long total_q) {
+__global__ void __launch_bounds__(kThreadsE, kBlocksPerSmE)
+    eval_bisect_kernel(const Inst *__restrict__ insts, int ninst, long long total_q) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   int cur = -1;  // instance whose grid is cached
   Grid G{};
@@ -238,7 +238,8 @@ cudaError_t launch_eval(const Inst *d_insts, int ninst, long long total_q, int v
   // uniform grids (ascending by construction): runs of queries per lane with galloping brackets;
   // explicit positions (any order): one query per thread with bisection
   const long long per_block = uniform ? (long long)kThreadsE * kRunE : (long long)kThreadsE;
-  const long long blocks = std::min<long long>((total_q + per_block - 1) / per_block, (long long)sm_count * kBlocksPerSmE);
+  const long long blocks =
+      std::min<long long>((total_q + per_block - 1) / per_block, (long long)sm_count * kBlocksPerSmE);
   const unsigned grid = (unsigned)std::max<long long>(blocks, 1);
 #define SPL_EVAL_LAUNCH(V, F)                                                                         \
   (uniform ? (eval_runs_kernel<V, F><<<grid, kThreadsE, 0, stream>>>(d_insts, ninst, total_q), 0) \

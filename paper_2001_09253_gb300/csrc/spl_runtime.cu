@@ -490,7 +490,8 @@ cudaError_t enqueue(spl_ctx *c, const LaunchPlan &lp, char *pin_base, unsigned *
     if (e != cudaSuccess) break;
     e = cudaMemcpyAsync(c->arena + h.off_x, h.hx, 8 * h.n, cudaMemcpyHostToDevice, s_in);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->arena + h.off_y, h.hy, 8 * h.n, cudaMemcpyHostToDevice, s_in);
-    if (e == cudaSuccess && h.hxq) e = cudaMemcpyAsync(c->arena + h.off_xq, h.hxq, 8 * h.m, cudaMemcpyHostToDevice, s_in);
+    if (e == cudaSuccess && h.hxq)
+      e = cudaMemcpyAsync(c->arena + h.off_xq, h.hxq, 8 * h.m, cudaMemcpyHostToDevice, s_in);
     if (e == cudaSuccess && h.hyppin)
       e = cudaMemcpyAsync(c->arena + h.off_yppin, h.hyppin, 8 * h.n, cudaMemcpyHostToDevice, s_in);
   }

@@ -235,7 +235,8 @@ spl_status spl_serve_create(spl_ctx *c, const spl_serve_desc *d, spl_server **ou
   s->ctx = c;
   s->d = *d;
   // tile_rows 0: per request (serve_tile_for); otherwise one length, a whole number of chunks
-  if (s->d.tile_rows) s->d.tile_rows = (uint32_t)spl::serve_tile_rows((int)std::min<uint32_t>(s->d.tile_rows, 1u << 20));
+  if (s->d.tile_rows)
+    s->d.tile_rows = (uint32_t)spl::serve_tile_rows((int)std::min<uint32_t>(s->d.tile_rows, 1u << 20));
   const int scratch_rows = s->d.tile_rows ? (int)s->d.tile_rows : kServeTileMax;
   if (!s->d.idle_timeout_ms) s->d.idle_timeout_ms = 200;
   s->device = spl_ctx_device(c);
