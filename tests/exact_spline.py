@@ -46,12 +46,17 @@ def _solve_exact(A, b):
     return x
 
 
+def _rational(v):
+    """A Fraction or a decimal string is taken as given; anything else as its binary64 value."""
+    return v if isinstance(v, Fraction) else Fraction(v) if isinstance(v, str) else Fraction(float(v))
+
+
 class ExactSpline:
     """The exact spline through (x_i, y_i); slopes None mean a natural end."""
 
     def __init__(self, x, y, slope0=None, slope1=None):
-        X = [Fraction(float(v)) for v in x]
-        Y = [Fraction(float(v)) for v in y]
+        X = [_rational(v) for v in x]
+        Y = [_rational(v) for v in y]
         n = len(X)
         assert n >= 3
         npc = n - 1
