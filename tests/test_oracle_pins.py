@@ -62,26 +62,28 @@ def test_printed_natural_table():
 
 
 def load_true_tables():
-    """Per-knot deltas (13 x 8: x, y, then NR and "our" for natural, flat, twist) and the six
-    printed mean square errors."""
-    rows, mse = [], None
+    """Per-knot deltas (13 x 8: x, y, then NR and "our" for natural, flat, twist), the six
+    printed mean square errors of y'' and the two of the interpolated curve."""
+    rows, mse, mse_full = [], None, None
     with open(os.path.join(GOLDEN, "test_compare_true.txt")) as f:
         for line in f:
             line = line.strip()
             if not line or line.startswith("#"):
                 continue
-            if line.startswith("mse"):
+            if line.startswith("mse_full"):
+                mse_full = np.array([float(v) for v in line.split()[1:]])
+            elif line.startswith("mse"):
                 mse = np.array([float(v) for v in line.split()[1:]])
             else:
                 rows.append([float(v) for v in line.split()])
-    return np.array(rows), mse
+    return np.array(rows), mse, mse_full
 
 
 def test_true_tables_fixture_consistent():
     """The transcribed deltas of Tables tbl:test_compare_nat / _flat / _twist reproduce the
     mean square errors the paper prints for them (Tables tbl:mse_nat / _flat / _twist)."""
-    t, mse = load_true_tables()
-    assert t.shape == (13, 8) and mse.shape == (6,)
+    t, mse, mse_full = load_true_tables()
+    assert t.shape == (13, 8) and mse.shape == (6,) and mse_full.shape == (2,)
     assert np.array_equal(t[:, 0], np.array(TEST_KNOTS, float))
     assert np.array_equal(t[:, 1], np.array(TEST_VALUES, float))
     np.testing.assert_allclose(np.mean(t[:, 2:] ** 2, axis=0), mse, rtol=2e-5)
@@ -97,7 +99,7 @@ def test_oracle_rounding_matches_printed_true_tables(case):
     delta of one of them to its 5 digits: the oracle performs the paper's operations in the
     paper's order (a changed operation or order moves the deltas; a wrong term moves them by
     orders of magnitude)."""
-    t, mse = load_true_tables()
+    t, mse, _ = load_true_tables()
     bc = BC_CASES[case]
     ex = ExactSpline(TEST_KNOTS, TEST_VALUES, bc[0], bc[1])
     st, ypp = oracle.fit(TEST_KNOTS, TEST_VALUES, _slope(bc[0]), _slope(bc[1]))
@@ -110,6 +112,20 @@ def test_oracle_rounding_matches_printed_true_tables(case):
             for v, pair in zip(d, zip(nr, our)) for p in pair]
     knots_same = sum(any(same[2 * k: 2 * k + 2]) for k in range(13))
     assert knots_same >= 9, knots_same
+
+
+def test_interpolated_curve_error_matches_printed_mse():
+    """Table tbl:mse_full: the twist-end spline of the 13-knot curve evaluated at 2048 evenly
+    spaced queries (monotone sweep, one-division form) against the "true" curve.  The oracle's
+    mean square error against the exact spline of the binary64 inputs is within the printed
+    ones (~1e-30; a wrong term in the cubic or a wrong bracket gives errors many orders larger)."""
+    _, _, mse_full = load_true_tables()
+    ex = ExactSpline(TEST_KNOTS, TEST_VALUES, -1.0, 1.0)
+    res = oracle.fit_eval(TEST_KNOTS, TEST_VALUES, -1.0, 1.0, 2048)
+    assert res["status"] == oracle.OK
+    d = np.array([float(Fraction(float(v)) - ex.piece_value(int(j), float(q)))
+                  for v, j, q in zip(res["yq"], res["jq"], res["xq"])])
+    assert np.mean(d ** 2) <= 1.01 * np.max(mse_full)
 
 
 @pytest.mark.parametrize("bc", BC_CASES)
