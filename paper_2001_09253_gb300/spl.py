@@ -332,7 +332,7 @@ class Server:
         land first; False when the caller has made the arrays ready itself."""
         import torch
         r = make_request(x, y, yp1, ypn, m, ypp_out, yq_out, jq_out)
-        if sync:
+        if sync and x.is_cuda:  # host arrays are refused below (the loop reads device memory only)
             torch.cuda.current_stream(x.device).synchronize()
         t = ctypes.c_uint64()
         _check(self.lib.spl_serve_submit(self.handle, ctypes.byref(r), ctypes.byref(t)), "spl_serve_submit")

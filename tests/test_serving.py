@@ -180,6 +180,11 @@ def test_bad_request_is_isolated(ctx):
     for i, t in enumerate(tickets):
         s, _ = srv.wait(t)
         assert s == (spl.ERR_NONFINITE if i == 2 else spl.OK)
+    # host arrays are refused at submission (the loop reads device memory only)
+    p, o = pool[0], outs[0]
+    with pytest.raises(spl.SplError) as ei:
+        srv.submit(torch.from_numpy(p["x"]), torch.from_numpy(p["y"]), p["bc"][0], p["bc"][1], p["m"], o[0], o[1])
+    assert ei.value.status == spl.ERR_INVALID_ARG
     srv.close()
 
 
