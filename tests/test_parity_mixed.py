@@ -132,8 +132,10 @@ def test_refined_batch(ctx):
         assert yq_error(x, y, ref["ypp"], ref["jq"], k[3].cpu().numpy(), ref["yq"]) <= TOL_MIXED
 
 
-def test_full_size_n1e7(ctx):
-    """n = M = 10^7, seed 1, in the benchmark's launch configuration; all outputs compared."""
+@pytest.mark.parametrize("refine", [0, 1])
+def test_full_size_n1e7(ctx, refine):
+    """n = M = 10^7, seed 1, in the benchmark's launch configurations (no refinement, one
+    refinement step); all outputs compared."""
     import torch
     n = 10_000_000
     x, y = spl.generate_curve(1, n)
@@ -141,12 +143,54 @@ def test_full_size_n1e7(ctx):
     ypp = torch.empty(n, dtype=torch.float64, device="cuda")
     yq = torch.empty(n, dtype=torch.float64, device="cuda")
     jq = torch.empty(n, dtype=torch.int32, device="cuda")
-    t = ctx.submit(_plan(ctx), x, y, NAT, NAT, n, ypp, yq, jq)
+    t = ctx.submit(_plan(ctx, refine=refine), x, y, NAT, NAT, n, ypp, yq, jq)
     st, _ = ctx.wait(t, 300)
     assert st == 0
     ref = oracle.fit_eval(hx, hy, NAT, NAT, n)
     e1 = ypp_error(ypp.cpu().numpy(), ref["ypp"])
     assert np.array_equal(jq.cpu().numpy().astype(np.int64), ref["jq"])
     e2 = yq_error(hx, hy, ref["ypp"], ref["jq"], yq.cpu().numpy(), ref["yq"])
-    print("mixed n=1e7: y'' err %.3e  S err %.3e" % (e1, e2))
-    assert e1 <= TOL_MIXED and e2 <= TOL_MIXED
+    print("mixed n=1e7, %d refinement steps: y'' err %.3e  S err %.3e" % (refine, e1, e2))
+    assert e1 <= (1e-8 if refine else TOL_MIXED) and e2 <= TOL_MIXED
+
+
+def test_batched_workload_4096(ctx):
+    """The batched workload in the benchmark's launch configuration: 4,096 instances with n
+    log-uniform in [1e2, 1e5] (seed 2, instance i its own curve), natural ends, M = n, binary32
+    + one refinement step, one reusable batch replayed from a CUDA graph.  Every status OK; all
+    outputs of 64 sampled instances (and the largest and smallest) compared with the oracle."""
+    import torch
+    count = 4096
+    sizes = synth.sizes_loguniform(2, count, 1e2, 1e5)
+    total = int(sizes.sum())
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    X, Y, P, Q = (torch.empty(total, dtype=torch.float64, device="cuda") for _ in range(4))
+    for i, nn in enumerate(sizes):
+        xi, yi = spl.generate_curve(2, int(nn), instance=i)
+        X[off[i]:off[i + 1]].copy_(xi)
+        Y[off[i]:off[i + 1]].copy_(yi)
+    torch.cuda.synchronize()
+    plan = _plan(ctx, refine=1, max_n=int(sizes.max()))
+    reqs = [spl.make_request(X[off[i]:off[i + 1]], Y[off[i]:off[i + 1]], NAT, NAT, int(nn),
+                             P[off[i]:off[i + 1]], Q[off[i]:off[i + 1]]) for i, nn in enumerate(sizes)]
+    b = ctx.batch(plan, reqs, keep=(X, Y, P, Q))
+    first = None
+    for _ in range(2):  # the second replay gives the same outputs, bit for bit
+        P.fill_(np.nan)
+        Q.fill_(np.nan)
+        torch.cuda.synchronize()
+        b.launch()
+        assert (b.wait() == 0).all()
+        if first is None:
+            first = (P.clone(), Q.clone())
+    b.close()
+    assert torch.equal(first[0], P) and torch.equal(first[1], Q)
+    rng = np.random.default_rng(11)
+    pick = set(rng.choice(count, 64, replace=False).tolist()) | {int(np.argmax(sizes)), int(np.argmin(sizes))}
+    for i in sorted(pick):
+        x, y = synth.curve(2, int(sizes[i]), instance=i)
+        ref = oracle.fit_eval(x, y, NAT, NAT, len(x))
+        ypp = P[off[i]:off[i + 1]].cpu().numpy()
+        yq = Q[off[i]:off[i + 1]].cpu().numpy()
+        assert ypp_error(ypp, ref["ypp"]) <= 1e-8, i
+        assert yq_error(x, y, ref["ypp"], ref["jq"], yq, ref["yq"]) <= TOL_MIXED, i
