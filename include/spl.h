@@ -17,7 +17,9 @@
  *           section "Fast Interpolation".
  *   Bracket indices are bit-exact with a sequential FP64 reference; floating-point
  *   outputs agree with it to a relative 1e-12 (SPL_PREC_F64) or 1e-5
- *   (SPL_PREC_F32_REFINE), normwise.
+ *   (SPL_PREC_F32_REFINE): normwise for y'' (max error over max |y''|), per query for
+ *   S(x_k) (relative to the largest of |y_j|, |y_{j+1}|, |S(x_k)| and the curvature term
+ *   h_j^2 max(|y''_j|, |y''_{j+1}|)/6 of its interval).
  *
  * Conventions for every entry point:
  *   - Return an spl_status; nothing is thrown across the ABI.  SPL_OK is 0,
@@ -225,7 +227,8 @@ spl_status spl_get_stats(spl_ctx *ctx, spl_stats *out);
 
 /* Reusable batch: the descriptors of count device-memory requests are uploaded once and
  * the launch is captured in a CUDA graph; every spl_batch_launch replays it on the
- * context's stream (one persistent kernel over all tiles of all instances).  Statuses
+ * context's stream (one persistent kernel over all tiles of all instances; two, the fit and
+ * then the refinement with the evaluation, for a plan with a refinement step).  Statuses
  * of the last launch are read with spl_batch_wait. */
 spl_status spl_batch_create(spl_ctx *ctx, spl_plan *plan, const spl_request *reqs, uint32_t count,
                             spl_batch **out);
@@ -245,10 +248,9 @@ spl_status spl_generate_curve(uint64_t seed, uint64_t instance, uint64_t n, doub
  *
  * A server owns a persistent kernel (one CTA per SM, cooperative launch) on its own stream:
  * a scheduler warp takes requests from a ring in mapped host memory and publishes their tiles;
- * worker warps solve published tiles, one tile per warp (binary32 solve and cubic, exact binary64
- * differences and query positions: the mixed path without refinement, tiles of tile_rows rows
- * rounded up to a multiple of 32) while further requests arrive, so the
- * work of requests that arrive while others run overlaps on the device.  A request is admitted
+ * worker warps solve published tiles, one tile per warp (binary32 solve and cubic, exact
+ * binary64 differences and query positions: the mixed path without refinement), so the work of
+ * requests that arrive while others run overlaps on the device.  A request is admitted
  * when a slot is free, its tiles fit the tile map and its footprint (16 n + 8 m bytes, plus
  * 8 n for y'' and 4 m for indices when requested) fits in budget_bytes; otherwise it waits in
  * a host FIFO and is admitted by a later submit/poll/wait.  The device loop exits after
@@ -258,9 +260,10 @@ spl_status spl_generate_curve(uint64_t seed, uint64_t instance, uint64_t n, doub
  * loop may read the inputs and write the outputs at once.  Results equal those of a
  * single-request server, bit for bit, whatever else is in flight.
  *   max_inflight     requests resident on the device at once (slots), 1..65536.
- *   tile_rows        knots per tile, >= 16 (rounded up to a multiple of 32); shorter tiles lower the
- *                    latency of a request, longer ones raise the throughput (each tile repeats 96
- *                    rows of start-up).  0: per request, about 32 tiles each, 256..1024 rows.
+ *   tile_rows        knots per tile, >= 16 (rounded up to a multiple of 32); shorter tiles
+ *                    lower the latency of a request, longer ones raise the throughput (each
+ *                    tile repeats 96 rows of start-up).  0: per request, about 32 tiles each,
+ *                    256..1024 rows.
  *   budget_bytes     HBM budget for the footprints of resident requests.
  *   max_tiles        tile-map capacity (0 = max(2^20, 64 max_inflight)).
  *   idle_timeout_ms  0 = 200.
