@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 from paper_2001_09253_gb300 import build, spl
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "spl.h")
@@ -45,3 +47,25 @@ def test_create_rejects_bad_descriptors_without_touching_a_gpu():
 
 def test_sm103a_only():
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    """Without a CUDA device the entry points that compute fail with SPL_ERR_CUDA: nothing
+    falls back to the CPU (only meaningful on a machine without a GPU)."""
+    import numpy as np
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    lib = spl.load()
+    h = ctypes.c_void_p()
+    d = spl.CtxDesc(device=0, max_slots=4, stream=None, arena=None, arena_bytes=64 << 20)
+    assert lib.spl_create(ctypes.byref(h), ctypes.byref(d)) == spl.ERR_CUDA
+    assert not h.value
+    x = np.arange(10, dtype=np.float64)
+    y = np.sin(x)
+    yq = np.full(10, np.nan)
+    st = ctypes.c_int32(spl.PENDING)
+    r = lib.spl_fit_eval_noalloc(x.ctypes.data, y.ctypes.data, 10, 1e32, 1e32, 10, None, yq.ctypes.data, None,
+                                 ctypes.byref(st))
+    assert r == spl.ERR_CUDA
+    assert np.isnan(yq).all()  # no output written by any other route
