@@ -27,6 +27,20 @@ MUTANTS = [
     ("natural sentinel not strict", "slope > 0.99e30", "slope >= 0.99e30"),
     ("grid product and sum fused order", "double t = (double)k * step;\n    xq[k] = t + x[0];",
      "xq[k] = x[0] + (double)k * (x[n - 1] - x[0]) / (double)(m - 1);"),
+    ("first clamped row with b and c swapped", "*b = 2.0 * h;\n    *c = h;", "*b = h;\n    *c = 2.0 * h;"),
+    ("sign of the end slope", "*d = 6.0 * (ypn - (y[n - 1] - y[n - 2]) / h);",
+     "*d = 6.0 * ((y[n - 1] - y[n - 2]) / h - ypn);"),
+    ("interior widths transposed in the slopes", "/ cj - (y[j] - y[j - 1]) / aj);", "/ aj - (y[j] - y[j - 1]) / cj);"),
+    ("interior a and c swapped", "*a = aj;\n  *c = cj;", "*a = cj;\n  *c = aj;"),
+    ("first c' formed from d", "cp[0] = c / b;", "cp[0] = d / b;"),
+    ("back substitution skips the second-to-last row", "for (int64_t i = n - 2; i >= 0; --i)",
+     "for (int64_t i = n - 3; i >= 0; --i)"),
+    ("grid step over m instead of m - 1", "/ (double)(m - 1);", "/ (double)m;"),
+    ("last grid point not forced to the last knot", "  xq[m - 1] = x[n - 1];\n", ""),
+    ("y''_{j+1} replaced by y''_j in the cubic", "ppj1 * left * (left * left - w2)", "ppj * left * (left * left - w2)"),
+    ("squared width taken from the left offset", "double w2 = width * width;", "double w2 = left * left;"),
+    ("equal knots let through", "if (!(x[i] > x[i - 1])) return ORC_NOT_INCREASING;",
+     "if (!(x[i] >= x[i - 1])) return ORC_NOT_INCREASING;"),
 ]
 
 

@@ -291,6 +291,13 @@ def test_query_grid_is_numpy_linspace():
         assert np.array_equal(xq, np.linspace(x[0], x[-1], m))
     x, _ = synth.curve(0, 9)
     assert np.array_equal(oracle.grid(x, 1), np.linspace(x[0], x[-1], 1))
+    # grids whose last product-and-sum point misses the last knot by rounding: the last query
+    # is the knot itself (numpy.linspace sets it so too)
+    for knots, m in (([0.1, 0.4, 0.7, 1.0], 4), ([-1.1, 0.5, 3.3], 2), ([0.0, 1.0, 2.5], 78)):
+        x = np.array(knots)
+        assert (m - 1) * ((x[-1] - x[0]) / (m - 1)) + x[0] != x[-1]  # the case meant
+        xq = oracle.grid(x, m)
+        assert np.array_equal(xq, np.linspace(x[0], x[-1], m)) and xq[-1] == x[-1]
 
 
 def test_bracket_sweep_and_bisection_match_brute_force():
