@@ -41,6 +41,10 @@ MUTANTS = [
     ("squared width taken from the left offset", "double w2 = width * width;", "double w2 = left * left;"),
     ("equal knots let through", "if (!(x[i] > x[i - 1])) return ORC_NOT_INCREASING;",
      "if (!(x[i] >= x[i - 1])) return ORC_NOT_INCREASING;"),
+    ("bisection sends a tie to the right", "if (x[mid] < q) lo = mid + 1;", "if (x[mid] <= q) lo = mid + 1;"),
+    ("bisection never reaches the last interval", "int64_t lo = 0, hi = n - 1;", "int64_t lo = 0, hi = n - 2;"),
+    ("sweep never reaches the last interval", "while (i + 1 < n - 1 && x[i + 1] < xq[k]) ++i;",
+     "while (i + 1 < n - 2 && x[i + 1] < xq[k]) ++i;"),
 ]
 
 
