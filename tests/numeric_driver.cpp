@@ -41,3 +41,21 @@ extern "C" {
 int t_diff_small_f32(double b, double a, float *out) { return spl::diff_small_f32(b, a, out) ? 1 : 0; }
 int t_diff_up_f32(double b, double a, float *out) { return spl::diff_up_f32(b, a, out) ? 1 : 0; }
 }
+
+extern "C" {
+void t_two_sum(float a, float b, float *s, float *e) {
+  spl::F2 r = spl::two_sum(a, b);
+  *s = r.hi;
+  *e = r.lo;
+}
+void t_two_prod(float a, float b, float *p, float *e) {
+  spl::F2 r = spl::two_prod(a, b);
+  *p = r.hi;
+  *e = r.lo;
+}
+void t_df_mul(float ah, float al, float bh, float bl, float *ph, float *pl) {
+  spl::F2 q = spl::df_mul(spl::F2{ah, al}, spl::F2{bh, bl});
+  *ph = q.hi;
+  *pl = q.lo;
+}
+}

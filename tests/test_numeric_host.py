@@ -18,7 +18,8 @@ CSRC = os.path.join(os.path.dirname(HERE), "paper_2001_09253_gb300", "csrc")
 def lib():
     d = tempfile.mkdtemp(prefix="splnum_")
     so = os.path.join(d, "libnum.so")
-    subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I", CSRC, "-o", so,
+    # no contraction of a*b + c: the error-free transformations must round each step as written
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-I", CSRC, "-o", so,
                     os.path.join(HERE, "numeric_driver.cpp")], check=True)
     L = ctypes.CDLL(so)
     L.t_diff_f32.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_float)]
@@ -227,8 +228,18 @@ def _setup_df(L):
     L.t_df_div.argtypes = [f, f, f, f, pf, pf]
     L.t_df_add.argtypes = [f, f, f, f, pf, pf]
     L.t_df_mul_f.argtypes = [f, f, f, pf, pf]
-    for nm in ("t_df_div", "t_df_add", "t_df_mul_f"):
+    L.t_df_mul.argtypes = [f, f, f, f, pf, pf]
+    L.t_two_sum.argtypes = [f, f, pf, pf]
+    L.t_two_prod.argtypes = [f, f, pf, pf]
+    for nm in ("t_df_div", "t_df_add", "t_df_mul_f", "t_df_mul", "t_two_sum", "t_two_prod"):
         getattr(L, nm).restype = None
+
+
+def _pair(L, name, *args):
+    a = ctypes.c_float()
+    b = ctypes.c_float()
+    getattr(L, name)(*args, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
 
 
 def _rand_f2(rng):
@@ -264,6 +275,29 @@ def test_double_float_difference_and_arithmetic(lib):
         c = float(np.float32(rng.normal()))
         p = _f2(lib, "t_df_mul_f", ah, al, c)
         assert abs(p - A * Fraction(c)) <= abs(A * Fraction(c)) * Fraction(1, 2 ** 46)
+
+
+def test_error_free_sum_and_product(lib):
+    """TwoSum and TwoProduct return the rounded result and its exact error: s + e == a + b and
+    p + e == a * b exactly (operands within binary32's normal range, products not underflowing),
+    with s and p the binary32 roundings; the double-float product carries ~46 bits."""
+    _setup_df(lib)
+    rng = np.random.default_rng(5)
+    for _ in range(4000):
+        a = float(np.float32(rng.normal() * 2.0 ** int(rng.integers(-30, 31))))
+        b = float(np.float32(rng.normal() * 2.0 ** int(rng.integers(-30, 31))))
+        s, e = _pair(lib, "t_two_sum", a, b)
+        assert Fraction(s) + Fraction(e) == Fraction(a) + Fraction(b)
+        assert s == rn32(Fraction(a) + Fraction(b)) or Fraction(a) + Fraction(b) == 0
+        p, e = _pair(lib, "t_two_prod", a, b)
+        assert Fraction(p) + Fraction(e) == Fraction(a) * Fraction(b)
+        assert p == rn32(Fraction(a) * Fraction(b))
+    for _ in range(3000):
+        ah, al = _rand_f2(rng)
+        bh, bl = _rand_f2(rng)
+        A, B = Fraction(ah) + Fraction(al), Fraction(bh) + Fraction(bl)
+        q = _f2(lib, "t_df_mul", ah, al, bh, bl)
+        assert abs(q - A * B) <= abs(A * B) * Fraction(1, 2 ** 45)
 
 
 def test_float_double_conversions(lib):
