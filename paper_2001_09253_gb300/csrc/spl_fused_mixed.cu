@@ -1,6 +1,6 @@
 // Mixed-precision fit + evaluation, one thread per tile of knots: the kernel of launches of many
-// small instances, of the serving loop and of the no-allocation entry point (long instances go
-// to the warp-cooperative kernel of spl_mixed_scan.cu).
+// small instances and of the no-allocation entry point (long instances and the serving loop use
+// the warp-cooperative tiles of spl_mixed_scan.cu).
 //
 // Same method and tiling as the plain FP64 kernel (tridiagonal system of eq. (init_val) with
 // the end rows of "Start and End Derivatives", Thomas recurrences of "Implementation",
