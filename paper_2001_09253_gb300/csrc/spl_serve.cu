@@ -1,5 +1,5 @@
 // Host side of the serving loop (include/spl.h, spl_serve_*): continuous batching of
-// independent instances onto the persistent device loop of spl_fused_mixed.cu.
+// independent instances onto the persistent device loop of spl_mixed_scan.cu (serve_kernel).
 //
 // A request is admitted when a slot is free, its tiles fit in the device tile map and its
 // footprint (inputs and outputs) fits in the HBM budget; otherwise it waits in a host FIFO and
