@@ -92,19 +92,33 @@ def kernel_hash(files) -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(which: str):
-    """DRAM bytes per launch of the kernel from its committed ncu summary, or None when the
-    summary is absent or was taken on a different version of the kernel sources."""
+def profiled_field(which: str, key: str):
+    """A number recorded as `key: value` in the kernel's committed ncu summary, or None when the
+    summary is absent, lacks it, or was taken on a different version of the kernel sources."""
     path, files = PROFILES[which]
     try:
         text = open(path).read()
     except OSError:
         return None
     mh = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
-    mb = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
-    if not mh or not mb or mh.group(1) != kernel_hash(files):
+    mv = re.search(r"^" + re.escape(key) + r":\s*([0-9.eE+-]+)", text, re.M)
+    if not mh or not mv or mh.group(1) != kernel_hash(files):
         return None
-    return float(mb.group(1))
+    try:
+        return float(mv.group(1))
+    except ValueError:
+        return None
+
+
+def profiled_traffic(which: str):
+    """DRAM bytes per launch of the kernel (ncu: dram__bytes_read.sum + dram__bytes_write.sum)."""
+    return profiled_field(which, "dram_bytes_per_launch_full_size")
+
+
+def profiled_fraction(which: str, key: str):
+    """A percentage counter of the committed ncu summary as a fraction, or None."""
+    v = profiled_field(which, key)
+    return None if v is None else v / 100.0
 
 
 class Clocks:
@@ -659,7 +673,8 @@ def run_ours(args, world, rank, local):
     }
     others["mixed_f32"]["roofline"] = {"bound": "hbm", "traffic": profiled_traffic("mixed"),
                                        "achieved": others["mixed_f32"]["gb_per_s"], "peak": hbm, "unit": "GB/s",
-                                       "frac": others["mixed_f32"]["hbm_frac_of_measured"]}
+                                       "frac": others["mixed_f32"]["hbm_frac_of_measured"],
+                                       "issue_active_ncu": profiled_fraction("mixed", "issue_active_pct")}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -691,6 +706,7 @@ def run_ours(args, world, rank, local):
                               "peak = 2 FP64 ops/clk/SM x 152 SMs x 2.07 GHz (one op per lane per clock)"
                               % FLOPS_PER_POINT),
                      "frac_of_fma_counted_peak": achieved / PEAK_FP64_TFLOPS,
+                     "fp64_pipe_active_ncu": profiled_fraction("f64", "fp64_pipe_active_pct"),
                      "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / hbm if hbm else None},
         "cpu_baseline": cpu,
         "e2e": e2e,

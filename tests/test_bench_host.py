@@ -45,6 +45,29 @@ def test_traffic_is_dropped_once_the_kernel_changes(bench, tmp_path, monkeypatch
     assert bench.profiled_traffic("f64") is None
 
 
+def test_profiled_counters_follow_the_same_rule(bench, tmp_path, monkeypatch):
+    """The pipe-utilisation counters reported beside each roofline come from the same summaries,
+    as fractions, under the same source-hash rule."""
+    expect = {"f64": "fp64_pipe_active_pct", "mixed": "issue_active_pct"}
+    for which, key in expect.items():
+        path, files = bench.PROFILES[which]
+        text = open(path).read()
+        assert key + ":" in text, which
+        fresh = tmp_path / ("fresh_%s.md" % which)
+        fresh.write_text(text)
+        monkeypatch.setitem(bench.PROFILES, which, (str(fresh), files))
+        text_hash_ok = bench.kernel_hash(files) in text
+        v = bench.profiled_fraction(which, key)
+        if text_hash_ok:
+            assert v is not None and 0.0 < v <= 1.0, which
+        stale = tmp_path / ("stale_%s.md" % which)
+        stale.write_text(text.replace(bench.kernel_hash(files), "f" * 16))
+        monkeypatch.setitem(bench.PROFILES, which, (str(stale), files))
+        assert bench.profiled_fraction(which, key) is None
+        monkeypatch.setitem(bench.PROFILES, which, (str(fresh), files))
+        assert bench.profiled_field(which, "no_such_counter") is None
+
+
 class _Done:
     def terminate(self):
         pass
