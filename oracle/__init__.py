@@ -63,9 +63,6 @@ def _bind(path):
     L.orc_eval.restype = None
     L.orc_fit_eval.argtypes = [i64, dp, dp, d, d, i64, dp, dp, lp, dp]
     L.orc_fit_eval.restype = ctypes.c_int
-    i32p = ctypes.POINTER(ctypes.c_int32)
-    L.orc_batch.argtypes = [i64, lp, lp, dp, dp, dp, dp, dp, dp, lp, dp, i32p]
-    L.orc_batch.restype = i64
     return L
 
 
@@ -182,20 +179,3 @@ def fit_eval(x, y, yp1=NATURAL, ypn=NATURAL, m: int | None = None):
     if st != OK:
         return {"status": st, "ypp": None, "xq": None, "jq": None, "yq": None}
     return {"status": st, "ypp": ypp[:n], "xq": xq[:m], "jq": jq[:m], "yq": yq[:m]}
-
-
-def batch(off, qoff, x, y, yp1, ypn):
-    """Many instances laid out back to back (off/qoff are prefix offsets of length count+1)."""
-    off = np.ascontiguousarray(off, dtype=np.int64)
-    qoff = np.ascontiguousarray(qoff, dtype=np.int64)
-    x, y = _f64(x), _f64(y)
-    yp1, ypn = _f64(yp1), _f64(ypn)
-    count = len(off) - 1
-    ypp = np.zeros(max(int(off[-1]), 1))
-    xq = np.zeros(max(int(qoff[-1]), 1))
-    jq = np.zeros(max(int(qoff[-1]), 1), dtype=np.int64)
-    yq = np.zeros(max(int(qoff[-1]), 1))
-    status = np.zeros(max(count, 1), dtype=np.int32)
-    lib().orc_batch(count, _lp(off), _lp(qoff), _dp(x), _dp(y), _dp(yp1), _dp(ypn), _dp(ypp), _dp(xq),
-                    _lp(jq), _dp(yq), status.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
-    return {"status": status[:count], "ypp": ypp, "xq": xq, "jq": jq, "yq": yq}

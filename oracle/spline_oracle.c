@@ -201,21 +201,3 @@ int orc_fit_eval(int64_t n, const double *x, const double *y, double yp1, double
   orc_eval(n, x, y, ypp, m, xq, jq, yq);
   return ORC_OK;
 }
-
-/* Many independent instances back to back, each laid out contiguously at
- * offsets off[i] (knots) and qoff[i] (queries); used to time the oracle on a
- * batch.  Returns the number of instances whose status was not ORC_OK. */
-int64_t orc_batch(int64_t count, const int64_t *off, const int64_t *qoff, const double *x,
-                  const double *y, const double *yp1, const double *ypn, double *ypp, double *xq,
-                  int64_t *jq, double *yq, int32_t *status) {
-  int64_t bad = 0;
-  for (int64_t i = 0; i < count; ++i) {
-    int64_t n = off[i + 1] - off[i];
-    int64_t m = qoff[i + 1] - qoff[i];
-    int st = orc_fit_eval(n, x + off[i], y + off[i], yp1[i], ypn[i], m, ypp + off[i],
-                          xq + qoff[i], jq + qoff[i], yq + qoff[i]);
-    if (status) status[i] = st;
-    if (st != ORC_OK) ++bad;
-  }
-  return bad;
-}

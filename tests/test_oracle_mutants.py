@@ -45,6 +45,12 @@ MUTANTS = [
     ("bisection never reaches the last interval", "int64_t lo = 0, hi = n - 1;", "int64_t lo = 0, hi = n - 2;"),
     ("sweep never reaches the last interval", "while (i + 1 < n - 1 && x[i + 1] < xq[k]) ++i;",
      "while (i + 1 < n - 2 && x[i + 1] < xq[k]) ++i;"),
+    ("evaluation takes y''_j at both ends of the interval", "ypp[j], ypp[j + 1]);", "ypp[j], ypp[j]);"),
+    ("evaluation takes the right knot's value twice", "y[j], y[j + 1], ypp[j]", "y[j + 1], y[j + 1], ypp[j]"),
+    ("non-finite values let through", "if (!isfinite(x[i]) || !isfinite(y[i])) return ORC_NONFINITE;",
+     "if (!isfinite(x[i])) return ORC_NONFINITE;"),
+    ("whole path brackets against the first knot only", "orc_bracket_sweep(n, x, m, xq, jq);\n  orc_eval",
+     "for (int64_t k = 0; k < m; ++k) jq[k] = 0;\n  orc_eval"),
 ]
 
 
