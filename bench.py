@@ -35,6 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "instances/sec and GB/s (% roofline) at fixed oracle error; p50/p99 latency"
+WORKLOAD = "fit+eval, n=M=1e7, seed 1, natural ends, plain FP64"
 N_POINTS = 10_000_000
 SEED = 1
 # Algorithmic work per point (knot and query, M = n), from the paper's own operation counts:
@@ -232,8 +233,8 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "instances/s", "n_gpus": args.gpus,
         "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "fit+eval, n=M=1e7, seed 1, natural ends", "n": N_POINTS, "m": N_POINTS,
-                   "instances_per_step": 1},
+        "config": {"workload": WORKLOAD, "n": N_POINTS, "m": N_POINTS, "instances_per_step": 1,
+                   "l2": "inputs+outputs 320 MB > 129 MB L2, no flush", "parallelism": "one instance per GPU"},
         "cpu_baseline": {"value": v, "unit": "instances/s", "cores": 1, "kind": "oracle",
                          "sample": "%d full n=1e7 instances, single thread" % steps},
         "e2e": {"value": v, "unit": "instances/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -693,7 +694,7 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": main["value"], "unit": "instances/s", "n_gpus": world, "steps": r.K,
         "warmup": r.W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "fit+eval, n=M=1e7, seed 1, natural ends, plain FP64", "n": n, "m": n,
+        "config": {"workload": WORKLOAD, "n": n, "m": n,
                    "instances_per_step": 1, "l2": "inputs+outputs 320 MB > 129 MB L2, no flush",
                    "parallelism": "one instance per GPU"},
         "points_per_s": main["value"] * n, "gb_per_s": gbs,

@@ -200,16 +200,30 @@ typedef struct spl_stats {
 
 const char *spl_status_str(int32_t status);
 
+/* Creates a context (device, stream, arena) for the fit and evaluation of section "Fast
+ * Interpolation" / "Generating Second Derivatives"; SPL_ERR_INVALID_ARG for a null or malformed
+ * descriptor (max_slots < 1, arena_bytes < 1 MiB, an arena not 256-byte aligned), SPL_ERR_CUDA when
+ * the device is absent or an allocation fails.  *out is NULL on failure. */
 spl_status spl_create(spl_ctx **out, const spl_ctx_desc *desc);
 void spl_destroy(spl_ctx *ctx);  /* waits for the context's work; NULL is a no-op.  Destroy the
                                     context's servers first: they use its arena. */
 
+/* Options of the problem statement of section "Implementation" (new_second_derivative: knots,
+ * values, start and end derivatives) and of section "Curve Interpolation" (the evaluated form and
+ * its queries), fixed for the requests that use the plan.  SPL_ERR_INVALID_ARG for max_n < 3, an
+ * unknown precision, query mode or form, refine_steps outside 0..1 (0 for SPL_PREC_F64), or
+ * 0 < tile_rows < 16. */
 spl_status spl_plan_create(spl_ctx *ctx, const spl_plan_desc *desc, spl_plan **out);
 void spl_plan_destroy(spl_plan *plan);
 
-/* Validate and enqueue one instance on the context's stream.  On SPL_OK *ticket names it
- * until spl_poll/spl_wait returns a final status.  Device-side validation errors
- * (NOT_INCREASING, NONFINITE) are reported at completion. */
+/* Validate and enqueue one instance on the context's stream: the second derivatives of section
+ * "Generating Second Derivatives" with the end rows of "Start and End Derivatives"
+ * (new_second_derivative), then newint of "Fast Interpolation" at the request's queries.  On
+ * SPL_OK *ticket names it until spl_poll/spl_wait returns a final status.  Host-side checks return
+ * SPL_ERR_INVALID_ARG (n < 3 or > max_n, null arrays, a NaN or -inf end slope), SPL_ERR_BUDGET
+ * (footprint above the arena) or SPL_ERR_QUEUE_FULL (no slot or memory now).  The paper's input
+ * asserts (strictly increasing knots) and finite values are checked on the device and reported at
+ * completion (NOT_INCREASING, NONFINITE). */
 spl_status spl_submit(spl_ctx *ctx, spl_plan *plan, const spl_request *req, uint64_t *ticket);
 
 /* Many instances in one launch; tickets[i] names req[i].  All requests must use the same
@@ -217,10 +231,14 @@ spl_status spl_submit(spl_ctx *ctx, spl_plan *plan, const spl_request *req, uint
 spl_status spl_submit_batch(spl_ctx *ctx, spl_plan *plan, const spl_request *reqs, uint32_t count,
                             uint64_t *tickets);
 
-/* Non-blocking.  Returns SPL_PENDING, or the final status (then the ticket is released). */
+/* Completion of a request submitted for the fit and evaluation of sections "Generating Second
+ * Derivatives" and "Fast Interpolation".  Non-blocking.  Returns SPL_PENDING, or the final status
+ * (then the ticket is released), or SPL_ERR_UNKNOWN_TICKET. */
 spl_status spl_poll(spl_ctx *ctx, uint64_t ticket, spl_result *res);
 
-/* Blocks up to timeout_ns (bounded; never forever); SPL_ERR_TIMEOUT when it runs out. */
+/* As spl_poll (completion of the fit and evaluation of sections "Generating Second Derivatives"
+ * and "Fast Interpolation"), blocking up to timeout_ns (bounded; never forever);
+ * SPL_ERR_TIMEOUT when it runs out (the ticket stays valid). */
 spl_status spl_wait(spl_ctx *ctx, uint64_t ticket, uint64_t timeout_ns, spl_result *res);
 
 spl_status spl_get_stats(spl_ctx *ctx, spl_stats *out);
@@ -323,8 +341,12 @@ void spl_serve_destroy(spl_server *srv);
  * and larger n returns SPL_ERR_BUDGET without launching anything.  The call makes no
  * cudaMalloc, cudaFree or other allocating call.
  *
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress),
- * once per device; make that first call before any stream capture.  Every call shares the
+ * The first call in each CUDA context looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it, keyed by the context's unique ID: make that first call
+ * before any stream capture.  A device reset (cudaDeviceReset) destroys the context and the
+ * array with it; the next call then runs in a new context and looks the address up again.
+ * The context is the one current on the calling thread, or else the current device's primary
+ * context (bound with cudaSetDevice).  Every call shares the
  * same array and leaves the previous call's contents in it (each call clears what must start
  * at zero): calls whose work overlaps on the GPU (different streams, or several host threads)
  * race and give wrong results; order them on one stream or synchronise between them.

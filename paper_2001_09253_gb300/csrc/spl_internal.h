@@ -34,6 +34,18 @@ cudaError_t launch_fused_f64(const Inst *d_insts, int ninst, long long total_til
 
 // Mixed-precision fused fit + evaluation (spl_fused_mixed.cu).
 long long threads_mixed(int sm_count, long long total_tiles);
+int mixed_threads_per_sm();  // threads of one ring-kernel CTA (one CTA per SM)
+// Tile length of the ring kernel for ONE instance of n points: 16-row tiles while n is too small
+// to keep every SM busy with long tiles (one tile's serial chain is then the time; measured on
+// GB300 for n = 1e3..1e6, 16 rows ran the binary32 fit ~3x faster than 128), else the length
+// that gives every thread of one wave one tile, at least 128 rows.
+inline int mixed_ring_tile_rows(int sm_count, unsigned long long n) {
+  if (n <= (unsigned long long)sm_count * 13000ull) return 16;
+  const unsigned long long target = (unsigned long long)sm_count * (unsigned long long)mixed_threads_per_sm();
+  unsigned long long L = (n + target - 1) / target;
+  L = L < 128 ? 128 : (L > (1u << 20) ? (1u << 20) : L);
+  return (int)L;
+}
 // fit_only: first pass of the refined path (y'' in binary32 to each Inst::z, no queries).
 cudaError_t launch_fused_mixed(const Inst *d_insts, int ninst, long long total_tiles, int sm_count,
                                unsigned long long *counter, cudaStream_t stream, bool fit_only);
@@ -48,7 +60,6 @@ cudaError_t launch_serve(const ServeArgs &args, int sm_count, cudaStream_t strea
 int serve_tile_rows(int tile_rows);
 long long serve_rows_cap(int tile_rows);
 size_t serve_scratch_bytes(int sm_count, int tile_rows);
-int mixed_threads_per_sm();  // threads of one mixed-kernel CTA (one CTA per SM)
 
 // Warp-cooperative binary32 fit + evaluation (spl_mixed_scan.cu): one warp per tile of
 // scan_mixed_tile_rows rows (a multiple of 32), per-warp scratch of scratch_bytes_scan_mixed

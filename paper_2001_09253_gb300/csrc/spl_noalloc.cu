@@ -19,25 +19,69 @@ constexpr size_t kScratchBytes = kZOff + 4 * kMaxN;
 // the device address comes from cudaGetSymbolAddress (see setup_device).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 128;
-std::mutex g_mu;
-unsigned char *g_addr[kMaxDevices];  // device address of g_noalloc_scratch, per device
-int g_sms[kMaxDevices];
+// The array's device address, looked up once per CUDA context.  A context is recognised by its
+// process-unique ID (cuCtxGetId), not by the device ordinal: a device reset destroys the primary
+// context and the module with it, so the context that replaces it (whatever its handle) gets its
+// own look-up instead of a stale address.  The driver calls are fetched through the runtime, so
+// the library needs no link-time dependency on the driver library.
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
 
-// Once per device, with that device current: look up the array's device address.
+constexpr int kMaxContexts = 64;
+struct AddrEntry {
+  unsigned long long ctx_id;
+  unsigned char *addr;
+  int sms;
+};
+std::mutex g_mu;
+AddrEntry g_cache[kMaxContexts];
+int g_cached = 0;
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+
+spl_status driver_fns() {
+  if (g_ctx_current && g_ctx_id) return SPL_OK;
+  void *f1 = nullptr, *f2 = nullptr;
+  cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = cudaDriverEntryPointSymbolNotFound;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+      q1 != cudaDriverEntryPointSuccess || !f1)
+    return SPL_ERR_CUDA;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+      q2 != cudaDriverEntryPointSuccess || !f2)
+    return SPL_ERR_CUDA;
+  g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+  g_ctx_id = reinterpret_cast<CtxGetIdFn>(f2);
+  return SPL_OK;
+}
+
+// With the caller's device current: the array's device address in the current context (looked
+// up with cudaGetSymbolAddress on the first call in each context) and the device's SM count.
 spl_status setup_device(int dev, unsigned char **addr, int *sms) {
-  if (dev < 0 || dev >= kMaxDevices) return SPL_ERR_CUDA;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SPL_ERR_CUDA;
-    int s = 0;
-    if (cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SPL_ERR_CUDA;
-    g_sms[dev] = s;
-    g_addr[dev] = static_cast<unsigned char *>(p);
+  spl_status s = driver_fns();
+  if (s != SPL_OK) return s;
+  void *ctx = nullptr;
+  if (g_ctx_current(&ctx) != 0) return SPL_ERR_CUDA;
+  if (!ctx) {  // no context bound to this thread yet: cudaSetDevice binds the device's primary one
+    if (cudaSetDevice(dev) != cudaSuccess || g_ctx_current(&ctx) != 0 || !ctx) return SPL_ERR_CUDA;
   }
-  *addr = g_addr[dev];
-  *sms = g_sms[dev];
+  unsigned long long id = 0;
+  if (g_ctx_id(ctx, &id) != 0) return SPL_ERR_CUDA;
+  for (int i = 0; i < g_cached; ++i) {
+    if (g_cache[i].ctx_id == id) {
+      *addr = g_cache[i].addr;
+      *sms = g_cache[i].sms;
+      return SPL_OK;
+    }
+  }
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SPL_ERR_CUDA;
+  int n_sm = 0;
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SPL_ERR_CUDA;
+  // a full table keeps serving by looking the address up again on each call
+  if (g_cached < kMaxContexts) g_cache[g_cached++] = AddrEntry{id, static_cast<unsigned char *>(p), n_sm};
+  *addr = static_cast<unsigned char *>(p);
+  *sms = n_sm;
   return SPL_OK;
 }
 
@@ -73,9 +117,7 @@ extern "C" spl_status spl_fit_eval_noalloc(const double *x, const double *y, uin
   I.x = x; I.y = y; I.ypp = ypp_out; I.yq = yq_out; I.jq = nullptr;
   I.n = (long long)n; I.m = (long long)m;
   I.yp1 = yp1; I.ypn = ypn;
-  long long target = (long long)sms * spl::mixed_threads_per_sm();  // one tile per thread of one wave
-  long long L = ((long long)n + target - 1) / target;
-  L = L < 128 ? 128 : L;
+  const long long L = spl::mixed_ring_tile_rows(sms, n);  // the runtime's rule for one instance
   I.tile_rows = (int)L;
   I.ntiles = ((long long)n + L - 1) / L;
   I.tile_begin = 0;

@@ -204,18 +204,15 @@ int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points, uint3
   // 16-row tiles halve the FP64 time (0.36-0.41 -> 0.17 ms) and cut the binary32 time 3x; past
   // a few 1e5 points (FP64) the halo work that every short tile repeats outweighs the shorter
   // chain, and from ~1e6 the grouped long tiles below win.
-  const uint64_t upto16 = (uint64_t)c->sm_count * (precision == SPL_PREC_F64 ? 2000ull : 13000ull);
-  const uint64_t upto32 = (uint64_t)c->sm_count * (precision == SPL_PREC_F64 ? 8000ull : 0ull);
+  if (precision != SPL_PREC_F64) return spl::mixed_ring_tile_rows(c->sm_count, total_points);
+  const uint64_t upto16 = (uint64_t)c->sm_count * 2000ull;
+  const uint64_t upto32 = (uint64_t)c->sm_count * 8000ull;
   if (total_points <= upto16) return 16;
   if (total_points <= upto32) return 32;
-  const long long per_sm = precision == SPL_PREC_F64 ? spl::f64_threads_per_sm() : spl::mixed_threads_per_sm();
-  const long long target = (long long)c->sm_count * per_sm;
-  long long L = (long long)((total_points + target - 1) / target);
-  if (precision == SPL_PREC_F64) {
-    const long long warps = std::max<long long>(target / 32, 1);
-    const long long per_warp = (long long)((total_points + warps - 1) / warps);
-    L = (per_warp + spl::overhang_rows_f64() + spl::lane0_short_rows_f64() + 31) / 32;
-  }
+  const long long target = (long long)c->sm_count * spl::f64_threads_per_sm();
+  const long long warps = std::max<long long>(target / 32, 1);
+  const long long per_warp = (long long)((total_points + warps - 1) / warps);
+  long long L = (per_warp + spl::overhang_rows_f64() + spl::lane0_short_rows_f64() + 31) / 32;
   L = std::max<long long>(L, 128);
   L = std::min<long long>(L, 1 << 20);
   return (int)L;

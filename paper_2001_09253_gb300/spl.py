@@ -387,10 +387,13 @@ class Server:
 def fit_eval_noalloc(x, y, yp1=NATURAL, ypn=NATURAL, m=None, ypp_out=None, yq_out=None, stream=None,
                      want_status=True):
     """spl_fit_eval_noalloc: one instance, no allocation inside the library (device tensors
-    in and out, n <= NOALLOC_MAX_N).  Returns (call status, device status or None)."""
+    in and out, n <= NOALLOC_MAX_N).  m defaults to n when yq_out is given, else to 0 (fit only).
+    Returns (call status, device status or None)."""
     L = load()
     n = int(x.shape[0])
-    m = n if m is None else int(m)
+    if m is None:
+        m = n if yq_out is not None else 0
+    m = int(m)
     st = ctypes.c_int32(PENDING)
     s = L.spl_fit_eval_noalloc(_ptr(x), _ptr(y), n, float(yp1), float(ypn), m, _ptr(ypp_out), _ptr(yq_out),
                                stream.cuda_stream if stream is not None else None,
