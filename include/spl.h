@@ -324,6 +324,19 @@ spl_status spl_serve_stats(spl_server *srv, uint64_t *loop_launches, uint64_t *w
 /* Stops the device loop (bounded wait) and releases the server's memory. */
 void spl_serve_destroy(spl_server *srv);
 
+/* Self-test of the division replacement of the SPL_PREC_F64 kernel (no counterpart in the paper:
+ * the paper divides with the CPU's IEEE division).  The FP64 kernel forms the slopes of eq.
+ * (init_val) and its reciprocals with a MUFU seed refined by a Newton step plus a Markstein
+ * correction instead of IEEE divisions; this call runs those routines and CUDA's correctly rounded
+ * reciprocal and quotient on the same operands, elementwise:
+ *   r_fast[i] = the kernel's 1/den[i],  q_fast[i] = the kernel's num[i]/den[i],
+ *   r_ieee[i] = RN(1/den[i]),           q_ieee[i] = RN(num[i]/den[i]).
+ * All arrays are device arrays of count doubles (caller-owned), on the current device; the work is
+ * enqueued on `stream` (NULL = legacy default stream).  SPL_ERR_INVALID_ARG for a null array,
+ * SPL_ERR_CUDA when the launch fails. */
+spl_status spl_selftest_div64(const double *num, const double *den, uint64_t count, double *q_fast, double *r_fast,
+                              double *q_ieee, double *r_ieee, void *stream);
+
 /* One instance without any allocation, for callers that cannot allocate device memory:
  * host applications that own all of the GPU's memory themselves (a simulation or game
  * engine, a database or plug-in host that hands out fixed pools), and code under a hard

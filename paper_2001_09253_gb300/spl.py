@@ -32,7 +32,7 @@ EXPORTS = [
     "spl_submit_batch", "spl_poll", "spl_wait", "spl_get_stats", "spl_batch_create", "spl_batch_launch",
     "spl_batch_wait", "spl_batch_destroy", "spl_generate_scratch_bytes", "spl_generate_curve",
     "spl_fit_eval_noalloc", "spl_serve_create", "spl_serve_submit", "spl_serve_poll", "spl_serve_wait",
-    "spl_serve_replay", "spl_serve_stats", "spl_serve_destroy",
+    "spl_serve_replay", "spl_serve_stats", "spl_serve_destroy", "spl_selftest_div64",
 ]
 NOALLOC_MAX_N = 1048576
 
@@ -122,10 +122,12 @@ def load(path: str | None = None):
         L.spl_serve_stats.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)]
         L.spl_serve_destroy.argtypes = [vp]
         L.spl_serve_destroy.restype = None
+        L.spl_selftest_div64.argtypes = [vp, vp, u64, vp, vp, vp, vp, vp]
         for name in ["spl_create", "spl_plan_create", "spl_submit", "spl_submit_batch", "spl_poll", "spl_wait",
                      "spl_get_stats", "spl_batch_create", "spl_batch_launch", "spl_batch_wait",
                      "spl_generate_curve", "spl_fit_eval_noalloc", "spl_serve_create", "spl_serve_submit",
-                     "spl_serve_poll", "spl_serve_wait", "spl_serve_replay", "spl_serve_stats"]:
+                     "spl_serve_poll", "spl_serve_wait", "spl_serve_replay", "spl_serve_stats",
+                     "spl_selftest_div64"]:
             getattr(L, name).restype = i32
         _lib = L
         return L
@@ -399,6 +401,18 @@ def fit_eval_noalloc(x, y, yp1=NATURAL, ypn=NATURAL, m=None, ypp_out=None, yq_ou
                                stream.cuda_stream if stream is not None else None,
                                ctypes.byref(st) if want_status else None)
     return s, (st.value if want_status else None)
+
+
+def selftest_div64(num, den, stream=None):
+    """spl_selftest_div64 on device tensors: returns (q_fast, r_fast, q_ieee, r_ieee) tensors."""
+    import torch
+    L = load()
+    n = int(num.shape[0])
+    outs = [torch.empty(max(n, 1), dtype=torch.float64, device=num.device) for _ in range(4)]
+    st = stream if stream is not None else torch.cuda.current_stream(num.device)
+    _check(L.spl_selftest_div64(_ptr(num), _ptr(den), n, *[_ptr(o) for o in outs], st.cuda_stream),
+           "spl_selftest_div64")
+    return tuple(o[:n] for o in outs)
 
 
 def generate_curve(seed: int, n: int, instance: int = 0, device: int = 0, stream=None):

@@ -70,6 +70,23 @@ def curve(seed: int, n: int, instance: int = 0):
     return x, y
 
 
+def curve_continuous(seed: int, n: int, instance: int = 0):
+    """The benchmark curve with the paper's continuous increments (section "Curve
+    Interpolation", step 5, read literally): eps_i uniform on [0, 1) with 53 random bits (an
+    eps of exactly 0 becomes 1e-4), x_i = x_{i-1} + eps_i summed left to right in binary64, so
+    knot gaps carry up to 53 significant bits and the partial sums round.  Host-only (the
+    sequential rounded sum has no bit-identical parallel form)."""
+    if n <= 0:
+        return np.zeros(0), np.zeros(0)
+    rx = draws(stream_key(seed, instance, STREAM_X), n - 1)
+    eps = (rx >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    eps[eps == 0.0] = 1e-4
+    x = np.concatenate([[0.0], eps]).cumsum()
+    ry = draws(stream_key(seed, instance, STREAM_Y), n)
+    y = (ry >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    return x, y
+
+
 def curve_adversarial(seed: int, n: int, decades: float = 8.0):
     """Knots with gap ratios spread over many decades (log-uniform gaps in
     [10^-decades, 1]) and values in [-1, 1): stresses the conditioning of the
