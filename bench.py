@@ -211,6 +211,20 @@ def pct(vals, q):
     return s[min(len(s) - 1, int(q * len(s)))] if s else None
 
 
+def dist_summary(a):
+    """A timing distribution as the paper reports its own (section "Curve Interpolation": no single
+    central value describes such timings): median with the 16th/84th percentiles, the tail, the
+    10 % trimmed mean."""
+    a = np.asarray(a, dtype=np.float64)
+    if a.size == 0:
+        return None
+    lo_, hi_ = np.quantile(a, [0.1, 0.9])
+    trimmed = a[(a >= lo_) & (a <= hi_)]
+    return {"count": int(a.size), "min": float(a.min()), "p16": float(np.quantile(a, 0.16)),
+            "median": float(np.median(a)), "p84": float(np.quantile(a, 0.84)), "p99": float(np.quantile(a, 0.99)),
+            "trimmed_mean_10": float(trimmed.mean()), "mean": float(a.mean()), "std": float(a.std())}
+
+
 # ------------------------------------------------------------------ reference arm (oracle)
 
 def run_reference(args, world, rank):
@@ -418,6 +432,38 @@ class Runner:
             return e0.elapsed_time(e1), float(res.device_ms), wall
         return e0.elapsed_time(e1)
 
+    def config1(self, reps=200):
+        """The smallest configuration: n = M = 1,000 (seed 0), natural and clamped (-1, 1) ends,
+        one request at a time through spl_submit + spl_wait, FP64 and binary32 with one refinement
+        step.  Latency per request: device (the library's CUDA events from the descriptor copy to
+        the status copy back) and wall (host clock around the Python submit and wait), as
+        distributions over `reps` requests after warm-up."""
+        torch, spl = self.torch, self.spl
+        from paper_2001_09253_gb300 import synth
+        n = 1000
+        hx, hy = synth.curve(0, n)
+        x = torch.from_numpy(hx).to(self.dev)
+        y = torch.from_numpy(hy).to(self.dev)
+        ypp = torch.empty(n, dtype=torch.float64, device=self.dev)
+        yq = torch.empty(n, dtype=torch.float64, device=self.dev)
+        out = {}
+        for label, prec, refine in (("f64", spl.PREC_F64, 0), ("mixed_refine1", spl.PREC_F32_REFINE, 1)):
+            plan = self.ctx.plan(n, prec, refine_steps=refine)
+            for bcl, (a, b) in (("natural", (spl.NATURAL, spl.NATURAL)), ("clamped", (-1.0, 1.0))):
+                dev_ms, wall_ms = [], []
+                for r in range(self.W + reps):
+                    w0 = time.perf_counter()
+                    t = self.ctx.submit(plan, x, y, a, b, n, ypp, yq)
+                    st, res = self.ctx.wait(t, 60.0)
+                    wl = (time.perf_counter() - w0) * 1e3
+                    assert st == spl.OK, spl.status_str(st)
+                    if r >= self.W:
+                        dev_ms.append(float(res.device_ms))
+                        wall_ms.append(wl)
+                out["%s/%s" % (label, bcl)] = {"device_ms": dist_summary(dev_ms), "wall_ms": dist_summary(wall_ms)}
+        return {"workload": "n = M = 1000, seed 0, natural and clamped (-1, 1) ends, one request at a time",
+                "requests_per_case": reps, **out}, (hx, hy)
+
     def eval_variants(self, reps=None):
         """The three forms of section "Fast Interpolation" that the paper benchmarks (orig: one
         reciprocal then a multiply; noinv: a division at the end; vol: orig with the reciprocal
@@ -435,27 +481,29 @@ class Runner:
         xq = torch.from_numpy(rng.uniform(lo, hi, n)).to(self.dev)
         yq = torch.empty(n, dtype=torch.float64, device=self.dev)
         jq = torch.empty(n, dtype=torch.int32, device=self.dev)
-        names = ["orig", "noinv", "vol"]
+        names = ["orig", "noinv", "vol", "noop"]
         out, samples = {}, {}
         pick = np.sort(rng.choice(n, size=20000, replace=False))
         for mode, label in ((spl.QUERY_UNIFORM, "sorted"), (spl.QUERY_EXPLICIT, "unsorted")):
-            plans = [self.ctx.plan(n, spl.PREC_F64, query_mode=mode, eval_variant=v) for v in range(3)]
-            times = [[] for _ in range(3)]
+            plans = [self.ctx.plan(n, spl.PREC_F64, query_mode=mode, eval_variant=v) for v in range(4)]
+            times = [[] for _ in range(4)]
             q = xq if mode == spl.QUERY_EXPLICIT else None
             for rep in range(self.W + K):
-                for v in rng.permutation(3):
+                for v in rng.permutation(4):
                     ms = self._timed_submit(plans[v], n, yq, jq, xq=q, ypp_in=ypp)
                     if rep >= self.W:
                         times[v].append(ms)
-                    if rep == self.W + K - 1:
+                    if rep == self.W + K - 1 and v < 3:
                         samples[(label, names[v])] = (yq.cpu().numpy()[pick], jq.cpu().numpy()[pick])
-            out[label] = {names[v]: {"ms_median": float(np.median(times[v])), "ms_min": float(np.min(times[v])),
-                                     "queries_per_s": n / (np.median(times[v]) * 1e-3), "reps": K}
-                          for v in range(3)}
-            out[label]["fastest"] = names[int(np.argmin([np.median(t) for t in times]))]
+            out[label] = {names[v]: {"ms": dist_summary(times[v]), "queries_per_s": n / (np.median(times[v]) * 1e-3),
+                                     "reps": K} for v in range(4)}
+            out[label]["fastest"] = names[int(np.argmin([np.median(t) for t in times[:3]]))]
+            # the paper's reading of its control loop: evaluation cost above query generation + bracketing
+            out[label]["orig_minus_noop_ms"] = float(np.median(times[0]) - np.median(times[3]))
         res = {"workload": "evaluation only from a stored FP64 fit of the n = 1e7 curve (seed 1), M = 1e7 "
                            "queries: the uniform grid (sorted) and seeded uniform positions (unsorted), "
-                           "galloping brackets on the grid, bisection on unsorted positions", **out}
+                           "galloping brackets on the grid, bisection on unsorted positions; noop = query "
+                           "generation and bracketing only (the paper's control loop)", **out}
         return res, (pick, xq.cpu().numpy()[pick], samples)
 
     def n_schedule(self, draws=256, seed=5):
@@ -506,11 +554,7 @@ class Runner:
                 a = a[mask]
             if a.size == 0:
                 return None
-            lo_, hi_ = np.quantile(a, [0.1, 0.9])
-            trimmed = a[(a >= lo_) & (a <= hi_)]
-            return {"count": int(a.size), "min": float(a.min()), "median": float(np.median(a)),
-                    "trimmed_mean_10": float(trimmed.mean()), "mean": float(a.mean()),
-                    "p99": float(np.quantile(a, 0.99)), "std": float(a.std())}
+            return dist_summary(a)
 
         bins = {"n<1e3": sizes_f < 1e3, "1e3<=n<1e5": (sizes_f >= 1e3) & (sizes_f < 1e5), "n>=1e5": sizes_f >= 1e5}
         out = {k: {"all": dist(v), **{b: dist(v, msk) for b, msk in bins.items()}} for k, v in ns.items()}
@@ -603,6 +647,26 @@ def serving(r, pool_count=512, seed=3, lo=1e2, hi=1e6, rate=20000.0, warm_s=1.0,
                                   "points_per_s": total / (t_ms * 1e-3), "ms_per_pool": t_ms}
     b.close()
     res["served_over_plain_instances_per_s"] = res["saturation"]["value"] / res["plain_f64_same_pool"]["value"]
+    # the same pool as one non-served binary32 batch (graph-captured launch over all of it), without
+    # and with refinement: what continuous batching buys beyond the drop to binary32
+    for refine in (0, 1):
+        planm = r.plan(spl.PREC_F32_REFINE, refine, max_n=int(sizes.max()))
+        bm = r.ctx.batch(planm, reqs, keep=(X, Y, P, Q))
+        for _ in range(2):
+            bm.launch()
+            assert (bm.wait() == 0).all()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(r.stream)
+        for _ in range(K):
+            bm.launch()
+        e1.record(r.stream)
+        assert (bm.wait() == 0).all()
+        tm = e0.elapsed_time(e1) / K
+        res["plain_mixed_refine%d_same_pool" % refine] = {"value": pool_count / (tm * 1e-3), "unit": "instances/s",
+                                                          "points_per_s": total / (tm * 1e-3), "ms_per_pool": tm}
+        bm.close()
+    res["served_over_plain_same_precision"] = (res["saturation"]["value"] /
+                                               res["plain_mixed_refine0_same_pool"]["value"])
     return res, (sizes, seed, r.rank * pool_count, sample)
 
 
@@ -644,6 +708,7 @@ def run_ours(args, world, rank, local):
     served, sdata = (None, None) if args.no_serving else serving(r)
     variants, vdata = r.eval_variants()
     schedule = r.n_schedule()
+    small, c1data = r.config1()
     if rank != 0:
         r.ctx.close()
         return
@@ -662,15 +727,18 @@ def run_ours(args, world, rank, local):
                 "latency_ms": {"p50": res["p50_ms"], "p99": res["p99_ms"]}, "gpu_launches": res["launches"],
                 "dtype": dtype, "tolerance": tol}
 
+    # the large distributions first, the compact per-configuration entries last (a reader of the
+    # line's tail sees those)
     others = {
+        "n_schedule": schedule,
+        "newint_variants": variants,
+        "n1000": small,
         "mixed_f32": path_entry(mixed0, "n=M=1e7 seed 1, binary32 solve + cubic, exact binary64 differences "
                                         "and query positions, no refinement", TOL["mixed"], "f32"),
         "mixed_f32_refine1": path_entry(mixed1, "same, plus one refinement step of y'' against a double-float "
                                                 "residual (two launches)", TOL["mixed"], "f32+df"),
         "batched": batched,
         "serving": served,
-        "newint_variants": variants,
-        "n_schedule": schedule,
     }
     others["mixed_f32"]["roofline"] = {"bound": "hbm", "traffic": profiled_traffic("mixed"),
                                        "achieved": others["mixed_f32"]["gb_per_s"], "peak": hbm, "unit": "GB/s",
@@ -680,6 +748,11 @@ def run_ours(args, world, rank, local):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu, errs = cpu_baseline_and_errors(r, main, mixed0, mixed1, bdata, sdata, vdata)
+        others_cpu = cpu_baselines_other(bdata, sdata, c1data)
+        others["n1000"]["cpu_baseline"] = others_cpu.get("n1000")
+        others["batched"]["cpu_baseline"] = others_cpu.get("batched")
+        if served is not None:
+            others["serving"]["cpu_baseline"] = others_cpu.get("serving_pool")
         if served is not None:
             others["serving"]["error_vs_oracle"] = errs["serving"]
         others["mixed_f32"]["error_vs_oracle"] = errs["mixed0"]
@@ -715,8 +788,120 @@ def run_ours(args, world, rank, local):
         "clocks": main["clocks"],
         "other_configs": others,
     }
+    line["summary"] = summary(line)
     print(json.dumps(line), flush=True)
     r.ctx.close()
+
+
+def oracle_rate(curves, threads: int):
+    """The FP64 oracle, as it stands, over a list of (x, y) instances (natural ends, M = n) on
+    `threads` host threads (ctypes releases the interpreter lock while the C code runs).  Returns
+    (instances per second, seconds)."""
+    import concurrent.futures as cf
+    import oracle
+
+    def one(xy):
+        r = oracle.fit_eval(xy[0], xy[1], oracle.NATURAL, oracle.NATURAL, len(xy[0]))
+        assert r["status"] == oracle.OK
+        return 0
+
+    t0 = time.perf_counter()
+    if threads <= 1:
+        for xy in curves:
+            one(xy)
+    else:
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(one, curves))
+    el = time.perf_counter() - t0
+    return len(curves) / el, el
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def cpu_baselines_other(bdata, sdata, c1data):
+    """Host baselines of the other workloads, the oracle as it stands: the smallest configuration
+    single-threaded (the paper's methodology), the batched workload single-threaded and on all
+    host cores (parallel over instances), the served pool on all host cores."""
+    import oracle
+    from paper_2001_09253_gb300 import synth
+    cores = host_cores()
+    out = {}
+    if c1data is not None:
+        hx, hy = c1data
+        oracle.fit_eval(hx, hy)
+        reps, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < 1.0:
+            oracle.fit_eval(hx, hy, oracle.NATURAL, oracle.NATURAL, len(hx))
+            reps += 1
+        el = time.perf_counter() - t0
+        out["n1000"] = {"value": reps / el, "unit": "instances/s", "us_per_instance": 1e6 * el / reps, "cores": 1,
+                        "kind": "oracle", "sample": "%d repetitions of the n = 1000 instance (seed 0), single "
+                                                    "thread, Python call overhead included" % reps}
+    if bdata is not None:
+        sizes = bdata[0]
+        curves = [synth.curve(2, int(nn), instance=i) for i, nn in enumerate(sizes)]
+        v1, el1 = oracle_rate(curves[:1024], 1)
+        vn, eln = oracle_rate(curves, cores)
+        out["batched"] = {"single_thread": {"value": v1, "unit": "instances/s", "cores": 1, "kind": "oracle",
+                                            "sample": "first 1024 of the 4096 instances (%.1f s)" % el1},
+                          "all_cores": {"value": vn, "unit": "instances/s", "cores": cores, "kind": "oracle",
+                                        "sample": "all 4096 instances, one per task (%.1f s)" % eln}}
+    if sdata is not None:
+        sizes_s, seed_s, base_s = sdata[0], sdata[1], sdata[2]
+        curves = [synth.curve(seed_s, int(nn), instance=base_s + i) for i, nn in enumerate(sizes_s)]
+        vn, eln = oracle_rate(curves, cores)
+        out["serving_pool"] = {"value": vn, "unit": "instances/s", "cores": cores, "kind": "oracle",
+                               "sample": "the %d pool instances once, one per task (%.1f s); the served stream "
+                                         "cycles the same pool" % (len(curves), eln)}
+    return out
+
+
+def summary(line):
+    """The headline numbers of every configuration, compact, at the end of the JSON line."""
+    def g(d, *ks):
+        for k in ks:
+            if not isinstance(d, dict) or k not in d or d[k] is None:
+                return None
+            d = d[k]
+        return round(d, 6) if isinstance(d, float) else d
+
+    oc = line.get("other_configs", {})
+    out = {"f64_1e7": {"ms": g(line, "ms_per_step"), "inst_s": g(line, "value"),
+                       "alu_frac": g(line, "roofline", "frac"), "e2e_inst_s": g(line, "e2e", "value"),
+                       "err_ypp": g(line, "error_vs_oracle", "ypp"), "err_yq": g(line, "error_vs_oracle", "yq"),
+                       "oracle_inst_s_1core": g(line, "cpu_baseline", "value")}}
+    for key, name in (("mixed_f32", "mixed_1e7"), ("mixed_f32_refine1", "mixed_refine1_1e7")):
+        e = oc.get(key) or {}
+        out[name] = {"ms": g(e, "ms_per_step"), "gb_s": g(e, "gb_per_s"), "hbm_frac": g(e, "hbm_frac_of_measured"),
+                     "err_ypp": g(e, "error_vs_oracle", "ypp"), "err_yq": g(e, "error_vs_oracle", "yq")}
+    b = oc.get("batched") or {}
+    out["batched_4096"] = {"ms": g(b, "ms_per_step"), "inst_s": g(b, "value"), "gb_s": g(b, "gb_per_s"),
+                           "err_ypp": g(b, "error_vs_oracle", "ypp"),
+                           "oracle_inst_s_1core": g(b, "cpu_baseline", "single_thread", "value"),
+                           "oracle_inst_s_all": g(b, "cpu_baseline", "all_cores", "value"),
+                           "cores": g(b, "cpu_baseline", "all_cores", "cores")}
+    sv = oc.get("serving") or {}
+    out["serving_20k"] = {"inst_s": g(sv, "value"), "p50_ms": g(sv, "latency_ms", "p50"),
+                          "p99_ms": g(sv, "latency_ms", "p99"), "sat_inst_s": g(sv, "saturation", "value"),
+                          "plain_f64_inst_s": g(sv, "plain_f64_same_pool", "value"),
+                          "plain_mixed_inst_s": g(sv, "plain_mixed_refine0_same_pool", "value"),
+                          "served_over_plain_f64": g(sv, "served_over_plain_instances_per_s"),
+                          "served_over_plain_same_precision": g(sv, "served_over_plain_same_precision"),
+                          "oracle_inst_s_all": g(sv, "cpu_baseline", "value"), "err_yq": g(sv, "error_vs_oracle", "yq")}
+    c1 = oc.get("n1000") or {}
+    out["n1000"] = {k: {"dev_p50_ms": g(c1, k, "device_ms", "median"), "dev_p99_ms": g(c1, k, "device_ms", "p99"),
+                        "wall_p50_ms": g(c1, k, "wall_ms", "median"), "wall_p99_ms": g(c1, k, "wall_ms", "p99")}
+                    for k in ("f64/natural", "mixed_refine1/natural")}
+    out["n1000"]["oracle_us_1core"] = g(c1, "cpu_baseline", "us_per_instance")
+    v = oc.get("newint_variants") or {}
+    out["eval_1e7_ms"] = {lab: {nm: g(v, lab, nm, "ms", "median") for nm in ("orig", "noinv", "vol", "noop")}
+                          for lab in ("sorted", "unsorted")}
+    return out
 
 
 def cpu_baseline_and_errors(r, main, mixed0, mixed1, bdata, sdata, vdata=None):

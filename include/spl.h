@@ -97,7 +97,10 @@ typedef enum spl_query_mode {
 typedef enum spl_eval_variant {
   SPL_EVAL_ORIG = 0,
   SPL_EVAL_NOINV = 1,
-  SPL_EVAL_VOL = 2
+  SPL_EVAL_VOL = 2,
+  SPL_EVAL_NOOP = 3         /* control of section "Curve Interpolation" (its noop loop): the queries
+                               are generated and bracketed but not evaluated; yq_out receives the
+                               left knot x_j of each query's interval, jq_out (if given) j */
 } spl_eval_variant;
 
 typedef struct spl_ctx spl_ctx;

@@ -7,8 +7,9 @@
 
 namespace spl {
 
-// Status bits a tile ORs into its instance's status word (device memory).
-enum : unsigned { kStNonFinite = 1u, kStNotIncreasing = 2u };
+// Status bits a tile ORs into its instance's status word (device memory).  kStBadTile: a tile
+// longer than the kernel's scratch holds (the host never launches one; the tile is skipped).
+enum : unsigned { kStNonFinite = 1u, kStNotIncreasing = 2u, kStBadTile = 4u };
 
 // One instance as the kernels see it (built by the host runtime, lives in device memory
 // or in the kernel parameter block).
@@ -56,8 +57,6 @@ struct ServeArgs {
   volatile unsigned *h_done;                             // per slot: status, seq
   unsigned long long idle_ns, deadline_ns;
   unsigned fault_flags;                                  // tests: bit 0, the scheduler leaves at once
-  float4 *scan_scratch;                                  // per worker warp: scan_rows_cap rows
-  long long scan_rows_cap;
 };
 
 // Natural end condition: section "Start and End Derivatives" (slope > 0.99e30).

@@ -41,9 +41,13 @@ __device__ __forceinline__ long long bracket_bisect(const double *__restrict__ x
 // kVariant 1 (noinv): the sum divided by ba.
 // kVariant 2 (vol): orig with inv_ba held in a volatile local, whose store and reload pin the
 // division ahead of the cubic.
+// kVariant 3 (noop): the paper's control loop of section "Curve Interpolation" (query generation
+// and bracketing without the evaluation): the bracket's left knot x_j is written in place of the
+// value, so the output traffic is the same and the bracket cannot be optimised away.
 template <int kVariant>
 __device__ __forceinline__ double newint_variant(double q, double xj, double xj1, double yj, double yj1, double ppj,
                                                  double ppj1) {
+  if (kVariant == 3) return xj;
   const double ba = xj1 - xj;
   double inv_ba = 0.0;
   volatile double inv_pinned;
@@ -76,6 +80,7 @@ __device__ __forceinline__ float near_diff32(double b, double a) {
 template <int kVariant>
 __device__ __forceinline__ double newint_variant32(double q, double xj, double xj1, double yj, double yj1,
                                                    double ppj, double ppj1) {
+  if (kVariant == 3) return xj;
   const float ba = near_diff32(xj1, xj);
   const float xa = near_diff32(q, xj);
   const float bx = ba - xa;
@@ -186,8 +191,11 @@ __global__ void __launch_bounds__(kThreadsE, kBlocksPerSmE)
       jprev = j;
       const double *__restrict__ y = I.y;
       const double *__restrict__ ypp = I.ypp;
-      I.yq[k] = kF32 ? newint_variant32<kVariant>(q, x[j], x[j + 1], y[j], y[j + 1], ypp[j], ypp[j + 1])
-                     : newint_variant<kVariant>(q, x[j], x[j + 1], y[j], y[j + 1], ypp[j], ypp[j + 1]);
+      if (kVariant == 3)
+        I.yq[k] = x[j];
+      else
+        I.yq[k] = kF32 ? newint_variant32<kVariant>(q, x[j], x[j + 1], y[j], y[j + 1], ypp[j], ypp[j + 1])
+                       : newint_variant<kVariant>(q, x[j], x[j + 1], y[j], y[j + 1], ypp[j], ypp[j + 1]);
       if (I.jq) I.jq[k] = (int32_t)j;
     }
   }
@@ -226,8 +234,11 @@ __global__ void __launch_bounds__(kThreadsE, kBlocksPerSmE)
     const long long j = bracket_bisect(x, n, dkey(q));
     const double *__restrict__ y = I.y;
     const double *__restrict__ ypp = I.ypp;
-    I.yq[k] = kF32 ? newint_variant32<kVariant>(q, x[j], x[j + 1], y[j], y[j + 1], ypp[j], ypp[j + 1])
-                   : newint_variant<kVariant>(q, x[j], x[j + 1], y[j], y[j + 1], ypp[j], ypp[j + 1]);
+    if (kVariant == 3)
+      I.yq[k] = x[j];
+    else
+      I.yq[k] = kF32 ? newint_variant32<kVariant>(q, x[j], x[j + 1], y[j], y[j + 1], ypp[j], ypp[j + 1])
+                     : newint_variant<kVariant>(q, x[j], x[j + 1], y[j], y[j + 1], ypp[j], ypp[j + 1]);
     if (I.jq) I.jq[k] = (int32_t)j;
   }
 }
@@ -249,6 +260,8 @@ cudaError_t launch_eval(const Inst *d_insts, int ninst, long long total_q, int v
     case 3: SPL_EVAL_LAUNCH(1, true); break;
     case 4: SPL_EVAL_LAUNCH(2, false); break;
     case 5: SPL_EVAL_LAUNCH(2, true); break;
+    case 6: SPL_EVAL_LAUNCH(3, false); break;
+    case 7: SPL_EVAL_LAUNCH(3, true); break;
     case 1: SPL_EVAL_LAUNCH(0, true); break;
     default: SPL_EVAL_LAUNCH(0, false); break;
   }

@@ -54,23 +54,22 @@ cudaError_t launch_refine_mixed(const Inst *d_insts, int ninst, long long total_
                                 unsigned long long *counter, cudaStream_t stream);
 
 // Persistent serving loop (spl_mixed_scan.cu): a cooperative launch of one CTA per SM; its
-// workers solve tiles of serve_tile_rows(tile_rows) rows with the warp-cooperative kernel's
-// solver, in ServeArgs::scan_scratch (serve_scratch_bytes bytes, serve_rows_cap rows per warp).
+// workers solve tiles of serve_tile_rows(tile_rows) rows (at most serve_tile_max()) with the
+// warp-cooperative kernel's solver, each in its own shared memory.
 cudaError_t launch_serve(const ServeArgs &args, int sm_count, cudaStream_t stream);
 int serve_tile_rows(int tile_rows);
-long long serve_rows_cap(int tile_rows);
-size_t serve_scratch_bytes(int sm_count, int tile_rows);
+int serve_tile_max();
 
 // Warp-cooperative binary32 fit + evaluation (spl_mixed_scan.cu): one warp per tile of
-// scan_mixed_tile_rows rows (a multiple of 32), per-warp scratch of scratch_bytes_scan_mixed
-// bytes.  mode 0: fit + eval; 1: fit only into Inst::z (binary32), the refined path's first
-// pass; 2: refinement of Inst::z + eval.
+// scan_mixed_tile_rows rows (a multiple of 32, at most scan_mixed_tile_max()), its scratch in
+// shared memory.  mode 0: fit + eval; 1: fit only into Inst::z (binary32), the refined path's
+// first pass; 2: refinement of Inst::z + eval.  `counter` must be zero when the kernel starts.
 int scan_mixed_threads_per_sm();
+int scan_mixed_tile_max();
 int scan_mixed_tile_rows(long long total_points, int sm_count, int count);
 long long threads_scan_mixed(int sm_count, long long total_tiles);
-size_t scratch_bytes_scan_mixed(long long threads, int tile_rows);
-cudaError_t launch_scan_mixed(const Inst *d_insts, int ninst, long long total_tiles, float *scratch, int tile_rows,
-                              int sm_count, unsigned long long *counter, cudaStream_t stream, int mode);
+cudaError_t launch_scan_mixed(const Inst *d_insts, int ninst, long long total_tiles, int sm_count,
+                              unsigned long long *counter, cudaStream_t stream, int mode);
 
 // Separate evaluation (spl_eval.cu): queries q_begin .. q_begin+mq-1 of each instance, explicit
 // (Inst::xq) or on the uniform grid, with the y'' in Inst::ypp; variant = spl_eval_variant; f32:

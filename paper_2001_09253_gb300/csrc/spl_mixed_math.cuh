@@ -36,10 +36,15 @@ __device__ __forceinline__ float dif32_near(double b, double a) {
 // bracketing knot), without FP64 instructions in the common case (the integer/FP32 route of
 // diff_up_f32): for kernels that are throughput-bound with many warps in flight, where the FP64
 // pipe (~1/64 of the FP32 rate) is the scarce unit; other pairs as dif32_near.
+static __device__ __noinline__ float dif32_near_slow(double b, double a) { return dif32_near(b, a); }
 __device__ __forceinline__ float dif32_up(double b, double a) {
   float v;
   if (diff_up_f32(b, a, &v)) return v;
-  return dif32_near(b, a);
+  // wider same-binade pairs (small knots: an ulp count of 2^39 or more) on the integer pipe too
+  if (diff_same_f32(b, a, &v)) return v;
+  // out of line: inlined, the FP64 subtraction of dif32_near's Sterbenz case was evaluated
+  // speculatively for every operand pair (measured: the FP64 pipe twice as busy)
+  return dif32_near_slow(b, a);
 }
 
 __device__ __forceinline__ F2 dif2(double b, double a) {

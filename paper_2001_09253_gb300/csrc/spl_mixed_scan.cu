@@ -1,31 +1,34 @@
 // Warp-cooperative binary32 fit + evaluation ("scan" form of the mixed-precision path).
 //
-// The same system and arithmetic as the binary32 ring kernel (spl_fused_mixed.cu: tridiagonal system of eq.
-// (init_val) with the end rows of "Start and End Derivatives", Thomas recurrences of
-// "Implementation", the one-division form of "Fast Interpolation" on the grid of "Curve
-// Interpolation"; binary32 arithmetic on exact, once-rounded differences of the binary64
-// inputs), laid out the other way round: a warp solves one tile of rows, 32 consecutive rows
-// at a time, lane l holding row R + l.  Every global access of a warp is then one contiguous
-// run (coalesced), and the recurrences become warp scans:
-//   * c'_j = c_j / (b_j - a_j c'_{j-1}) contracts errors in c'_{j-1} by 1/12 or more per row
-//     (diagonal dominance), so a few relaxation sweeps across the lanes reach the sequential
-//     values;
+// The system and arithmetic are those of the binary32 ring kernel (spl_fused_mixed.cu): the
+// tridiagonal system of eq. (init_val) with the end rows of "Start and End Derivatives", the
+// Thomas recurrences of "Implementation", and the one-division form of "Fast Interpolation" on
+// the grid of "Curve Interpolation", in binary32 arithmetic on exact, once-rounded differences of
+// the binary64 inputs.  A warp solves one tile of rows, kStepS = 128 consecutive rows per step, lane
+// l holding the kVS = 4 consecutive rows R + 4l .. R + 4l + 3, so that the recurrences become a
+// short sequential part inside each lane and a warp scan across the lanes:
+//   * c'_j = c_j / (b_j - a_j c'_{j-1}) contracts an error in c'_{j-1} by at least 12 per row
+//     (b = 2(a + c) and c' <= 1/2 give |dc'_j/dc'_{j-1}| = ac/(b - a c')^2 <= ac/(1.5a + 2c)^2
+//     <= 1/12), so three relaxation passes over a lane's four rows, each starting from the
+//     previous lane's output of the pass before (lane 0 from the carried c'_{R-1}), reach the
+//     sequential values: the guess error 1/4 shrinks to 12^-8 / 4 < 2^-30 before the last pass;
 //   * d'_j = (d_j - a_j d'_{j-1}) / den_j and the back substitution y''_j = d'_j - c'_j y''_{j+1}
-//     are affine maps, composed by an inclusive scan (the second one from the top down);
-//   * the queries of a chunk's 32 intervals are evaluated 32 at a time, lane-parallel: each finds
-//     its interval among the lanes' knots by a 5-step search on the order-preserving keys (so
-//     brackets stay bit-identical to the sequential sweep) and gathers the interval's data by
-//     shuffles.
-// A tile starts its forward sweep 64 rows early from a guessed state (the guess error decays by
-// <= 2/3 per row for d' and <= 1/12 for c') and its back substitution 32 rows past its end (the
-// error decays by c' < 1/2 per row).  (c', d') of the tile's rows, with the binary32 width and
-// value the evaluation needs, go to a per-warp scratch (16 bytes per row, a few tens of MB for
-// all warps: L2-resident between the two sweeps), so the back substitution re-reads only the
-// knots.
-// Exact differences of neighbouring knots take the integer/FP32 route: with 16 warps per SM
-// the kernel is bound by instruction throughput, where the FP64 pipe (~1/64 of the FP32 rate)
-// is the scarce unit.
+//     are affine maps t -> A t + B: each lane composes its four, an inclusive warp scan (the
+//     second one from the top lane down) composes the lanes', and each lane then applies its own
+//     four maps to the value entering it;
+//   * the queries of a step's intervals are evaluated 32 at a time, lane-parallel, from the top
+//     query down: each finds its interval by a 5-step search over the lanes' first knots
+//     (shuffles of order-preserving integer keys, so brackets stay bit-identical to the
+//     sequential sweep) and a 3-key search among the four knots of that lane (shared memory).
+// A tile starts its forward sweep kHaloS = 64 rows early from a guessed state (the guess error in
+// d' decays by at most 2/3 per row: (2/3)^64 < 2^-37) and its back substitution kOvS = 32 rows
+// past its end from y'' = 0 (the error decays by c' < 1/2 per row).  The forward results (c', d',
+// binary32 width and value) of every row of the tile and its halo live in the warp's shared
+// memory (16 bytes per row, transposed within a step so that lanes touch consecutive words); the
+// back substitution overwrites (c', d') in place by what the evaluation needs besides the width and
+// value (1/width, y''); no global scratch is used, so DRAM sees only the inputs and outputs.
 #include <algorithm>
+#include <atomic>
 
 #include "spl_device.cuh"
 #include "spl_internal.h"
@@ -34,27 +37,267 @@
 
 namespace spl {
 
-constexpr int kThreadsS = 1024;  // one CTA per SM (more warps hide the scans' shuffle latency)
-constexpr int kHaloS = 64;      // forward rows before a tile (a multiple of 32)
-constexpr int kOvS = 32;        // back-substitution start past a tile
+constexpr int kVS = 4;                 // consecutive rows per lane in a step
+constexpr int kStepS = 32 * kVS;       // rows per warp step
+constexpr int kHaloS = 64;             // forward rows before a tile
+constexpr int kOvS = 32;               // back-substitution start past a tile
+constexpr int kWarpsS = 16;            // warps per CTA (one CTA per SM)
+constexpr int kThreadsS = 32 * kWarpsS;
+constexpr int kTileMaxS = 512;         // longest tile the shared-memory scratch holds
+constexpr int kRowsCapS = (kTileMaxS + kHaloS + kOvS + kStepS - 1) / kStepS * kStepS;
 constexpr unsigned kFullS = 0xffffffffu;
-constexpr int kRelaxS = 8;     // relaxation sweeps of the c' recurrence in a chunk
+constexpr long long kKeyInf = 0x7FF0000000000000LL;  // key of +inf: above every finite knot
+
+// Shared memory of one warp.  w: per row of the tile's forward range, (c', d', h, y) after the
+// forward sweep and (1/h, y'', h, y) after the back substitution; within each step of 128 rows the
+// row R + 4l + v sits at v*32 + l.  keys: order-preserving keys of the knots of the current
+// back-substitution step (same transposition), and of x_{R+128} at index 128.
+struct ScanSmem {
+  float4 w[kRowsCapS];
+  long long keys[kStepS + 2];
+};
+constexpr size_t kSmemPerWarpS = sizeof(ScanSmem);
 
 __device__ __forceinline__ double shfl_f64(double v, int src) {
   return __longlong_as_double(__shfl_sync(kFullS, __double_as_longlong(v), src));
 }
 __device__ __forceinline__ long long shfl_i64(long long v, int src) { return __shfl_sync(kFullS, v, src); }
+__device__ __forceinline__ int wpos(int row_in_step) { return (row_in_step & 3) * 32 + (row_in_step >> 2); }
 
-// Least k in [0, m] with x_k > v on the uniform grid (x_0 <= v): an estimate from the grid step,
-// corrected on the exact grid points.
-__device__ __forceinline__ long long first_above(const Grid &G, double v, double inv_step) {
-  if (G.m <= 1) return (G.m == 1 && dkey(G.x0) <= dkey(v)) ? 1 : 0;
-  const double e = (v - G.x0) * inv_step;
-  long long k = !(e >= 0.0) ? 0 : (e >= (double)G.m ? G.m : (long long)e + 1);
+// Inverse of dkey (the -0 it folds comes back as +0).
+__device__ __forceinline__ double key_to_double(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7FFFFFFFFFFFFFFFLL));
+}
+
+// Least k in [0, m] with x_k > v on the uniform grid, one value per lane: the estimate
+// floor((v - x_0) / step) from binary64 arithmetic (within one of the answer: the grid points are
+// rounded sums) checked on the two grid points around it by their keys, with a walk for the rare
+// miss.  Lanes with need = false return 0 (their FP64 work is shared by the warp anyway).
+__device__ __forceinline__ long long grid_first_above(const Grid &G, double inv_step, bool need, double v) {
+  if (!need || G.m == 0) return 0;
   const long long kv = dkey(v);
-  while (k > 0 && dkey(G.at(k - 1)) > kv) --k;
-  while (k < G.m && dkey(G.at(k)) <= kv) ++k;
-  return k;
+  if (G.m == 1) return dkey(G.x0) <= kv ? 1 : 0;
+  const double e = (v - G.x0) * inv_step;
+  long long k = (e >= 0.0) ? (long long)e : -1;  // ~ the last grid point at or below v
+  k = max(min(k, G.m - 1), -1LL);
+  const bool lo_ok = k < 0 || dkey(G.at(k)) <= kv;
+  const bool hi_ok = k + 1 >= G.m || dkey(G.at(k + 1)) > kv;
+  if (lo_ok && hi_ok) return k + 1;
+  long long kk = k + 1;
+  while (kk > 0 && dkey(G.at(kk - 1)) > kv) --kk;
+  while (kk < G.m && dkey(G.at(kk)) <= kv) ++kk;
+  return kk;
+}
+
+// The uniform grid of the instance: x_0, x_{n-1}, step = (x_{n-1} - x_0)/(m - 1) as the correctly
+// rounded quotient (quot64 equals the IEEE division bit for bit) and 1/step for estimates.
+__device__ __forceinline__ Grid grid_of(const double *x, long long n, long long m, double *inv_step) {
+  Grid g;
+  g.x0 = x[0];
+  g.xl = x[n - 1];
+  g.m = m;
+  g.step = 0.0;
+  *inv_step = 0.0;
+  if (m >= 2) {
+    const double den = i2d_exact(m - 1);
+    g.step = quot64(g.xl - g.x0, den, rcp64(den));
+    *inv_step = rcp64(g.step);
+  }
+  return g;
+}
+
+// Forward state carried from the last row of one step to the next: c', d', width and slope of
+// the last row's interval (double-float in the refinement), and the refinement's Z.
+struct CarryS {
+  float c, d, z;
+  F2 h, s;
+};
+
+// Loads of a lane's rows j0 .. j0+4 (the fifth is the next lane's first: the width and slope of
+// the fourth row's interval need it).  `full`: every row exists.
+template <typename T>
+__device__ __forceinline__ void load5(const T *__restrict__ p, long long j0, long long n, bool full, T (&v)[kVS + 1]) {
+  if (full) {
+#pragma unroll
+    for (int u = 0; u <= kVS; ++u) v[u] = p[j0 + u];
+  } else {
+#pragma unroll
+    for (int u = 0; u <= kVS; ++u) v[u] = (j0 + u < n) ? p[j0 + u] : T(0);
+  }
+}
+
+// Forward elimination of one step: rows R .. R+127 of the tile's forward range [f0, f1), written
+// to the step's shared-memory slice.  kEdge: the step holds row 0, row n-1 or rows past f1 (or
+// loads past n); otherwise every row is an interior row of the system.
+// End conditions of an instance (section "Start and End Derivatives"), decided once per tile.
+struct EndsS {
+  bool nat0, nat1;
+  float yp1, ypn;  // binary32 end slopes (clamped ends)
+  F2 yp1F, ypnF;   // double-float end slopes (the refinement's residual)
+};
+
+template <int kMode, bool kEdge>
+__device__ __forceinline__ void fwd_step(const Inst &I, const EndsS &E, long long R, long long f1, int lane,
+                                         const double (&xv)[kVS + 1], const double (&yv)[kVS + 1],
+                                         const float (&zv)[kVS + 1], CarryS &C, float4 *__restrict__ ws,
+                                         unsigned &bad) {
+  const long long n = I.n;
+  const long long j0 = R + (long long)kVS * lane;
+  const bool nat0 = E.nat0, nat1 = E.nat1;
+  F2 h[kVS], s[kVS];
+#pragma unroll
+  for (int v = 0; v < kVS; ++v) {
+    const long long j = j0 + v;
+    const bool hasn = !kEdge || j <= n - 2;
+    h[v] = F2{0.0f, 0.0f};
+    s[v] = F2{0.0f, 0.0f};
+    if (hasn) {
+      if (kMode == 2) {
+        // exact widths as double-floats (same binade: the integer ulp count), value differences
+        // as the binary64 difference split in two (the rounding the binary64 slopes see too)
+        if (!diff_up_f2(xv[v + 1], xv[v], &h[v])) h[v] = dif2(xv[v + 1], xv[v]);
+        F2 dy;
+        if (!f64_to_f2(yv[v + 1] - yv[v], &dy)) dy = dif2(yv[v + 1], yv[v]);
+        s[v] = df_div(dy, h[v], rcp32(h[v].hi));
+      } else {
+        h[v].hi = dif32_up(xv[v + 1], xv[v]);
+        s[v].hi = quot32(dy32(yv[v + 1], yv[v]), h[v].hi, rcp32(h[v].hi));
+      }
+    }
+    if (kMode != 2 && (!kEdge || j < f1)) bad |= row_check(xv[v], yv[v], hasn, xv[v + 1]);
+  }
+  // the interval below the lane's first row: the previous lane's last, or the carry
+  F2 hm{__shfl_up_sync(kFullS, h[kVS - 1].hi, 1), 0.0f}, sm{__shfl_up_sync(kFullS, s[kVS - 1].hi, 1), 0.0f};
+  float zm = 0.0f;
+  if (kMode == 2) {
+    hm.lo = __shfl_up_sync(kFullS, h[kVS - 1].lo, 1);
+    sm.lo = __shfl_up_sync(kFullS, s[kVS - 1].lo, 1);
+    zm = __shfl_up_sync(kFullS, zv[kVS - 1], 1);
+  }
+  if (lane == 0) {
+    hm = C.h;
+    sm = C.s;
+    zm = C.z;
+  }
+  // rows: a y''_{j-1} + b y''_j + c y''_{j+1} = d (the refinement: the same matrix, d the residual)
+  float a[kVS], b[kVS], c[kVS], d[kVS];
+#pragma unroll
+  for (int v = 0; v < kVS; ++v) {
+    const F2 hp = v ? h[v - 1] : hm, sp = v ? s[v - 1] : sm;
+    a[v] = hp.hi;
+    c[v] = h[v].hi;
+    b[v] = 2.0f * (hp.hi + h[v].hi);
+    if (kMode == 2) {
+      const float z0 = zv[v], z1 = zv[v + 1], zp = v ? zv[v - 1] : zm;
+      const F2 dd = df_mul_f(df_add(s[v], df_neg(sp)), 6.0f);
+      const F2 az = df_add(df_add(df_mul_f(hp, zp), df_mul_f(df_add(hp, h[v]), 2.0f * z0)), df_mul_f(h[v], z1));
+      const F2 res = df_add(dd, df_neg(az));
+      d[v] = res.hi + res.lo;
+    } else {
+      d[v] = 6.0f * (s[v].hi - sp.hi);
+    }
+    if (kEdge) {
+      const long long j = j0 + v;
+      if (j == 0) {
+        a[v] = 0.0f;
+        if (nat0) {
+          b[v] = 1.0f;
+          c[v] = 0.0f;
+          d[v] = kMode == 2 ? -zv[v] : 0.0f;  // natural first row: y''_0 = 0
+        } else {
+          b[v] = 2.0f * h[v].hi;
+          if (kMode == 2) {
+            const F2 dd = df_mul_f(df_add(s[v], df_neg(E.yp1F)), 6.0f);
+            const F2 res = df_add(dd, df_neg(df_add(df_mul_f(h[v], 2.0f * zv[v]), df_mul_f(h[v], zv[v + 1]))));
+            d[v] = res.hi + res.lo;
+          } else {
+            d[v] = 6.0f * (s[v].hi - E.yp1);
+          }
+        }
+      } else if (j == n - 1) {
+        c[v] = 0.0f;
+        if (nat1) {
+          a[v] = 0.0f;
+          b[v] = 1.0f;
+          d[v] = kMode == 2 ? -zv[v] : 0.0f;  // y''_{n-1} = 0
+        } else {
+          b[v] = 2.0f * hp.hi;
+          if (kMode == 2) {
+            const float zp = v ? zv[v - 1] : zm;
+            const F2 dd = df_mul_f(df_add(E.ypnF, df_neg(sp)), 6.0f);
+            const F2 res = df_add(dd, df_neg(df_add(df_mul_f(hp, zp), df_mul_f(hp, 2.0f * zv[v]))));
+            d[v] = res.hi + res.lo;
+          } else {
+            d[v] = 6.0f * (E.ypn - sp.hi);
+          }
+        }
+      }
+      if (j >= f1) {  // past the sweep: identity rows
+        a[v] = 0.0f;
+        b[v] = 1.0f;
+        c[v] = 0.0f;
+        d[v] = 0.0f;
+      }
+    }
+  }
+  // c' by relaxation (see the file header): two passes from the guess 1/4 with the MUFU
+  // reciprocal alone, the third with the refined reciprocal that the d' step uses
+  float t = (lane == 0) ? C.c : 0.25f;
+#pragma unroll
+  for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+    for (int v = 0; v < kVS; ++v) t = c[v] * rcp_approx32(fmaf(-a[v], t, b[v]));
+    t = __shfl_up_sync(kFullS, t, 1);
+    if (lane == 0) t = C.c;
+  }
+  float cp[kVS], iden[kVS];
+#pragma unroll
+  for (int v = 0; v < kVS; ++v) {
+    iden[v] = rcp32(fmaf(-a[v], t, b[v]));
+    cp[v] = c[v] * iden[v];
+    t = cp[v];
+  }
+  // d': the maps t -> A t + B of the lane's rows, composed, scanned over the lanes, applied
+  float A[kVS], B[kVS];
+#pragma unroll
+  for (int v = 0; v < kVS; ++v) {
+    A[v] = -a[v] * iden[v];
+    B[v] = d[v] * iden[v];
+  }
+  float PA = A[0], PB = B[0];
+#pragma unroll
+  for (int v = 1; v < kVS; ++v) {
+    PB = fmaf(A[v], PB, B[v]);
+    PA *= A[v];
+  }
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const float A2 = __shfl_up_sync(kFullS, PA, off), B2 = __shfl_up_sync(kFullS, PB, off);
+    if (lane >= off) {
+      PB = fmaf(PA, B2, PB);
+      PA *= A2;
+    }
+  }
+  const float tA = __shfl_up_sync(kFullS, PA, 1), tB = __shfl_up_sync(kFullS, PB, 1);
+  float dpv = (lane == 0) ? C.d : fmaf(tA, C.d, tB);
+  float dp[kVS];
+#pragma unroll
+  for (int v = 0; v < kVS; ++v) {
+    dp[v] = fmaf(A[v], dpv, B[v]);
+    dpv = dp[v];
+  }
+#pragma unroll
+  for (int v = 0; v < kVS; ++v)
+    ws[v * 32 + lane] = make_float4(cp[v], dp[v], h[v].hi, kMode == 1 ? 0.0f : to_f32(yv[v]));
+  C.c = __shfl_sync(kFullS, cp[kVS - 1], 31);
+  C.d = __shfl_sync(kFullS, dp[kVS - 1], 31);
+  C.h.hi = __shfl_sync(kFullS, h[kVS - 1].hi, 31);
+  C.s.hi = __shfl_sync(kFullS, s[kVS - 1].hi, 31);
+  if (kMode == 2) {
+    C.h.lo = __shfl_sync(kFullS, h[kVS - 1].lo, 31);
+    C.s.lo = __shfl_sync(kFullS, s[kVS - 1].lo, 31);
+    C.z = __shfl_sync(kFullS, zv[kVS - 1], 31);
+  }
 }
 
 // One tile: rows [s0, e0) of instance I.  kMode 0: fit + evaluation; 1: fit only, the binary32
@@ -62,245 +305,225 @@ __device__ __forceinline__ long long first_above(const Grid &G, double v, double
 // r = d - A Z in double-float arithmetic from exact double-float widths and value differences,
 // A delta = r solved with the binary32 matrix), y'' = Z + delta, and the evaluation.
 template <int kMode>
-__device__ void scan_tile(const Inst &I, long long tile, float4 *__restrict__ W, int lane) {
+__device__ void scan_tile(const Inst &I, long long tile, ScanSmem &S, int lane) {
   const long long n = I.n, TR = I.tile_rows;
+  if (TR < 1 || TR > kTileMaxS) {  // never launched by the host: the scratch would not hold it
+    if (lane == 0) atomicOr(I.status, kStBadTile);
+    return;
+  }
   const long long s0 = tile * TR, e0 = min(s0 + TR, n);
   const long long f0 = max(s0 - kHaloS, 0LL), f1 = min(e0 + kOvS, n);
+  const int nsteps = (int)((f1 - f0 + kStepS - 1) / kStepS);
   const double *__restrict__ x = I.x;
   const double *__restrict__ y = I.y;
   const float *__restrict__ z = I.z;
-  const bool nat0 = is_natural(I.yp1), nat1 = is_natural(I.ypn);
-  const float yp1f = nat0 ? 0.0f : to_f32(I.yp1), ypnf = nat1 ? 0.0f : to_f32(I.ypn);
   unsigned bad = 0;
+  EndsS E;
+  E.nat0 = is_natural(I.yp1);
+  E.nat1 = is_natural(I.ypn);
+  E.yp1 = E.nat0 ? 0.0f : to_f32(I.yp1);
+  E.ypn = E.nat1 ? 0.0f : to_f32(I.ypn);
+  E.yp1F = (kMode == 2 && !E.nat0) ? f2_of(I.yp1) : F2{0.0f, 0.0f};
+  E.ypnF = (kMode == 2 && !E.nat1) ? f2_of(I.ypn) : F2{0.0f, 0.0f};
 
-  // ---- forward sweep, rows f0 .. f1-1 ----
-  // row R-1 (a guess at a tile's start): c', d', width, slope (double-float in the refinement), Z
-  float cp = 0.0f, dp = 0.0f, zp = 0.0f;
-  F2 hp{0.0f, 0.0f}, sp{0.0f, 0.0f};
-  // rows of the next chunk are loaded one chunk ahead (rows up to f1, the row past the sweep
-  // giving the last row's width and slope)
-  const long long lim = min(f1 + 1, n);
-  double xn = (f0 + lane < lim) ? x[f0 + lane] : 0.0, yn = (f0 + lane < lim) ? y[f0 + lane] : 0.0;
-  float zn = (kMode == 2 && f0 + lane < lim) ? z[f0 + lane] : 0.0f;
-  for (long long R = f0; R < f1; R += 32) {
-    const long long j = R + lane;
-    const bool act = j < f1, hasn = act && j <= n - 2;
-    const double x0 = xn, y0 = yn;
-    const float z0 = zn;
-    xn = (j + 32 < lim) ? x[j + 32] : 0.0;
-    yn = (j + 32 < lim) ? y[j + 32] : 0.0;
-    if (kMode == 2) zn = (j + 32 < lim) ? z[j + 32] : 0.0f;
-    const double xf = shfl_f64(xn, 0), yf = shfl_f64(yn, 0);  // row R+32
-    double x1 = shfl_f64(x0, (lane + 1) & 31), y1 = shfl_f64(y0, (lane + 1) & 31);
-    if (lane == 31) {
-      x1 = xf;
-      y1 = yf;
-    }
-    F2 hF{0.0f, 0.0f}, sF{0.0f, 0.0f};
-    if (hasn) {
-      if (kMode == 2) {
-        hF = dif2(x1, x0);
-        sF = df_div(dif2(y1, y0), hF, rcp32(hF.hi));
-      } else {
-        hF.hi = dif32_up(x1, x0);
-        sF.hi = quot32(dy32(y1, y0), hF.hi, rcp32(hF.hi));
-      }
-    }
-    const float h = hF.hi;
-    if (kMode != 2 && act && j >= s0 && j < e0) bad |= row_check(x0, y0, j <= n - 2, x1);
-    F2 hm{__shfl_up_sync(kFullS, hF.hi, 1), 0.0f}, sm{__shfl_up_sync(kFullS, sF.hi, 1), 0.0f};
-    if (kMode == 2) {
-      hm.lo = __shfl_up_sync(kFullS, hF.lo, 1);
-      sm.lo = __shfl_up_sync(kFullS, sF.lo, 1);
-    }
-    if (lane == 0) {
-      hm = hp;
-      sm = sp;
-    }
-    // row j: a y''_{j-1} + b y''_j + c y''_{j+1} = d (the refinement: the same matrix, d the residual)
-    float a = hm.hi, b = 2.0f * (hm.hi + h), c = h, d;
-    if (kMode == 2) {
-      float zm = __shfl_up_sync(kFullS, z0, 1);
-      const float zf = __shfl_sync(kFullS, zn, 0);
-      float z1 = __shfl_down_sync(kFullS, z0, 1);
-      if (lane == 0) zm = zp;
-      if (lane == 31) z1 = zf;
-      F2 res;
-      if (j == 0) {
-        a = 0.0f;
-        if (nat0) {
-          b = 1.0f; c = 0.0f;
-          res = F2{-z0, 0.0f};  // natural first row: y''_0 = 0
-        } else {
-          b = 2.0f * h;
-          const F2 dd = df_mul_f(df_add(sF, df_neg(f2_of(I.yp1))), 6.0f);
-          res = df_add(dd, df_neg(df_add(df_mul_f(hF, 2.0f * z0), df_mul_f(hF, z1))));
-        }
-      } else if (j == n - 1) {
-        c = 0.0f;
-        if (nat1) {
-          a = 0.0f; b = 1.0f;
-          res = F2{-z0, 0.0f};  // y''_{n-1} = 0
-        } else {
-          b = 2.0f * hm.hi;
-          const F2 dd = df_mul_f(df_add(f2_of(I.ypn), df_neg(sm)), 6.0f);
-          res = df_add(dd, df_neg(df_add(df_mul_f(hm, zm), df_mul_f(hm, 2.0f * z0))));
-        }
-      } else {
-        const F2 dd = df_mul_f(df_add(sF, df_neg(sm)), 6.0f);
-        const F2 az = df_add(df_add(df_mul_f(hm, zm), df_mul_f(df_add(hm, hF), 2.0f * z0)), df_mul_f(hF, z1));
-        res = df_add(dd, df_neg(az));
-      }
-      d = res.hi + res.lo;
-      zp = __shfl_sync(kFullS, z0, (int)min(31LL, f1 - 1 - R));
-    } else {
-      d = 6.0f * (sF.hi - sm.hi);
-      if (j == 0) {
-        a = 0.0f;
-        if (nat0) { b = 1.0f; c = 0.0f; d = 0.0f; }
-        else { b = 2.0f * h; d = 6.0f * (sF.hi - yp1f); }
-      } else if (j == n - 1) {
-        c = 0.0f;
-        if (nat1) { a = 0.0f; b = 1.0f; d = 0.0f; }
-        else { b = 2.0f * hm.hi; d = 6.0f * (ypnf - sm.hi); }
-      }
-    }
-    if (!act) { a = 0.0f; b = 1.0f; c = 0.0f; d = 0.0f; }
-    // c'_j = c_j / (b_j - a_j c'_{j-1}): relaxation across the lanes from the guess c'_{j-1} = 0.
-    // The map contracts errors in c'_{j-1} by at most h_j h_{j-1} / (1.5 h_{j-1} + 2 h_j)^2 <= 1/12,
-    // so after kRelaxS sweeps every lane is within 12^-8 / 2 (< 2^-29) of the sequential value; lane 0
-    // starts from the carried c'_{R-1}.
-    // The sweeps before the last use the MUFU reciprocal alone (~1 ulp): they only move the
-    // guess, the last one forms the refined 1/den that the d' step uses.
-    float cj = c * rcp_approx32(b - a * (lane == 0 ? cp : 0.0f)), iden = 0.0f;
-#pragma unroll
-    for (int it = 0; it < kRelaxS; ++it) {
-      float cm = __shfl_up_sync(kFullS, cj, 1);
-      if (lane == 0) cm = cp;
-      iden = it + 1 < kRelaxS ? rcp_approx32(b - a * cm) : rcp32(b - a * cm);
-      cj = c * iden;
-    }
-    // d': scan of the affine maps t -> (-a/den) t + d/den, applied to d'_{R-1}
-    float A = -a * iden, B = d * iden;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const float A2 = __shfl_up_sync(kFullS, A, off), B2 = __shfl_up_sync(kFullS, B, off);
-      if (lane >= off) {
-        B = fmaf(A, B2, B);
-        A *= A2;
-      }
-    }
-    const float dj = fmaf(A, dp, B);
-    if (act) W[j - f0] = make_float4(cj, dj, h, kMode == 1 ? 0.0f : to_f32(y0));
-    const int last = (int)min(31LL, f1 - 1 - R);
-    cp = __shfl_sync(kFullS, cj, last);
-    dp = __shfl_sync(kFullS, dj, last);
-    hp.hi = __shfl_sync(kFullS, hF.hi, last);
-    sp.hi = __shfl_sync(kFullS, sF.hi, last);
-    if (kMode == 2) {
-      hp.lo = __shfl_sync(kFullS, hF.lo, last);
-      sp.lo = __shfl_sync(kFullS, sF.lo, last);
-    }
+  // ---- forward sweep, rows f0 .. f1-1, one step of 128 rows at a time; loads one step ahead ----
+  CarryS C;
+  C.c = C.d = C.z = 0.0f;
+  C.h = C.s = F2{0.0f, 0.0f};
+  double xn[kVS + 1], yn[kVS + 1];
+  float zn[kVS + 1];
+  {
+    const long long j0 = f0 + (long long)kVS * lane;
+    const bool full = f0 + kStepS + 1 <= n;
+    load5(x, j0, n, full, xn);
+    load5(y, j0, n, full, yn);
+    if (kMode == 2) load5(z, j0, n, full, zn);
   }
+  for (int st = 0; st < nsteps; ++st) {
+    const long long R = f0 + (long long)st * kStepS;
+    double xv[kVS + 1], yv[kVS + 1];
+    float zv[kVS + 1];
+#pragma unroll
+    for (int u = 0; u <= kVS; ++u) {
+      xv[u] = xn[u];
+      yv[u] = yn[u];
+      zv[u] = kMode == 2 ? zn[u] : 0.0f;
+    }
+    if (st + 1 < nsteps) {
+      const long long Rn = R + kStepS, j0 = Rn + (long long)kVS * lane;
+      const bool full = Rn + kStepS + 1 <= n;
+      load5(x, j0, n, full, xn);
+      load5(y, j0, n, full, yn);
+      if (kMode == 2) load5(z, j0, n, full, zn);
+    }
+    float4 *ws = S.w + st * kStepS;
+    const bool edge = R == 0 || R + kStepS > f1 || R + kStepS + 1 > n;
+    if (edge) fwd_step<kMode, true>(I, E, R, f1, lane, xv, yv, zv, C, ws, bad);
+    else fwd_step<kMode, false>(I, E, R, f1, lane, xv, yv, zv, C, ws, bad);
+  }
+  __syncwarp();
 
-  // ---- back substitution from row f1-1 down to s0, fused with the evaluation ----
-  const long long rt = f1 - 1;
+  // ---- back substitution from row f1-1 down to s0, step by step, fused with the evaluation ----
   const long long m = I.m;
   const bool evaluate = kMode != 1 && m > 0 && s0 <= n - 2;
-  const Grid G = make_grid(x, n, m);
-  const double inv_step = (m >= 2) ? 1.0 / G.step : 0.0;
-  // queries of the tile's intervals s0 .. min(e0, n-1)-1: klo .. khi-1, taken from the top down
-  // in batches of 32 (lane l: the l-th next one); a chunk takes the leading queries of a batch
-  // that lie above its lowest knot, the rest go to the chunks below
-  long long khi = 0, klo = 0;
+  Grid G;
+  G.x0 = G.xl = G.step = 0.0;
+  G.m = 0;
+  const int st_lo = (int)((s0 - f0) / kStepS);
+  // First query above the lowest knot of each step's intervals (lane s, steps above the bottom
+  // one), above x_{s0} (lane st_lo: the tile's first query) and above x_{e0} (lane 31: past the
+  // tile's last query), all at once; the queries of step s are [bnd_s, bnd of the step above).
+  long long bnd = 0, klo = 0, khi = 0;
   if (evaluate) {
-    khi = (e0 >= n - 1) ? m : (finite64(x[e0]) ? first_above(G, x[e0], inv_step) : 0);
-    klo = (s0 == 0) ? 0 : (finite64(x[s0]) ? min(first_above(G, x[s0], inv_step), khi) : khi);
-  }
-  float ycarry = 0.0f;  // recurrence value of row R+32 (a guess above the top row)
-  float pcarry = 0.0f;  // binary32 y'' of row R+32
-  float fytop = 0.0f;   // binary32 y_{R+32}
-  // the next chunk down (scratch, knots, stored Z) is loaded one chunk ahead
-  const long long Rtop = f0 + ((rt - f0) >> 5 << 5);
-  float4 cdn = (Rtop + lane <= rt) ? W[Rtop + lane - f0] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  double xjn = (evaluate && Rtop + lane <= rt) ? x[Rtop + lane] : 0.0;
-  float zjn = (kMode == 2 && Rtop + lane <= rt) ? z[Rtop + lane] : 0.0f;
-  for (long long R = Rtop; R >= s0; R -= 32) {
-    const long long j = R + lane;
-    const bool act = j <= rt;
-    const float4 cd = cdn;
-    const double xj = xjn;
-    const float zj = zjn;
-    if (R - 32 >= s0) {  // rows below R are all inside the forward range
-      cdn = W[j - 32 - f0];
-      if (evaluate) xjn = x[j - 32];
-      if (kMode == 2) zjn = z[j - 32];
+    double inv_step;
+    G = grid_of(x, n, m, &inv_step);
+    bool need = false;
+    long long r = 0;
+    if (lane == 31) {
+      r = e0;
+      need = e0 < n - 1;
+    } else if (lane >= st_lo && lane < nsteps) {
+      r = max(f0 + (long long)lane * kStepS, s0);
+      need = r > 0 && r < min(e0, n - 1);
     }
-    float A = act ? -cd.x : 1.0f, B = act ? cd.y : 0.0f;
+    const double v = need ? x[r] : 0.0;
+    need = need && finite64(v);
+    bnd = grid_first_above(G, inv_step, need, v);
+    if (lane == 31 && e0 >= n - 1) bnd = m;
+    khi = __shfl_sync(kFullS, bnd, 31);
+    klo = min(__shfl_sync(kFullS, bnd, st_lo), khi);
+  }
+
+  float ycarry = 0.0f;  // value of the recurrence at the row above the step (a guess above f1-1)
+  double xb[kVS + 1];
+  float zb[kVS + 1];
+  {
+    const long long j0 = f0 + (long long)(nsteps - 1) * kStepS + (long long)kVS * lane;
+    if (evaluate) load5(x, j0, n, false, xb);
+    if (kMode == 2) load5(z, j0, n, false, zb);
+  }
+  for (int st = nsteps - 1; st >= st_lo; --st) {
+    const long long R = f0 + (long long)st * kStepS;
+    const long long j0 = R + (long long)kVS * lane;
+    double xc[kVS + 1];
+    float zc[kVS + 1];
+#pragma unroll
+    for (int u = 0; u <= kVS; ++u) {
+      xc[u] = evaluate ? xb[u] : 0.0;
+      zc[u] = kMode == 2 ? zb[u] : 0.0f;
+    }
+    if (st > st_lo) {  // the step below lies inside the forward range: every row exists
+      const long long jb = j0 - kStepS;
+      if (evaluate) load5(x, jb, n, true, xb);
+      if (kMode == 2) load5(z, jb, n, true, zb);
+    }
+    float4 *ws = S.w + st * kStepS;
+    float4 cd[kVS];
+#pragma unroll
+    for (int v = 0; v < kVS; ++v) cd[v] = ws[v * 32 + lane];
+    float A[kVS], B[kVS];
+#pragma unroll
+    for (int v = 0; v < kVS; ++v) {
+      const bool act = j0 + v < f1;
+      A[v] = act ? -cd[v].x : 1.0f;
+      B[v] = act ? cd[v].y : 0.0f;
+    }
+    // the lane's maps composed from its top row down, then a suffix scan over the lanes
+    float FA = A[kVS - 1], FB = B[kVS - 1];
+#pragma unroll
+    for (int v = kVS - 2; v >= 0; --v) {
+      FB = fmaf(A[v], FB, B[v]);
+      FA *= A[v];
+    }
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      const float A2 = __shfl_down_sync(kFullS, A, off), B2 = __shfl_down_sync(kFullS, B, off);
+      const float A2 = __shfl_down_sync(kFullS, FA, off), B2 = __shfl_down_sync(kFullS, FB, off);
       if (lane + off < 32) {
-        B = fmaf(A, B2, B);
-        A *= A2;
+        FB = fmaf(FA, B2, FB);
+        FA *= A2;
       }
     }
-    const float v = fmaf(A, ycarry, B);  // y''_j, or the correction delta_j of the refinement
-    const float ypp = kMode == 2 ? zj + v : v;
-    const bool own = j >= s0 && j < e0;
-    if (kMode == 1) {
-      if (own) I.z[j] = v;
-    } else if (own && I.ypp) {
-      I.ypp[j] = kMode == 2 ? to_f64(zj) + to_f64(v) : to_f64(v);
-    }
-    if (evaluate) {
-      const float fy = cd.w;
-      float fy1 = __shfl_down_sync(kFullS, fy, 1), yp1 = __shfl_down_sync(kFullS, ypp, 1);
-      if (lane == 31) {
-        fy1 = fytop;
-        yp1 = pcarry;
-      }
-      const int hi = (int)(min(min(R + 31, e0 - 1), n - 2) - R);
-      if (R < e0 && hi >= 0) {  // the chunk holds intervals of the tile: R .. R+hi
-        float ba = 1.0f, iba = 1.0f;
-        if (lane <= hi) {
-          ba = cd.z;
-          iba = rcp32(ba);
-        }
-        const long long key = dkey(xj);
-        const long long keyR = shfl_i64(key, 0);
-        while (khi > klo) {
-          const long long k = khi - 1 - lane;
-          const bool qa = k >= klo;
-          const double q = qa ? G.at(k) : xj;
-          const long long kq = dkey(q);
-          const bool in = qa && (R == s0 || kq > keyR);
-          const int cnt = __popc(__ballot_sync(kFullS, in));
-          // the interval: largest l in [0, hi] with x_{R+l} < q (0 when none: the first interval)
-          int l = 0;
+    const float tA = __shfl_down_sync(kFullS, FA, 1), tB = __shfl_down_sync(kFullS, FB, 1);
+    float tv = (lane == 31) ? ycarry : fmaf(tA, ycarry, tB);
+    float val[kVS];  // y''_j, or the correction delta_j of the refinement
 #pragma unroll
-          for (int step = 16; step >= 1; step >>= 1) {
-            const int cand = l + step;
-            const long long kc = shfl_i64(key, cand & 31);
-            if (cand <= hi && kc < kq) l = cand;
+    for (int v = kVS - 1; v >= 0; --v) {
+      val[v] = fmaf(A[v], tv, B[v]);
+      tv = val[v];
+    }
+    ycarry = __shfl_sync(kFullS, val[0], 0);
+    // outputs of the tile's own rows
+#pragma unroll
+    for (int v = 0; v < kVS; ++v) {
+      const long long j = j0 + v;
+      if (j >= s0 && j < e0) {
+        if (kMode == 1) I.z[j] = val[v];
+        else if (I.ypp) I.ypp[j] = kMode == 2 ? to_f64(zc[v]) + to_f64(val[v]) : to_f64(val[v]);
+      }
+    }
+    if (!evaluate) continue;
+    // what the evaluation needs, in place: (1/width, y'') over (c', d'), next to the width and
+    // value the forward sweep left; and the step's knot keys
+#pragma unroll
+    for (int v = 0; v < kVS; ++v) {
+      const float pp = kMode == 2 ? zc[v] + val[v] : val[v];
+      const float hh = cd[v].z;
+      reinterpret_cast<float2 *>(ws + v * 32 + lane)[0] = make_float2(hh > 0.0f ? rcp32(hh) : 0.0f, pp);
+      S.keys[v * 32 + lane] = (j0 + v < n) ? dkey(xc[v]) : kKeyInf;
+    }
+    if (lane == 31) S.keys[kStepS] = (j0 + kVS < n) ? dkey(xc[kVS]) : kKeyInf;
+    __syncwarp();
+    const long long ilo = max(R, s0), ihi = min(min(R + kStepS, e0), n - 1);
+    if (ihi > ilo) {
+      // queries of this step's intervals: [kb0, khi), khi carried from the step above; the
+      // queries below kb0 (q <= x_ilo) belong to the steps below
+      const long long kb0 = (ilo == s0) ? klo : max(min(__shfl_sync(kFullS, bnd, st), khi), klo);
+      const long long K0 = S.keys[lane];  // key of the lane's first knot (row R + 4 lane)
+      const int imin = (int)(ilo - R), imax = (int)(ihi - R) - 1;
+      const float4 *wst = S.w + st * kStepS;
+      const float4 *wup = wst + kStepS;  // row R + 128 (the step above): right end of interval R + 127
+      // two independent queries per lane and round (k and k + 32), every lane through every
+      // shuffle; stores only for k < khi
+      for (long long kb = kb0; kb < khi; kb += 64) {
+        long long kk[2], kq[2];
+        double q[2];
+        int L[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          kk[u] = kb + 32 * u + lane;
+          q[u] = G.at(min(kk[u], khi - 1));
+          kq[u] = dkey(q[u]);
+          L[u] = 0;
+        }
+        // interval: largest i in [imin, imax] with x_{R+i} < q; first the lane among the
+        // lanes' first knots, then the row among that lane's four
+#pragma unroll
+        for (int stp = 16; stp >= 1; stp >>= 1) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const long long kc = shfl_i64(K0, L[u] + stp);
+            if (kc < kq[u]) L[u] += stp;
           }
-          const double xl = shfl_f64(xj, l);
-          const float fl = __shfl_sync(kFullS, fy, l), fl1 = __shfl_sync(kFullS, fy1, l);
-          const float pl = __shfl_sync(kFullS, ypp, l), pl1 = __shfl_sync(kFullS, yp1, l);
-          const float bl = __shfl_sync(kFullS, ba, l), ibl = __shfl_sync(kFullS, iba, l);
-          if (in) {
-            const float xa = dif32_up(q, xl);
-            I.yq[k] = to_f64(newint32(xa, bl - xa, fl, fl1, pl, pl1, bl, ibl));
-            if (I.jq) I.jq[k] = (int32_t)(R + l);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          int i = 4 * L[u];
+#pragma unroll
+          for (int v = 1; v < kVS; ++v) i += (S.keys[v * 32 + L[u]] < kq[u]) ? 1 : 0;
+          i = max(min(i, imax), imin);
+          if (kk[u] < khi) {
+            const float4 wj = wst[wpos(i)];
+            const float4 wj1 = (i + 1 < kStepS) ? wst[wpos(i + 1)] : wup[0];
+            const double xj = key_to_double(S.keys[wpos(i)]);
+            const float xa = dif32_up(q[u], xj);
+            I.yq[kk[u]] = to_f64(newint32(xa, wj.z - xa, wj.w, wj1.w, wj.y, wj1.y, wj.z, wj.x));
+            if (I.jq) I.jq[kk[u]] = (int32_t)(R + i);
           }
-          khi -= cnt;
-          if (cnt < 32) break;
         }
       }
-      fytop = __shfl_sync(kFullS, fy, 0);
+      khi = kb0;
     }
-    ycarry = __shfl_sync(kFullS, v, 0);
-    pcarry = __shfl_sync(kFullS, ypp, 0);
+    __syncwarp();
   }
   if (bad) atomicOr(I.status, bad);
 }
@@ -308,10 +531,10 @@ __device__ void scan_tile(const Inst &I, long long tile, float4 *__restrict__ W,
 template <int kMode>
 __global__ void __launch_bounds__(kThreadsS, 1)
     mixed_scan_kernel(const Inst *__restrict__ insts, int ninst, long long total_tiles,
-                      unsigned long long *__restrict__ counter, float4 *__restrict__ scratch, long long rows_cap) {
+                      unsigned long long *__restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  float4 *W = scratch + (size_t)warp * rows_cap;
+  ScanSmem &S = reinterpret_cast<ScanSmem *>(smem_raw)[threadIdx.x >> 5];
   for (;;) {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(counter, 1ull);
@@ -319,7 +542,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
     if ((long long)t >= total_tiles) break;
     const int i = find_inst(insts, ninst, (long long)t);
     const Inst I = insts[i];
-    scan_tile<kMode>(I, (long long)t - I.tile_begin, W, lane);
+    scan_tile<kMode>(I, (long long)t - I.tile_begin, S, lane);
     __syncwarp();
   }
 }
@@ -330,13 +553,12 @@ __global__ void __launch_bounds__(kThreadsS, 1)
 // device slot, maps the request's tiles into the device tile map and publishes them by
 // advancing `published`.  Every other warp is a worker: it claims one tile ticket at a time and,
 // once the ticket is published, solves that tile of that request with the warp-cooperative
-// binary32 fit + evaluation above (scan_tile<0>, in the warp's own scratch).  The warp finishing
-// a request's last tile writes the request's status and sequence number to mapped host memory.
-// All waits are
-// bounded: the scheduler leaves after `idle_ns` without work or at `deadline_ns`, and sets
-// `stop`; workers leave once stop is set and every published tile is claimed.  The host
-// relaunches the loop when new work arrives.  Launched cooperatively (one CTA per SM), so the
-// scheduler and the workers are co-resident.
+// binary32 fit + evaluation above (scan_tile<0>, in the warp's own shared memory).  The warp
+// finishing a request's last tile writes the request's status and sequence number to mapped host
+// memory.  All waits are bounded: the scheduler leaves after `idle_ns` without work or at
+// `deadline_ns`, and sets `stop`; workers leave once stop is set and every published tile is
+// claimed.  The host relaunches the loop when new work arrives.  Launched cooperatively (one CTA
+// per SM), so the scheduler and the workers are co-resident.
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -344,6 +566,7 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 }
 
 __global__ void __launch_bounds__(kThreadsS, 1) serve_kernel(ServeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const bool scheduler = (blockIdx.x == 0 && threadIdx.x < 32);
   const unsigned long long t_start = globaltimer_ns();
@@ -407,8 +630,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) serve_kernel(ServeArgs a) {
   }
 
   // workers: one ticket per warp; lane 0 waits for it (bounded) and the warp solves the tile
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  float4 *W = a.scan_scratch + (size_t)warp * a.scan_rows_cap;
+  ScanSmem &S = reinterpret_cast<ScanSmem *>(smem_raw)[threadIdx.x >> 5];
   for (;;) {
     unsigned long long t = 0;
     int state = 0;  // 1: the ticket is published; 2: no more work
@@ -451,7 +673,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) serve_kernel(ServeArgs a) {
 #pragma unroll
       for (int w = 0; w < (int)(sizeof(Inst) / 8); ++w) dst[w] = __ldcg(src + w);
     }
-    scan_tile<0>(I, (long long)(t - __ldcg(a.slot_first + slot)), W, lane);
+    scan_tile<0>(I, (long long)(t - __ldcg(a.slot_first + slot)), S, lane);
     __threadfence();
     __syncwarp();
     if (lane == 0) {
@@ -469,28 +691,50 @@ __global__ void __launch_bounds__(kThreadsS, 1) serve_kernel(ServeArgs a) {
   }
 }
 
+namespace {
+// The kernels take more than the default 48 KB of dynamic shared memory: allowed once per device
+// (the attribute belongs to the device's context).
+constexpr int kMaxDevS = 64;
+std::atomic<unsigned> g_smem_ok[kMaxDevS];
+cudaError_t allow_smem() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < kMaxDevS && g_smem_ok[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  const int bytes = (int)(kSmemPerWarpS * kWarpsS);
+  e = cudaFuncSetAttribute(mixed_scan_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(mixed_scan_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(mixed_scan_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && dev >= 0 && dev < kMaxDevS) g_smem_ok[dev].store(1u, std::memory_order_release);
+  return e;
+}
+}  // namespace
+
 cudaError_t launch_serve(const ServeArgs &args, int sm_count, cudaStream_t stream) {
+  const cudaError_t attr = allow_smem();
+  if (attr != cudaSuccess) return attr;
   ServeArgs copy = args;
   void *params[] = {&copy};
-  return cudaLaunchCooperativeKernel((const void *)serve_kernel, dim3((unsigned)sm_count), dim3(kThreadsS), params, 0,
-                                     stream);
+  return cudaLaunchCooperativeKernel((const void *)serve_kernel, dim3((unsigned)sm_count), dim3(kThreadsS), params,
+                                     kSmemPerWarpS * kWarpsS, stream);
 }
 
-int serve_tile_rows(int tile_rows) { return std::max(32, (tile_rows + 31) / 32 * 32); }
-long long serve_rows_cap(int tile_rows) { return (long long)serve_tile_rows(tile_rows) + kHaloS + kOvS; }
-size_t serve_scratch_bytes(int sm_count, int tile_rows) {
-  return (size_t)sm_count * (kThreadsS / 32) * (size_t)serve_rows_cap(tile_rows) * sizeof(float4);
+int serve_tile_rows(int tile_rows) {
+  return std::min(kTileMaxS, std::max(32, (tile_rows + 31) / 32 * 32));
 }
-
+int serve_tile_max() { return kTileMaxS; }
 
 int scan_mixed_threads_per_sm() { return kThreadsS; }
+int scan_mixed_tile_max() { return kTileMaxS; }
 
-// rows of one tile: a multiple of 32, about two tiles per resident warp for one instance
+// rows of one tile: a multiple of 32, about two tiles per resident warp for one instance, at most
+// the shared-memory capacity
 int scan_mixed_tile_rows(long long total_points, int sm_count, int count) {
-  const long long warps = (long long)sm_count * (kThreadsS / 32);
-  long long L = count > 1 ? 1024 : (total_points + 2 * warps - 1) / (2 * warps);
+  const long long warps = (long long)sm_count * kWarpsS;
+  long long L = count > 1 ? kTileMaxS : (total_points + 2 * warps - 1) / (2 * warps);
   L = (L + 31) / 32 * 32;
-  return (int)std::max<long long>(std::min<long long>(L, 1 << 20), 256);
+  return (int)std::max<long long>(std::min<long long>(L, kTileMaxS), 128);
 }
 
 long long threads_scan_mixed(int sm_count, long long total_tiles) {
@@ -499,21 +743,17 @@ long long threads_scan_mixed(int sm_count, long long total_tiles) {
   return (long long)blocks * bt;
 }
 
-size_t scratch_bytes_scan_mixed(long long threads, int tile_rows) {
-  const long long warps = (threads + 31) / 32;
-  return (size_t)warps * ((size_t)tile_rows + kHaloS + kOvS) * sizeof(float4);
-}
-
-cudaError_t launch_scan_mixed(const Inst *d_insts, int ninst, long long total_tiles, float *scratch, int tile_rows,
-                              int sm_count, unsigned long long *counter, cudaStream_t stream, int mode) {
+cudaError_t launch_scan_mixed(const Inst *d_insts, int ninst, long long total_tiles, int sm_count,
+                              unsigned long long *counter, cudaStream_t stream, int mode) {
+  const cudaError_t attr = allow_smem();
+  if (attr != cudaSuccess) return attr;
   int blocks, bt;
   spread_grid(sm_count, total_tiles * 32, kThreadsS, &blocks, &bt);
-  const long long rows_cap = (long long)tile_rows + kHaloS + kOvS;
-  float4 *W = reinterpret_cast<float4 *>(scratch);
+  const size_t smem = kSmemPerWarpS * (size_t)(bt / 32);
   switch (mode) {
-    case 1: mixed_scan_kernel<1><<<(unsigned)blocks, (unsigned)bt, 0, stream>>>(d_insts, ninst, total_tiles, counter, W, rows_cap); break;
-    case 2: mixed_scan_kernel<2><<<(unsigned)blocks, (unsigned)bt, 0, stream>>>(d_insts, ninst, total_tiles, counter, W, rows_cap); break;
-    default: mixed_scan_kernel<0><<<(unsigned)blocks, (unsigned)bt, 0, stream>>>(d_insts, ninst, total_tiles, counter, W, rows_cap); break;
+    case 1: mixed_scan_kernel<1><<<(unsigned)blocks, (unsigned)bt, smem, stream>>>(d_insts, ninst, total_tiles, counter); break;
+    case 2: mixed_scan_kernel<2><<<(unsigned)blocks, (unsigned)bt, smem, stream>>>(d_insts, ninst, total_tiles, counter); break;
+    default: mixed_scan_kernel<0><<<(unsigned)blocks, (unsigned)bt, smem, stream>>>(d_insts, ninst, total_tiles, counter); break;
   }
   return cudaGetLastError();
 }

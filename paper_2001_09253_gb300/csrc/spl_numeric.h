@@ -333,6 +333,69 @@ SPL_HD bool diff_f2(double b, double a, F2 *out) {
   return true;
 }
 
+// b - a as a double-float for b >= a with the same sign and exponent field (widths of increasing
+// knots): the count D < 2^52 of their shared ulp is exact; hi is D rounded to 24 significant bits
+// (an integer q in [2^23, 2^24] shifted, written straight into a binary32 encoding) and lo the
+// exact remainder D - hi rounded to binary32 (|lo| <= 2^-24 |hi|, so hi + lo carries about 47
+// bits), both times the ulp 2^(e-1075), a power of two within binary32's normal range.  Returns
+// false otherwise (b < a included); the caller then takes the general route (diff_f2).
+SPL_HD bool diff_up_f2(double b, double a, F2 *out) {
+  const uint64_t ub = bits64(b), ua = bits64(a);
+  const uint32_t hb = (uint32_t)(ub >> 52);
+  if (hb != (uint32_t)(ua >> 52)) return false;
+  const uint32_t e = hb & 0x7FFu;
+  if (e - 949u > 200u) return false;  // e in [949, 1149]: 2^(e-1075) and 2^(e-1075+53) normal
+  const uint64_t D = (hb & 0x800u) ? ua - ub : ub - ua;
+  if (D >> 52) return false;          // b < a (the count wraps)
+  const float scale = from_bits32((e - 1075u + 127u) << 23);
+  if (D < (1ull << 24)) {             // exact in binary32
+    *out = F2{(float)(uint32_t)D * scale, 0.0f};
+    return true;
+  }
+  const int sh = 40 - clz64(D);       // msb - 23, in [1, 28]
+  uint64_t q = D >> sh;
+  const uint64_t rem = D & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+  if (rem > half || (rem == half && (q & 1))) ++q;  // q in [2^23, 2^24]
+  const int64_t lo = (int64_t)(D - (q << sh));     // |lo| <= 2^(sh-1) < 2^28
+  // q in [2^23, 2^24] is 0x4A800000 + q as a binary32 encoding (2^24 rolls the exponent over);
+  // the shift goes into the exponent field
+  const float hi = from_bits32(0x4A800000u + (uint32_t)q + ((uint32_t)sh << 23));
+  *out = F2{hi * scale, (float)(int32_t)lo * scale};
+  return true;
+}
+
+// A binary64 value as a double-float on the integer pipe: hi = d rounded to binary32, lo = d - hi
+// rounded to binary32 (d - hi is exact: |d - hi| <= ulp32(hi)/2 holds at most 29 significant bits;
+// its rounding leaves hi + lo within 2^-48 |d|).  For |d| in binary32's normal range with room for
+// lo (biased binary64 exponent in [949, 1149]) and zero; false otherwise.
+SPL_HD bool f64_to_f2(double d, F2 *out) {
+  const uint64_t u = bits64(d);
+  const uint32_t e = (uint32_t)(u >> 52) & 0x7FFu;
+  if (e == 0u && (u << 1) == 0ull) {
+    *out = F2{from_bits32((uint32_t)(u >> 32) & 0x80000000u), 0.0f};
+    return true;
+  }
+  if (e - 949u > 200u) return false;
+  const uint64_t m = (u & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;  // 53 bits
+  uint64_t q = m >> 29;
+  const uint64_t rem = m & ((1ull << 29) - 1), half = 1ull << 28;
+  if (rem > half || (rem == half && (q & 1))) ++q;  // q in [2^23, 2^24]
+  const int32_t lo = (int32_t)((int64_t)m - (int64_t)(q << 29));  // |lo| <= 2^28
+  const uint32_t sign = (uint32_t)(u >> 63) << 31;
+  // hi = q 2^(e-1075+29): the encoding of q in [2^23, 2^24] moved by e - 1075 + 29 in the exponent
+  const float hi = from_bits32(sign | (0x4A800000u + (uint32_t)q + ((e - 1046u) << 23)));
+  const float lo_scale = from_bits32((e - 1075u + 127u) << 23);
+  *out = F2{hi, (sign ? -(float)lo : (float)lo) * lo_scale};
+  return true;
+}
+
+// Double-float product with a double-float: about 2^-46 relative (two_prod of the leading parts
+// plus the cross terms).
+SPL_HD F2 df_mul2(F2 a, F2 b) {
+  const F2 p = two_prod(a.hi, b.hi);
+  return fast_two_sum(p.hi, fma32(a.hi, b.lo, fma32(a.lo, b.hi, p.lo)));
+}
+
 // Exact binary32 -> binary64 conversion on the integer pipe (normal numbers and zero;
 // subnormal, infinite and NaN inputs go through the hardware conversion).
 SPL_HD double f32_to_f64(float f) {
@@ -359,6 +422,33 @@ SPL_HD float f64_to_f32(double d) {
   uint32_t bits = ((uint32_t)(u >> 63) << 31) | (uint32_t)((((uint64_t)e) << 23) + q);  // carry ripples into the exponent
   if (((bits >> 23) & 0xFF) == 0xFF) return (float)d;
   return from_bits32(bits);
+}
+
+// The one-division form of section "Fast Interpolation",
+//   S = (xa y_{j+1} + bx y_j + (1/6)((xa^2 - ba^2) xa y''_{j+1} + (bx^2 - ba^2) bx y''_j)) (1/ba),
+// with xa = q - x_j, bx = x_{j+1} - q, ba = x_{j+1} - x_j, evaluated in double-float arithmetic
+// (about 46 bits) on the integer and binary32 pipes: the differences exact (same-binade ulp
+// counts), the binary64 values, y'' and 1/ba split into double-floats, the result summed back into
+// binary64.  Returns false (and leaves *out unset) when an operand lies outside the routines'
+// domain (knots and query not in one binade, values outside binary32's range with room for the
+// low part); the caller then evaluates in binary64.
+SPL_HD bool newint_f2(double q, double xj, double xj1, double yj, double yj1, double ppj, double ppj1, double inv_ba,
+                      double *out) {
+  F2 xa, bx, ba, y0, y1, p0, p1, ib;
+  if (!diff_up_f2(q, xj, &xa) || !diff_up_f2(xj1, q, &bx) || !diff_up_f2(xj1, xj, &ba)) return false;
+  if (!f64_to_f2(yj, &y0) || !f64_to_f2(yj1, &y1) || !f64_to_f2(ppj, &p0) || !f64_to_f2(ppj1, &p1) ||
+      !f64_to_f2(inv_ba, &ib))
+    return false;
+  constexpr float kSixthHi = (float)(1.0 / 6.0);
+  constexpr float kSixthLo = (float)(1.0 / 6.0 - (double)kSixthHi);
+  const F2 ba2 = df_mul2(ba, ba);
+  const F2 C = df_mul2(df_mul2(df_add(df_mul2(xa, xa), df_neg(ba2)), xa), p1);
+  const F2 D = df_mul2(df_mul2(df_add(df_mul2(bx, bx), df_neg(ba2)), bx), p0);
+  const F2 lower = df_add(df_mul2(xa, y1), df_mul2(bx, y0));
+  const F2 sum = df_add(lower, df_mul2(df_add(C, D), F2{kSixthHi, kSixthLo}));
+  const F2 S = df_mul2(sum, ib);
+  *out = f32_to_f64(S.hi) + f32_to_f64(S.lo);
+  return true;
 }
 
 }  // namespace spl

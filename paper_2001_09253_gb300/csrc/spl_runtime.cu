@@ -157,6 +157,7 @@ namespace {
 spl_status cuda_fail(cudaError_t e) { return e == cudaSuccess ? SPL_OK : SPL_ERR_CUDA; }
 
 spl_status map_status_bits(unsigned bits) {
+  if (bits & spl::kStBadTile) return SPL_ERR_INVALID_ARG;
   if (bits & spl::kStNonFinite) return SPL_ERR_NONFINITE;
   if (bits & spl::kStNotIncreasing) return SPL_ERR_NOT_INCREASING;
   return SPL_OK;
@@ -285,8 +286,8 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
     for (uint32_t i = 0; i < count; ++i)
       if (reqs[i].n >= kScanMinRows) big += reqs[i].n;
     lp.scan_mixed = 2 * big >= total_points;
-    if (lp.scan_mixed)  // tiles of whole 32-row chunks
-      L = p->tile_rows > 0 ? (p->tile_rows + 31) / 32 * 32
+    if (lp.scan_mixed)  // tiles of whole 32-row chunks, no longer than the shared-memory scratch holds
+      L = p->tile_rows > 0 ? std::min((p->tile_rows + 31) / 32 * 32, spl::scan_mixed_tile_max())
                            : spl::scan_mixed_tile_rows((long long)total_points, c->sm_count, (int)count);
     else
       L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, count);
@@ -332,10 +333,7 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
   lp.total_tiles = tiles;
   lp.threads = threads_for(c, p->precision, tiles, lp.scan_mixed);
   lp.tile_rows = L;
-  lp.ring_bytes = !lp.fit                           ? 0
-                  : p->precision == SPL_PREC_F64   ? spl::ring_bytes_f64(lp.threads, L)
-                  : lp.scan_mixed                  ? spl::scratch_bytes_scan_mixed(lp.threads, L)
-                                                   : 0;
+  lp.ring_bytes = (lp.fit && p->precision == SPL_PREC_F64) ? spl::ring_bytes_f64(lp.threads, L) : 0;
 
   // footprint check against the whole budget first
   uint64_t need = round_up(sizeof(Inst) * count, kAlign) + round_up(status_block_bytes(count), kAlign) +
@@ -437,14 +435,12 @@ cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, 
                               lp.tile_rows, c->sm_count, counters, st);
     if (launches) *launches += 1;
   } else if (lp.scan_mixed) {
-    float *scr = reinterpret_cast<float *>(c->arena + d_ring_off);
     if (lp.refine_steps == 0) {
-      e = spl::launch_scan_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, c->sm_count, counters, st, 0);
+      e = spl::launch_scan_mixed(insts, count, lp.total_tiles, c->sm_count, counters, st, 0);
       if (launches) *launches += 1;
     } else {
-      e = spl::launch_scan_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, c->sm_count, counters, st, 1);
-      if (e == cudaSuccess)
-        e = spl::launch_scan_mixed(insts, count, lp.total_tiles, scr, lp.tile_rows, c->sm_count, counters + 1, st, 2);
+      e = spl::launch_scan_mixed(insts, count, lp.total_tiles, c->sm_count, counters, st, 1);
+      if (e == cudaSuccess) e = spl::launch_scan_mixed(insts, count, lp.total_tiles, c->sm_count, counters + 1, st, 2);
       if (launches) *launches += 2;
     }
   } else if (lp.refine_steps == 0) {
@@ -630,7 +626,7 @@ spl_status spl_plan_create(spl_ctx *c, const spl_plan_desc *d, spl_plan **out) {
   if (d->precision == SPL_PREC_F64 && d->refine_steps != 0) return SPL_ERR_INVALID_ARG;
   if (d->tile_rows != 0 && d->tile_rows < 16) return SPL_ERR_INVALID_ARG;
   if (d->query_mode != SPL_QUERY_UNIFORM && d->query_mode != SPL_QUERY_EXPLICIT) return SPL_ERR_INVALID_ARG;
-  if (d->eval_variant < SPL_EVAL_ORIG || d->eval_variant > SPL_EVAL_VOL) return SPL_ERR_INVALID_ARG;
+  if (d->eval_variant < SPL_EVAL_ORIG || d->eval_variant > SPL_EVAL_NOOP) return SPL_ERR_INVALID_ARG;
   spl_plan *p = new (std::nothrow) spl_plan();
   if (!p) return SPL_ERR_CUDA;
   p->ctx = c;

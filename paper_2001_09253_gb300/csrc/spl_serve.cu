@@ -39,12 +39,12 @@ double now_s() {
 uint64_t up256(uint64_t v) { return (v + 255) / 256 * 256; }
 
 // Per-request tile length of a server created with tile_rows = 0: about 32 tiles (warps) per
-// request, between 256 rows (a small request's latency: one short tile) and kServeTileMax (a
-// large one's throughput: each tile repeats 96 rows of start-up).
-constexpr int kServeTileMin = 256, kServeTileMax = 1024;
+// request, between 128 rows (a small request's latency: one short tile) and the longest tile the
+// workers' shared memory holds (a large one's throughput: each tile repeats 96 rows of start-up).
+constexpr int kServeTileMin = 128;
 int serve_tile_for(uint64_t n) {
   const uint64_t L = (n + 32 * 32 - 1) / (32 * 32) * 32;
-  return (int)std::min<uint64_t>(std::max<uint64_t>(L, kServeTileMin), kServeTileMax);
+  return (int)std::min<uint64_t>(std::max<uint64_t>(L, kServeTileMin), (uint64_t)spl::serve_tile_max());
 }
 
 struct Req {
@@ -169,8 +169,10 @@ spl_status pump(spl_server *s) {
     s->resident.pop_back();
     std::atomic_thread_fence(std::memory_order_acquire);
     const unsigned bits = s->h_done[2 * slot];
-    r.status = (bits & spl::kStNonFinite) ? SPL_ERR_NONFINITE : (bits & spl::kStNotIncreasing) ? SPL_ERR_NOT_INCREASING
-                                                                                                 : SPL_OK;
+    r.status = (bits & spl::kStBadTile)         ? SPL_ERR_INVALID_ARG
+               : (bits & spl::kStNonFinite)     ? SPL_ERR_NONFINITE
+               : (bits & spl::kStNotIncreasing) ? SPL_ERR_NOT_INCREASING
+                                                : SPL_OK;
     r.state = 2;
     r.t_done = t;
     s->slot_ticket[slot] = 0;
@@ -237,7 +239,6 @@ spl_status spl_serve_create(spl_ctx *c, const spl_serve_desc *d, spl_server **ou
   // tile_rows 0: per request (serve_tile_for); otherwise one length, a whole number of chunks
   if (s->d.tile_rows)
     s->d.tile_rows = (uint32_t)spl::serve_tile_rows((int)std::min<uint32_t>(s->d.tile_rows, 1u << 20));
-  const int scratch_rows = s->d.tile_rows ? (int)s->d.tile_rows : kServeTileMax;
   if (!s->d.idle_timeout_ms) s->d.idle_timeout_ms = 200;
   s->device = spl_ctx_device(c);
   s->sms = spl_ctx_sms(c);
@@ -253,14 +254,6 @@ spl_status spl_serve_create(spl_ctx *c, const spl_serve_desc *d, spl_server **ou
   if (!spl_ctx_arena_alloc(c, total, &off)) return SPL_ERR_BUDGET;
   s->blocks.push_back({off, total});
   char *base = spl_ctx_arena_base(c) + off;
-  // the workers' scratch (one slice per warp of the launch)
-  const uint64_t scratch = up256(spl::serve_scratch_bytes(s->sms, scratch_rows));
-  uint64_t soff = 0;
-  if (!spl_ctx_arena_alloc(c, scratch, &soff)) {
-    release_server(s.get());
-    return SPL_ERR_BUDGET;
-  }
-  s->blocks.push_back({soff, scratch});
   ServeArgs &a = s->args;
   a.published = reinterpret_cast<unsigned long long *>(base);
   a.claimed = a.published + 1;
@@ -285,8 +278,6 @@ spl_status spl_serve_create(spl_ctx *c, const spl_serve_desc *d, spl_server **ou
   // a single launch never runs longer than the deadline; the host relaunches
   a.deadline_ns = (unsigned long long)(s->d.deadline_ms ? s->d.deadline_ms : 30000u) * 1000000ull;
   a.fault_flags = s->d.fault_flags;
-  a.scan_scratch = reinterpret_cast<float4 *>(spl_ctx_arena_base(c) + soff);
-  a.scan_rows_cap = spl::serve_rows_cap(scratch_rows);
   // mapped host block: tail, stop, consumed, alive, done words, ring
   const uint64_t hbytes = 256 + up256(8ull * S) + sizeof(ServeEntry) * rcap;
   if (cudaHostAlloc(&s->hblock, hbytes, cudaHostAllocMapped) != cudaSuccess) {

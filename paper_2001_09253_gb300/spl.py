@@ -24,7 +24,7 @@ ERR_QUEUE_FULL, ERR_TIMEOUT, ERR_CUDA, ERR_UNKNOWN_TICKET, ERR_STATE = -5, -6, -
 PREC_F64, PREC_F32_REFINE = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 QUERY_UNIFORM, QUERY_EXPLICIT = 0, 1
-EVAL_ORIG, EVAL_NOINV, EVAL_VOL = 0, 1, 2
+EVAL_ORIG, EVAL_NOINV, EVAL_VOL, EVAL_NOOP = 0, 1, 2, 3
 NATURAL = 1e32
 
 EXPORTS = [

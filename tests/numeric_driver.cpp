@@ -59,3 +59,27 @@ void t_df_mul(float ah, float al, float bh, float bl, float *ph, float *pl) {
   *pl = q.lo;
 }
 }
+
+extern "C" {
+int t_diff_up_f2(double b, double a, float *hi, float *lo) {
+  spl::F2 r;
+  if (!spl::diff_up_f2(b, a, &r)) return 0;
+  *hi = r.hi;
+  *lo = r.lo;
+  return 1;
+}
+int t_f64_to_f2(double d, float *hi, float *lo) {
+  spl::F2 r;
+  if (!spl::f64_to_f2(d, &r)) return 0;
+  *hi = r.hi;
+  *lo = r.lo;
+  return 1;
+}
+}
+
+extern "C" {
+int t_newint_f2(double q, double xj, double xj1, double yj, double yj1, double ppj, double ppj1, double inv_ba,
+                double *out) {
+  return spl::newint_f2(q, xj, xj1, yj, yj1, ppj, ppj1, inv_ba, out) ? 1 : 0;
+}
+}

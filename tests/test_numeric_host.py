@@ -313,3 +313,99 @@ def test_float_double_conversions(lib):
     for base in [1.0, 1.5, 3.0]:
         tie = base + 2.0 ** -24 * (1 if base < 2 else 2)
         assert lib.t_f64_to_f32(tie) == float(np.float32(tie))
+
+
+def _f2_call(lib, name, *args):
+    fn = getattr(lib, name)
+    hi, lo = ctypes.c_float(), ctypes.c_float()
+    ok = fn(*args, ctypes.byref(hi), ctypes.byref(lo))
+    return bool(ok), Fraction(hi.value) + Fraction(lo.value), hi.value
+
+
+def test_ordered_difference_as_double_float(lib):
+    """The same-binade double-float width (b >= a): hi is b - a rounded to binary32, hi + lo is
+    within 2^-47 of the exact difference; other binades, b < a and out-of-range scales refused."""
+    lib.t_diff_up_f2.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_float),
+                                 ctypes.POINTER(ctypes.c_float)]
+    lib.t_diff_up_f2.restype = ctypes.c_int
+    rng = np.random.default_rng(12)
+    hits = 0
+    for _ in range(8000):
+        a = rng.normal() * 10.0 ** rng.integers(-20, 20)
+        b = a + abs(a) * rng.random() * 10.0 ** rng.integers(-16, 0)
+        if rng.random() < 0.05:
+            b = a
+        ok, got, hi = _f2_call(lib, "t_diff_up_f2", float(b), float(a))
+        if not ok:
+            continue
+        hits += 1
+        exact = Fraction(float(b)) - Fraction(float(a))
+        assert abs(got - exact) <= abs(exact) * Fraction(1, 2 ** 47), (a, b)
+        assert hi == rn32(exact), (a, b)
+    assert hits > 5000
+    one, ulp = 1.0, 2.0 ** -52
+    for d in (1, 2 ** 24 - 1, 2 ** 24, 2 ** 24 + 1, 2 ** 24 + 3, 3 * 2 ** 30 + 2 ** 6, 2 ** 51 + 12345, 2 ** 52 - 1):
+        b = one + d * ulp
+        for (bb, aa) in ((b, one), (-one, -b)):
+            ok, got, hi = _f2_call(lib, "t_diff_up_f2", bb, aa)
+            assert ok and got == Fraction(bb) - Fraction(aa) or abs(got - (Fraction(bb) - Fraction(aa))) <= \
+                (Fraction(bb) - Fraction(aa)) * Fraction(1, 2 ** 47), d
+        assert not _f2_call(lib, "t_diff_up_f2", one, b)[0], d          # b < a
+    assert not _f2_call(lib, "t_diff_up_f2", 2.0, 1.9)[0]                # two binades
+    assert not _f2_call(lib, "t_diff_up_f2", 1e300, 1e300 * (1 - 1e-15))[0]
+
+
+def test_binary64_as_double_float(lib):
+    """A binary64 value split into hi = RN32(d) and lo = RN32(d - hi): hi + lo within 2^-48 |d|,
+    signs and zeros kept; values outside the range refused."""
+    lib.t_f64_to_f2.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
+    lib.t_f64_to_f2.restype = ctypes.c_int
+    rng = np.random.default_rng(13)
+    for _ in range(8000):
+        d = float(rng.normal() * 10.0 ** rng.integers(-20, 30))
+        ok, got, hi = _f2_call(lib, "t_f64_to_f2", d)
+        assert ok == (2.0 ** -74 <= abs(d) < 2.0 ** 126), d  # binary64 exponents 949 .. 1149
+        if not ok:
+            continue
+        assert hi == rn32(Fraction(d)), d
+        assert abs(got - Fraction(d)) <= abs(Fraction(d)) * Fraction(1, 2 ** 48), d
+    for d in (1.0, -1.0, 1.0 + 2.0 ** -52, 2.0 - 2.0 ** -52, -(2.0 - 2.0 ** -52), 1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -25,
+              2.0 ** -70, 2.0 ** 100 * 1.7):
+        ok, got, hi = _f2_call(lib, "t_f64_to_f2", d)
+        assert ok and hi == rn32(Fraction(d)) and abs(got - Fraction(d)) <= abs(Fraction(d)) * Fraction(1, 2 ** 48), d
+    ok, got, hi = _f2_call(lib, "t_f64_to_f2", -0.0)
+    assert ok and got == 0 and math.copysign(1.0, hi) == -1.0
+    for d in (1e-200, 1e200, 2.0 ** -80, 2.0 ** 127, float("inf"), float("nan"), 5e-324):
+        assert not _f2_call(lib, "t_f64_to_f2", d)[0], d
+
+
+def test_newint_in_double_float_against_exact(lib):
+    """The one-division form of "Fast Interpolation" in double-float arithmetic against the same
+    form evaluated exactly on the binary64 operands: within 2^-40 of the largest term magnitude
+    (|y_j|, |y_{j+1}|, h^2 max|y''| / 6), far inside the FP64 path's 1e-12."""
+    lib.t_newint_f2.argtypes = [ctypes.c_double] * 8 + [ctypes.POINTER(ctypes.c_double)]
+    lib.t_newint_f2.restype = ctypes.c_int
+    rng = np.random.default_rng(14)
+    hits = 0
+    for _ in range(4000):
+        x0 = float(rng.random() * 10.0 ** rng.integers(-2, 7))
+        h = float(abs(x0) * 10.0 ** rng.uniform(-9, -1) + 1e-3 * rng.random())
+        x1 = x0 + h
+        if not x1 > x0:
+            continue
+        q = x0 + (x1 - x0) * float(rng.random())
+        q = min(max(q, x0), x1)
+        y0, y1 = (float(v) for v in rng.normal(size=2) * 10.0 ** rng.integers(-3, 3))
+        p0, p1 = (float(v) for v in rng.normal(size=2) * 10.0 ** rng.integers(-3, 6))
+        inv = 1.0 / (x1 - x0)
+        out = ctypes.c_double()
+        if not lib.t_newint_f2(q, x0, x1, y0, y1, p0, p1, inv, ctypes.byref(out)):
+            continue
+        hits += 1
+        Q, X0, X1 = Fraction(q), Fraction(x0), Fraction(x1)
+        xa, bx, ba = Q - X0, X1 - Q, X1 - X0
+        exact = (xa * Fraction(y1) + bx * Fraction(y0) + ((xa * xa - ba * ba) * xa * Fraction(p1) +
+                 (bx * bx - ba * ba) * bx * Fraction(p0)) / 6) * Fraction(inv)
+        scale = max(abs(Fraction(y0)), abs(Fraction(y1)), ba * ba * max(abs(Fraction(p0)), abs(Fraction(p1))) / 6)
+        assert abs(Fraction(out.value) - exact) <= scale * Fraction(1, 2 ** 40), (q, x0, x1)
+    assert hits > 2500
