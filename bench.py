@@ -609,7 +609,9 @@ def serving(r, pool_count=512, seed=3, lo=1e2, hi=1e6, rate=20000.0, warm_s=1.0,
                        "cubic, exact binary64 differences and query positions), admission under a 150 GB HBM budget, "
                        "persistent device loop" % (rate, run_s, pool_count),
            "requests": nm, "offered_rate": rate, "value": nm / makespan, "unit": "instances/s",
-           "points_per_s": pts / makespan, "latency_ms": {"p50": float(np.percentile(lat, 50)),
+           "points_per_s": pts / makespan, "latency_ms": {"p16": float(np.percentile(lat, 16)),
+                                                          "p50": float(np.percentile(lat, 50)),
+                                                          "p84": float(np.percentile(lat, 84)),
                                                           "p99": float(np.percentile(lat, 99)),
                                                           "max": float(lat.max()),
                                                           "what": "scheduled arrival to completion seen by the host"}}
@@ -624,6 +626,24 @@ def serving(r, pool_count=512, seed=3, lo=1e2, hi=1e6, rate=20000.0, warm_s=1.0,
     res["loop_launches"] = st1["loop_launches"] - st0["loop_launches"]
     srv.close()
     torch.cuda.synchronize(r.dev)
+    # the same stream with one refinement step per request (the precision the targets state)
+    srvr = spl.Server(r.ctx, max_inflight=2048, tile_rows=0, budget_bytes=150 * 10 ** 9, refine_steps=1)
+    s, _, _ = srvr.replay(reqs, np.arange(nw) % pool_count, synth.poisson_arrivals(seed + 101, rate, nw))
+    assert s == spl.OK
+    nr = int(rate * min(run_s, 4.0))
+    s, latr, mkr = srvr.replay(reqs, pick[:nr], arr[:nr])
+    assert s == spl.OK
+    s, _, mkr2 = srvr.replay(reqs, np.arange(nsat) % pool_count, np.zeros(nsat))
+    assert s == spl.OK
+    srvr.close()
+    torch.cuda.synchronize(r.dev)
+    res["refined"] = {"workload": "the same arrivals (first %d) served with one refinement step of y'' per request"
+                                  % nr, "requests": nr, "value": nr / mkr, "unit": "instances/s",
+                      "latency_ms": {"p16": float(np.percentile(latr, 16)), "p50": float(np.percentile(latr, 50)),
+                                     "p84": float(np.percentile(latr, 84)), "p99": float(np.percentile(latr, 99)),
+                                     "max": float(latr.max())},
+                      "saturation": {"requests": nsat, "value": nsat / mkr2, "unit": "instances/s",
+                                     "gb_per_s": BYTES_PER_POINT * pts2 / mkr2 / 1e9}}
     rng = np.random.default_rng(1)
     sample = {}
     for i in rng.choice(pool_count, size=24, replace=False):
@@ -868,7 +888,7 @@ def summary(line):
             if not isinstance(d, dict) or k not in d or d[k] is None:
                 return None
             d = d[k]
-        return round(d, 6) if isinstance(d, float) else d
+        return float("%.4g" % d) if isinstance(d, float) else d
 
     oc = line.get("other_configs", {})
     out = {"f64_1e7": {"ms": g(line, "ms_per_step"), "inst_s": g(line, "value"),
@@ -892,7 +912,10 @@ def summary(line):
                           "plain_mixed_inst_s": g(sv, "plain_mixed_refine0_same_pool", "value"),
                           "served_over_plain_f64": g(sv, "served_over_plain_instances_per_s"),
                           "served_over_plain_same_precision": g(sv, "served_over_plain_same_precision"),
-                          "oracle_inst_s_all": g(sv, "cpu_baseline", "value"), "err_yq": g(sv, "error_vs_oracle", "yq")}
+                          "oracle_inst_s_all": g(sv, "cpu_baseline", "value"), "err_yq": g(sv, "error_vs_oracle", "yq"),
+                          "refined_p50_ms": g(sv, "refined", "latency_ms", "p50"),
+                          "refined_p99_ms": g(sv, "refined", "latency_ms", "p99"),
+                          "refined_sat_inst_s": g(sv, "refined", "saturation", "value")}
     c1 = oc.get("n1000") or {}
     out["n1000"] = {k: {"dev_p50_ms": g(c1, k, "device_ms", "median"), "dev_p99_ms": g(c1, k, "device_ms", "p99"),
                         "wall_p50_ms": g(c1, k, "wall_ms", "median"), "wall_p99_ms": g(c1, k, "wall_ms", "p99")}

@@ -270,8 +270,8 @@ spl_status spl_generate_curve(uint64_t seed, uint64_t instance, uint64_t n, doub
  * A server owns a persistent kernel (one CTA per SM, cooperative launch) on its own stream:
  * a scheduler warp takes requests from a ring in mapped host memory and publishes their tiles;
  * worker warps solve published tiles, one tile per warp (binary32 solve and cubic, exact
- * binary64 differences and query positions: the mixed path without refinement), so the work of
- * requests that arrive while others run overlaps on the device.  A request is admitted
+ * binary64 differences and query positions: the mixed path, with or without refinement), so the
+ * work of requests that arrive while others run overlaps on the device.  A request is admitted
  * when a slot is free, its tiles fit the tile map and its footprint (16 n + 8 m bytes, plus
  * 8 n for y'' and 4 m for indices when requested) fits in budget_bytes; otherwise it waits in
  * a host FIFO and is admitted by a later submit/poll/wait.  The device loop exits after
@@ -295,7 +295,13 @@ spl_status spl_generate_curve(uint64_t seed, uint64_t instance, uint64_t n, doub
  *                    rest, so the context stays usable.
  *   fault_flags      failure-detection tests only (0 otherwise): bit 0 makes the scheduler warp
  *                    leave at once without publishing any work or the stop word, so that the
- *                    workers' bounded waits run out. */
+ *                    workers' bounded waits run out.
+ *   refine_steps     0: the binary32 solve as is; 1: one step of iterative refinement of y''
+ *                    against a double-float residual before the evaluation, as spl_plan_desc's
+ *                    refine_steps (each tile is solved twice: the second pass of a request starts
+ *                    once all of its first-pass tiles are done).  The footprint then includes 4 n
+ *                    bytes of binary32 y'' carved from the context's arena while the request is
+ *                    resident.  Other values are SPL_ERR_INVALID_ARG. */
 typedef struct spl_server spl_server;
 typedef struct spl_serve_desc {
   uint32_t max_inflight;
@@ -305,7 +311,7 @@ typedef struct spl_serve_desc {
   uint32_t idle_timeout_ms;
   uint32_t deadline_ms;
   uint32_t fault_flags;
-  uint32_t reserved;
+  uint32_t refine_steps;
 } spl_serve_desc;
 
 spl_status spl_serve_create(spl_ctx *ctx, const spl_serve_desc *desc, spl_server **out);

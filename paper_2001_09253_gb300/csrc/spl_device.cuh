@@ -24,13 +24,16 @@ struct Inst {
   long long tile_begin; // global index of this instance's first tile
   long long ntiles;     // tiles of this instance
   int tile_rows;        // knots per tile (the last tile of an instance is ragged)
-  int pad;              // bit 0: grouped tile geometry (FP64 kernel)
+  int pad;              // bit 0: grouped tile geometry (FP64 kernel); bit 1: served with refinement
   unsigned *status;     // device word, OR of kSt* bits
   float *z;             // mixed path with refinement: binary32 y'' of the first pass (n), scratch
   const double *xq;     // separate evaluation: explicit query positions (mq), or null for the grid
   long long mq;         // separate evaluation: queries (the fused kernels see m = 0 then)
   long long q_begin;    // separate evaluation: global index of this instance's first query
 };
+
+// Inst::pad bit of a served request with one refinement step (two passes over its tiles).
+constexpr int kServeRefined = 2;
 
 // One request appended by the host to the serving ring (mapped host memory).
 struct ServeEntry {

@@ -32,6 +32,12 @@ int f64_threads_per_sm();  // resident threads of the FP64 kernel per SM
 cudaError_t launch_fused_f64(const Inst *d_insts, int ninst, long long total_tiles, double *scratch,
                              int tile_rows, int sm_count, unsigned long long *counter, cudaStream_t stream);
 
+// FP64 fit + evaluation of small instances, one CTA per instance (spl_small_f64.cu): for
+// instances of at most small_f64_max_rows() knots (latency path; no scratch beyond the CTA's
+// shared memory).
+int small_f64_max_rows();
+cudaError_t launch_small_f64(const Inst *d_insts, int ninst, cudaStream_t stream);
+
 // Mixed-precision fused fit + evaluation (spl_fused_mixed.cu).
 long long threads_mixed(int sm_count, long long total_tiles);
 int mixed_threads_per_sm();  // threads of one ring-kernel CTA (one CTA per SM)

@@ -41,7 +41,7 @@ constexpr int kVS = 4;                 // consecutive rows per lane in a step
 constexpr int kStepS = 32 * kVS;       // rows per warp step
 constexpr int kHaloS = 64;             // forward rows before a tile
 constexpr int kOvS = 32;               // back-substitution start past a tile
-constexpr int kWarpsS = 16;            // warps per CTA (one CTA per SM)
+constexpr int kWarpsS = 20;            // warps per CTA (one CTA per SM; 12 / 16 / 20 measured: more is faster)
 constexpr int kThreadsS = 32 * kWarpsS;
 constexpr int kTileMaxS = 512;         // longest tile the shared-memory scratch holds
 constexpr int kRowsCapS = (kTileMaxS + kHaloS + kOvS + kStepS - 1) / kStepS * kStepS;
@@ -69,6 +69,14 @@ __device__ __forceinline__ double key_to_double(long long k) {
   return __longlong_as_double(k ^ ((k >> 63) & 0x7FFFFFFFFFFFFFFFLL));
 }
 
+// kCG: through L2 only (ld.global.cg): the persistent serving loop reads buffers that other SMs,
+// or earlier requests at the same addresses, may have left in this SM's L1.
+template <bool kCG, typename T>
+__device__ __forceinline__ T ldx(const T *p) {
+  if (kCG) return __ldcg(p);
+  return *p;
+}
+
 // Least k in [0, m] with x_k > v on the uniform grid, one value per lane: the estimate
 // floor((v - x_0) / step) from binary64 arithmetic (within one of the answer: the grid points are
 // rounded sums) checked on the two grid points around it by their keys, with a walk for the rare
@@ -91,10 +99,11 @@ __device__ __forceinline__ long long grid_first_above(const Grid &G, double inv_
 
 // The uniform grid of the instance: x_0, x_{n-1}, step = (x_{n-1} - x_0)/(m - 1) as the correctly
 // rounded quotient (quot64 equals the IEEE division bit for bit) and 1/step for estimates.
+template <bool kCG>
 __device__ __forceinline__ Grid grid_of(const double *x, long long n, long long m, double *inv_step) {
   Grid g;
-  g.x0 = x[0];
-  g.xl = x[n - 1];
+  g.x0 = ldx<kCG>(x);
+  g.xl = ldx<kCG>(x + n - 1);
   g.m = m;
   g.step = 0.0;
   *inv_step = 0.0;
@@ -115,14 +124,14 @@ struct CarryS {
 
 // Loads of a lane's rows j0 .. j0+4 (the fifth is the next lane's first: the width and slope of
 // the fourth row's interval need it).  `full`: every row exists.
-template <typename T>
+template <bool kCG, typename T>
 __device__ __forceinline__ void load5(const T *__restrict__ p, long long j0, long long n, bool full, T (&v)[kVS + 1]) {
   if (full) {
 #pragma unroll
-    for (int u = 0; u <= kVS; ++u) v[u] = p[j0 + u];
+    for (int u = 0; u <= kVS; ++u) v[u] = ldx<kCG>(p + j0 + u);
   } else {
 #pragma unroll
-    for (int u = 0; u <= kVS; ++u) v[u] = (j0 + u < n) ? p[j0 + u] : T(0);
+    for (int u = 0; u <= kVS; ++u) v[u] = (j0 + u < n) ? ldx<kCG>(p + j0 + u) : T(0);
   }
 }
 
@@ -304,7 +313,7 @@ __device__ __forceinline__ void fwd_step(const Inst &I, const EndsS &E, long lon
 // y'' to I.z (first pass of the refined path); 2: one refinement step of I.z (the residual
 // r = d - A Z in double-float arithmetic from exact double-float widths and value differences,
 // A delta = r solved with the binary32 matrix), y'' = Z + delta, and the evaluation.
-template <int kMode>
+template <int kMode, bool kCG = false>
 __device__ void scan_tile(const Inst &I, long long tile, ScanSmem &S, int lane) {
   const long long n = I.n, TR = I.tile_rows;
   if (TR < 1 || TR > kTileMaxS) {  // never launched by the host: the scratch would not hold it
@@ -335,9 +344,9 @@ __device__ void scan_tile(const Inst &I, long long tile, ScanSmem &S, int lane) 
   {
     const long long j0 = f0 + (long long)kVS * lane;
     const bool full = f0 + kStepS + 1 <= n;
-    load5(x, j0, n, full, xn);
-    load5(y, j0, n, full, yn);
-    if (kMode == 2) load5(z, j0, n, full, zn);
+    load5<kCG>(x, j0, n, full, xn);
+    load5<kCG>(y, j0, n, full, yn);
+    if (kMode == 2) load5<kCG>(z, j0, n, full, zn);
   }
   for (int st = 0; st < nsteps; ++st) {
     const long long R = f0 + (long long)st * kStepS;
@@ -352,9 +361,9 @@ __device__ void scan_tile(const Inst &I, long long tile, ScanSmem &S, int lane) 
     if (st + 1 < nsteps) {
       const long long Rn = R + kStepS, j0 = Rn + (long long)kVS * lane;
       const bool full = Rn + kStepS + 1 <= n;
-      load5(x, j0, n, full, xn);
-      load5(y, j0, n, full, yn);
-      if (kMode == 2) load5(z, j0, n, full, zn);
+      load5<kCG>(x, j0, n, full, xn);
+      load5<kCG>(y, j0, n, full, yn);
+      if (kMode == 2) load5<kCG>(z, j0, n, full, zn);
     }
     float4 *ws = S.w + st * kStepS;
     const bool edge = R == 0 || R + kStepS > f1 || R + kStepS + 1 > n;
@@ -376,7 +385,7 @@ __device__ void scan_tile(const Inst &I, long long tile, ScanSmem &S, int lane) 
   long long bnd = 0, klo = 0, khi = 0;
   if (evaluate) {
     double inv_step;
-    G = grid_of(x, n, m, &inv_step);
+    G = grid_of<kCG>(x, n, m, &inv_step);
     bool need = false;
     long long r = 0;
     if (lane == 31) {
@@ -386,7 +395,7 @@ __device__ void scan_tile(const Inst &I, long long tile, ScanSmem &S, int lane) 
       r = max(f0 + (long long)lane * kStepS, s0);
       need = r > 0 && r < min(e0, n - 1);
     }
-    const double v = need ? x[r] : 0.0;
+    const double v = need ? ldx<kCG>(x + r) : 0.0;
     need = need && finite64(v);
     bnd = grid_first_above(G, inv_step, need, v);
     if (lane == 31 && e0 >= n - 1) bnd = m;
@@ -399,8 +408,8 @@ __device__ void scan_tile(const Inst &I, long long tile, ScanSmem &S, int lane) 
   float zb[kVS + 1];
   {
     const long long j0 = f0 + (long long)(nsteps - 1) * kStepS + (long long)kVS * lane;
-    if (evaluate) load5(x, j0, n, false, xb);
-    if (kMode == 2) load5(z, j0, n, false, zb);
+    if (evaluate) load5<kCG>(x, j0, n, false, xb);
+    if (kMode == 2) load5<kCG>(z, j0, n, false, zb);
   }
   for (int st = nsteps - 1; st >= st_lo; --st) {
     const long long R = f0 + (long long)st * kStepS;
@@ -414,8 +423,8 @@ __device__ void scan_tile(const Inst &I, long long tile, ScanSmem &S, int lane) 
     }
     if (st > st_lo) {  // the step below lies inside the forward range: every row exists
       const long long jb = j0 - kStepS;
-      if (evaluate) load5(x, jb, n, true, xb);
-      if (kMode == 2) load5(z, jb, n, true, zb);
+      if (evaluate) load5<kCG>(x, jb, n, true, xb);
+      if (kMode == 2) load5<kCG>(z, jb, n, true, zb);
     }
     float4 *ws = S.w + st * kStepS;
     float4 cd[kVS];
@@ -559,6 +568,12 @@ __global__ void __launch_bounds__(kThreadsS, 1)
 // `deadline_ns`, and sets `stop`; workers leave once stop is set and every published tile is
 // claimed.  The host relaunches the loop when new work arrives.  Launched cooperatively (one CTA
 // per SM), so the scheduler and the workers are co-resident.
+// Tile tickets of a served request: its tiles once, or twice with refinement (first pass, then
+// the refinement pass with the evaluation).
+__device__ __forceinline__ unsigned long long serve_tickets(const Inst &I) {
+  return (unsigned long long)I.ntiles * ((I.pad & kServeRefined) ? 2ull : 1ull);
+}
+
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -595,14 +610,13 @@ __global__ void __launch_bounds__(kThreadsS, 1) serve_kernel(ServeArgs a) {
         const unsigned slot = ent.slot;
         if (lane == 0) {
           ent.inst.status = a.slot_status + slot;
-          ent.inst.z = nullptr;
           a.slot_inst[slot] = ent.inst;
           a.slot_first[slot] = ent.first_tile;
           a.slot_done[slot] = 0u;
           a.slot_status[slot] = 0u;
           a.slot_seq[slot] = ent.seq;
         }
-        const unsigned long long nt = (unsigned long long)ent.inst.ntiles;
+        const unsigned long long nt = serve_tickets(ent.inst);
         for (unsigned long long i = lane; i < nt; i += 32) a.tile_slot[(ent.first_tile + i) % a.tile_cap] = slot;
         __threadfence();
         __syncwarp();
@@ -673,12 +687,38 @@ __global__ void __launch_bounds__(kThreadsS, 1) serve_kernel(ServeArgs a) {
 #pragma unroll
       for (int w = 0; w < (int)(sizeof(Inst) / 8); ++w) dst[w] = __ldcg(src + w);
     }
-    scan_tile<0>(I, (long long)(t - __ldcg(a.slot_first + slot)), S, lane);
+    const long long local = (long long)(t - __ldcg(a.slot_first + slot));
+    bool ok = true;
+    if (!(I.pad & kServeRefined)) {
+      scan_tile<0, true>(I, local, S, lane);
+    } else if (local < I.ntiles) {  // refinement, first pass: binary32 y'' into the request's Z
+      scan_tile<1, true>(I, local, S, lane);
+    } else {
+      // second pass: once every first-pass tile of the request is done (its tiles were claimed
+      // before this one and never wait, so this wait ends; it is bounded all the same)
+      if (lane == 0) {
+        unsigned sleep_ns = 32;
+        while (*(volatile unsigned *)(a.slot_done + slot) < (unsigned)I.ntiles) {
+          if (globaltimer_ns() - t_start > a.deadline_ns + 1000000000ull) {
+            atomicOr(a.err, 1u);
+            ok = false;
+            break;
+          }
+          __nanosleep(sleep_ns);
+          if (sleep_ns < 1024) sleep_ns <<= 1;
+        }
+        __threadfence();
+      }
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      __syncwarp();
+      if (ok) scan_tile<2, true>(I, local - I.ntiles, S, lane);
+    }
+    if (!ok) continue;  // the loop's error flag is raised: the host times the request out
     __threadfence();
     __syncwarp();
     if (lane == 0) {
       const unsigned done = atomicAdd(a.slot_done + slot, 1u) + 1u;
-      if (done == (unsigned)I.ntiles) {
+      if (done == (unsigned)serve_tickets(I)) {
         __threadfence();
         const unsigned st = *(volatile unsigned *)(a.slot_status + slot);
         a.h_done[2 * slot] = st;

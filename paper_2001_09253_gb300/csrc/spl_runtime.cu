@@ -240,6 +240,7 @@ struct LaunchPlan {
   long long threads = 0;
   uint64_t ring_bytes = 0;
   bool fit = true;             // run the fit kernel(s)
+  bool small_f64 = false;      // FP64: every instance small enough for one CTA (latency path)
   bool scan_mixed = false;     // binary32: the warp-cooperative kernel (with refinement: two launches)
   bool separate_eval = false;  // evaluate with the separate kernel (explicit queries, stored y'')
   int eval_variant = 0;
@@ -295,6 +296,10 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
     L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, count);
   }
   lp.eval_variant = p->eval_variant;
+  if (p->precision == SPL_PREC_F64 && p->tile_rows == 0 && lp.fit && !lp.separate_eval) {
+    lp.small_f64 = true;
+    for (uint32_t i = 0; i < count; ++i) lp.small_f64 = lp.small_f64 && reqs[i].n <= (uint64_t)spl::small_f64_max_rows();
+  }
   lp.insts.resize(count);
   // Instances of 32 tiles or more of the FP64 kernel use the grouped geometry: their tiles
   // start on a warp boundary, and each warp's 32 tiles cover 32L - overhang - lane0_short rows
@@ -333,7 +338,7 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
   lp.total_tiles = tiles;
   lp.threads = threads_for(c, p->precision, tiles, lp.scan_mixed);
   lp.tile_rows = L;
-  lp.ring_bytes = (lp.fit && p->precision == SPL_PREC_F64) ? spl::ring_bytes_f64(lp.threads, L) : 0;
+  lp.ring_bytes = (lp.fit && p->precision == SPL_PREC_F64 && !lp.small_f64) ? spl::ring_bytes_f64(lp.threads, L) : 0;
 
   // footprint check against the whole budget first
   uint64_t need = round_up(sizeof(Inst) * count, kAlign) + round_up(status_block_bytes(count), kAlign) +
@@ -430,6 +435,9 @@ cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, 
   cudaError_t e = cudaSuccess;
   if (!lp.fit) {
     // stored y'': evaluation only
+  } else if (lp.precision == SPL_PREC_F64 && lp.small_f64) {
+    e = spl::launch_small_f64(insts, count, st);
+    if (launches) *launches += 1;
   } else if (lp.precision == SPL_PREC_F64) {
     e = spl::launch_fused_f64(insts, count, lp.total_tiles, reinterpret_cast<double *>(c->arena + d_ring_off),
                               lp.tile_rows, c->sm_count, counters, st);

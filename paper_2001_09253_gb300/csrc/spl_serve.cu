@@ -50,7 +50,8 @@ int serve_tile_for(uint64_t n) {
 struct Req {
   int state = 0;  // 0 waiting on the host, 1 resident on the device, 2 done
   Inst inst{};
-  uint64_t ntiles = 0, bytes = 0, first_tile = 0;
+  uint64_t ntiles = 0, bytes = 0, first_tile = 0;  // ntiles: tile tickets (twice the tiles when refined)
+  uint64_t z_off = 0, z_bytes = 0;                 // refinement: binary32 y'' in the context's arena
   unsigned slot = 0, seq = 0;
   double t_submit = 0, t_done = 0;
   int status = SPL_PENDING;
@@ -89,6 +90,12 @@ struct spl_server {
 
 namespace {
 
+// The request is finished with the device: its refinement buffer goes back to the arena.
+void release_z(spl_server *s, Req &r) {
+  if (r.z_bytes) spl_ctx_arena_release(s->ctx, r.z_off, r.z_bytes);
+  r.z_bytes = 0;
+}
+
 spl_status relaunch(spl_server *s) {
   cudaError_t e = cudaSuccess;
   // tickets claimed past the last published tile by the previous loop are void
@@ -125,6 +132,7 @@ spl_status after_exit(spl_server *s) {
     r.status = SPL_ERR_TIMEOUT;
     r.state = 2;
     r.t_done = t;
+    release_z(s, r);
     s->slot_ticket[slot] = 0;
     s->free_slots.push_back(slot);
     s->bytes_inflight -= r.bytes;
@@ -175,6 +183,7 @@ spl_status pump(spl_server *s) {
                                                 : SPL_OK;
     r.state = 2;
     r.t_done = t;
+    release_z(s, r);
     s->slot_ticket[slot] = 0;
     s->free_slots.push_back(slot);
     s->bytes_inflight -= r.bytes;
@@ -190,6 +199,14 @@ spl_status pump(spl_server *s) {
                       s->next_tile + r.ntiles - oldest <= s->args.tile_cap &&
                       s->tail - *s->h_consumed < s->args.rcap;
     if (!fits) break;
+    if (r.inst.pad & spl::kServeRefined) {  // the first pass's binary32 y'', from the arena
+      uint64_t off = 0;
+      const uint64_t zb = (4ull * (uint64_t)r.inst.n + 255) / 256 * 256;
+      if (!spl_ctx_arena_alloc(s->ctx, zb, &off)) break;  // waits for a completion to free memory
+      r.z_off = off;
+      r.z_bytes = zb;
+      r.inst.z = reinterpret_cast<float *>(spl_ctx_arena_base(s->ctx) + off);
+    }
     s->waiting.pop_front();
     r.slot = s->free_slots.back();
     s->free_slots.pop_back();
@@ -232,6 +249,7 @@ spl_status spl_serve_create(spl_ctx *c, const spl_serve_desc *d, spl_server **ou
   *out = nullptr;
   if (d->max_inflight < 1 || d->max_inflight > 65536) return SPL_ERR_INVALID_ARG;
   if (d->tile_rows != 0 && d->tile_rows < 16) return SPL_ERR_INVALID_ARG;
+  if (d->refine_steps > 1) return SPL_ERR_INVALID_ARG;
   std::unique_ptr<spl_server> s(new (std::nothrow) spl_server());
   if (!s) return SPL_ERR_CUDA;
   s->ctx = c;
@@ -334,6 +352,11 @@ spl_status spl_serve_submit(spl_server *s, const spl_request *r, uint64_t *ticke
   I.tile_begin = 0;
   q.ntiles = (uint64_t)I.ntiles;
   q.bytes = 16 * r->n + (r->ypp_out ? 8 * r->n : 0) + 8 * r->m + (r->jq_out ? 4 * r->m : 0);
+  if (s->d.refine_steps) {  // two passes over the tiles, binary32 y'' of the first in between
+    I.pad |= spl::kServeRefined;
+    q.ntiles *= 2;
+    q.bytes += 4 * r->n;
+  }
   if (q.bytes > s->d.budget_bytes || q.ntiles > s->args.tile_cap) return SPL_ERR_BUDGET;
   std::lock_guard<std::mutex> lk(s->mu);
   if (cudaSetDevice(s->device) != cudaSuccess) return SPL_ERR_CUDA;
@@ -442,6 +465,7 @@ void spl_serve_destroy(spl_server *s) {
   while (s->launched && cudaEventQuery(s->ev_exit) == cudaErrorNotReady && now_s() - t0 < 40.0)
     std::this_thread::sleep_for(std::chrono::microseconds(100));
   cudaStreamSynchronize(s->stream);
+  for (auto &kv : s->reqs) release_z(s, kv.second);
   release_server(s);
   delete s;
 }

@@ -59,7 +59,7 @@ class Request(ctypes.Structure):
 class ServeDesc(ctypes.Structure):
     _fields_ = [("max_inflight", ctypes.c_uint32), ("tile_rows", ctypes.c_uint32), ("budget_bytes", ctypes.c_uint64),
                 ("max_tiles", ctypes.c_uint64), ("idle_timeout_ms", ctypes.c_uint32), ("deadline_ms", ctypes.c_uint32),
-                ("fault_flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("fault_flags", ctypes.c_uint32), ("refine_steps", ctypes.c_uint32)]
 
 
 class Result(ctypes.Structure):
@@ -316,11 +316,12 @@ class Server:
     """Continuous-batching server on a persistent device loop (spl_serve_*)."""
 
     def __init__(self, ctx: Context, max_inflight: int = 1024, tile_rows: int = 0, budget_bytes: int = 1 << 34,
-                 max_tiles: int = 0, idle_timeout_ms: int = 0, deadline_ms: int = 0, fault_flags: int = 0):
+                 max_tiles: int = 0, idle_timeout_ms: int = 0, deadline_ms: int = 0, fault_flags: int = 0,
+                 refine_steps: int = 0):
         self.ctx, self.lib = ctx, ctx.lib
         d = ServeDesc(max_inflight=int(max_inflight), tile_rows=int(tile_rows), budget_bytes=int(budget_bytes),
                       max_tiles=int(max_tiles), idle_timeout_ms=int(idle_timeout_ms), deadline_ms=int(deadline_ms),
-                      fault_flags=int(fault_flags), reserved=0)
+                      fault_flags=int(fault_flags), refine_steps=int(refine_steps))
         h = ctypes.c_void_p()
         _check(self.lib.spl_serve_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)), "spl_serve_create")
         self.handle = h

@@ -196,7 +196,7 @@ def test_explicit_errors(ctx):
     x, y = synth.curve(24, 500)
     xt, yt = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
     # unknown modes and variants are refused
-    for kw in ({"query_mode": 2}, {"eval_variant": 3}, {"eval_variant": -1}):
+    for kw in ({"query_mode": 2}, {"eval_variant": 4}, {"eval_variant": -1}):
         with pytest.raises(spl.SplError) as ei:
             ctx.plan(500, **kw)
         assert ei.value.status == spl.ERR_INVALID_ARG
@@ -313,3 +313,33 @@ def test_uniform_grid_batch_from_stored_fits(ctx, precision):
         assert np.array_equal(j, ref["jq"]), np.nonzero(j != ref["jq"])[0][:10]
         e = yq_error(x, y, ref["ypp"], ref["jq"], yq.cpu().numpy()[:m], ref["yq"])
         assert e <= tol, "S(x) error %.3e (n = %d, m = %d)" % (e, len(x), m)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_noop_control_brackets_only(ctx, precision, mode):
+    """The paper's control loop (query generation and bracketing, no evaluation): brackets equal
+    the oracle's, and the value written is the bracket's left knot; uniform and explicit queries,
+    both precisions."""
+    import torch
+    from paper_2001_09253_gb300 import spl
+    dev = torch.device("cuda", ctx.device)
+    x, y = synth.curve(25, 3001)
+    ref = oracle.fit_eval(x, y, NAT, NAT, 3001)
+    xt, yt = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
+    ypp = torch.from_numpy(ref["ypp"]).to(dev)
+    if mode == spl.QUERY_EXPLICIT:
+        q = np.random.default_rng(3).uniform(x[0] - 1.0, x[-1] + 1.0, 4000)
+        xq = torch.from_numpy(q).to(dev)
+        jref = oracle.bracket_any(x, q)
+    else:
+        q, xq, jref = None, None, ref["jq"]
+    m = len(jref)
+    plan = ctx.plan(3001, precision, query_mode=mode, eval_variant=spl.EVAL_NOOP)
+    yq = torch.full((m,), np.nan, dtype=torch.float64, device=dev)
+    jq = torch.full((m,), -1, dtype=torch.int32, device=dev)
+    st, _ = ctx.wait(ctx.submit(plan, xt, yt, NAT, NAT, m, None, yq, jq, xq=xq, ypp_in=ypp), 60.0)
+    assert st == spl.OK
+    j = jq.cpu().numpy().astype(np.int64)
+    assert np.array_equal(j, jref)
+    assert np.array_equal(yq.cpu().numpy(), x[jref])

@@ -198,3 +198,52 @@ def test_full_size_n1e7(ctx):
     assert ypp_error(ypp.cpu().numpy(), ref["ypp"]) <= TOL_F64
     assert np.array_equal(jq.cpu().numpy().astype(np.int64), ref["jq"])
     assert yq_error(hx, hy, ref["ypp"], ref["jq"], yq.cpu().numpy(), ref["yq"]) <= TOL_F64
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 127, 128, 129, 255, 256, 257, 1000, 2047, 4095, 4096, 4097])
+def test_small_instances_one_cta(ctx, n):
+    """Automatic tiling sends single FP64 instances of up to 4,096 knots to the one-CTA latency
+    kernel (pieces of ceil(n / 128) rows, block scans of the d' and y'' maps); 4,097 takes the
+    tiled kernel.  Every end-condition pair, query counts below, at and above n."""
+    x, y = synth.curve(4000 + n, n)
+    plan = _plan(ctx, 0)
+    for bc in ((NAT, NAT), (-1.0, 1.0), (NAT, 2.0), (-3.0, NAT)):
+        for m in sorted({0, 1, 2, n, 2 * n + 1}):
+            check_instance(ctx, plan, x, y, bc[0], bc[1], m)
+
+
+def test_small_instances_adversarial_and_far_knots(ctx):
+    """The one-CTA kernel on 8-decade gaps and on knots near 5e6 with small gaps."""
+    x, y = synth.curve_adversarial(7, 3000, decades=8)
+    check_instance(ctx, _plan(ctx, 0), x, y, NAT, NAT, 4001)
+    check_instance(ctx, _plan(ctx, 0), x, y, 0.5, -2.0, 2999)
+    x, y = synth.curve(8, 2500)
+    check_instance(ctx, _plan(ctx, 0), x + 5.0e6, y, -1.0, 1.0, 2500)
+
+
+def test_small_instances_batched_and_errors(ctx):
+    """Several small FP64 instances in one launch (one CTA each) with one bad instance."""
+    import torch
+    plan = _plan(ctx, 0)
+    sizes = [3, 1000, 17, 4096, 640]
+    reqs, keep, refs = [], [], []
+    for i, n in enumerate(sizes):
+        x, y = synth.curve(50 + i, n)
+        if i == 2:
+            x = x.copy()
+            x[5] = x[4]
+        xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+        ypp = torch.empty(n, dtype=torch.float64, device="cuda")
+        yq = torch.empty(n + 3, dtype=torch.float64, device="cuda")
+        reqs.append(spl.make_request(xt, yt, NAT, NAT, n + 3, ypp, yq))
+        keep.append((xt, yt, ypp, yq))
+        refs.append((x, y))
+    for i, (t, (x, y), k) in enumerate(zip(ctx.submit_batch(plan, reqs, keep), refs, keep)):
+        st, _ = ctx.wait(t)
+        if i == 2:
+            assert st == spl.ERR_NOT_INCREASING
+            continue
+        assert st == 0
+        ref = oracle.fit_eval(x, y, NAT, NAT, len(x) + 3)
+        assert ypp_error(k[2].cpu().numpy(), ref["ypp"]) <= TOL_F64
+        assert yq_error(x, y, ref["ypp"], ref["jq"], k[3].cpu().numpy(), ref["yq"]) <= TOL_F64

@@ -204,3 +204,43 @@ def test_trace_replay(ctx):
     assert np.all(lat > 0) and np.all(np.isfinite(lat))
     assert makespan >= arrivals[-1]
     srv.close()
+
+
+@pytest.mark.parametrize("tile", [TILE, 0])
+def test_refined_serving_alone_and_in_the_mix(ctx, tile):
+    """Served with one refinement step (two passes over each request's tiles, the second once
+    the first is complete): y'' within the refined tolerance of the oracle, S(x_k) within the
+    mixed one, and each result the same alone and in the mix, bit for bit."""
+    import torch
+    pool = _pool(24, 9)
+    refs = []
+    for p in pool:  # alone: a server with nothing else in flight
+        srv = spl.Server(ctx, max_inflight=1, tile_rows=tile, idle_timeout_ms=20, refine_steps=1)
+        ypp, yq = _outputs(p)
+        s, _ = srv.wait(srv.submit(p["xt"], p["yt"], p["bc"][0], p["bc"][1], p["m"], ypp, yq))
+        srv.close()
+        assert s == spl.OK
+        refs.append((ypp.cpu().numpy(), yq.cpu().numpy()))
+    srv = spl.Server(ctx, max_inflight=64, tile_rows=tile, budget_bytes=1 << 34, refine_steps=1)
+    outs, tickets = [], []
+    for p in pool:
+        o = _outputs(p)
+        outs.append(o)
+        tickets.append(srv.submit(p["xt"], p["yt"], p["bc"][0], p["bc"][1], p["m"], o[0], o[1]))
+    for t in tickets:
+        s, _ = srv.wait(t)
+        assert s == spl.OK
+    torch.cuda.synchronize()
+    srv.close()
+    for o, ref in zip(outs, refs):
+        assert np.array_equal(o[0].cpu().numpy(), ref[0]) and np.array_equal(o[1].cpu().numpy(), ref[1])
+    for o, p in zip(outs, pool):
+        r = oracle.fit_eval(p["x"], p["y"], p["bc"][0], p["bc"][1], p["m"])
+        assert ypp_error(o[0].cpu().numpy(), r["ypp"]) <= 1e-8
+        assert yq_error(p["x"], p["y"], r["ypp"], r["jq"], o[1].cpu().numpy(), r["yq"]) <= TOL_MIXED
+
+
+def test_refined_serving_rejects_bad_option(ctx):
+    with pytest.raises(spl.SplError) as ei:
+        spl.Server(ctx, max_inflight=4, refine_steps=2)
+    assert ei.value.status == spl.ERR_INVALID_ARG
