@@ -367,7 +367,10 @@ __device__ void scan_tile(const Inst &I, long long tile, ScanSmem &S, int lane) 
     }
     float4 *ws = S.w + st * kStepS;
     const bool edge = R == 0 || R + kStepS > f1 || R + kStepS + 1 > n;
-    if (edge) fwd_step<kMode, true>(I, E, R, f1, lane, xv, yv, zv, C, ws, bad);
+    // the refinement pass keeps one copy of its (long, double-float) step, with the edge checks:
+    // two copies overflowed the instruction cache when warps sat in different phases (batched
+    // launches: "no instruction" stalls 12 per issue)
+    if (kMode == 2 || edge) fwd_step<kMode, true>(I, E, R, f1, lane, xv, yv, zv, C, ws, bad);
     else fwd_step<kMode, false>(I, E, R, f1, lane, xv, yv, zv, C, ws, bad);
   }
   __syncwarp();
@@ -590,6 +593,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) serve_kernel(ServeArgs a) {
 
   if (scheduler && (a.fault_flags & 1u)) return;  // failure-detection tests: no work is published
   if (scheduler) {
+    ScanSmem &S0 = reinterpret_cast<ScanSmem *>(smem_raw)[0];  // this warp's slot (never a worker's)
     unsigned long long consumed = *a.consumed;
     unsigned long long last_work = t_start;
     unsigned sleep_ns = 64;
@@ -597,36 +601,50 @@ __global__ void __launch_bounds__(kThreadsS, 1) serve_kernel(ServeArgs a) {
     for (;;) {
       const unsigned long long tail = *a.h_tail;
       if (consumed < tail) {
-        __threadfence_system();  // the entry was written before the tail: read it after
-        const ServeEntry *e = a.h_ring + (consumed % a.rcap);
-        // one 8-byte word of the entry per lane from mapped host memory, shared by shuffles
+        __threadfence_system();  // the entries were written before the tail: read them after
+        // up to kRingBatch entries per round trip to mapped host memory: every 8-byte word of the
+        // batch is loaded at once (lane l: words l, l + 32, ...) into this warp's shared memory,
+        // which no worker uses, then the entries are installed one by one
         constexpr int kWords = (int)(sizeof(ServeEntry) / 8);
-        static_assert(kWords <= 32, "a serving entry must fit in one warp's loads");
-        const volatile unsigned long long *src = reinterpret_cast<const volatile unsigned long long *>(e);
-        const unsigned long long word = (lane < kWords) ? src[lane] : 0ull;
-        ServeEntry ent;
-        unsigned long long *dst = reinterpret_cast<unsigned long long *>(&ent);
-        for (int w = 0; w < kWords; ++w) dst[w] = __shfl_sync(0xffffffffu, word, w);
-        const unsigned slot = ent.slot;
-        if (lane == 0) {
-          ent.inst.status = a.slot_status + slot;
-          a.slot_inst[slot] = ent.inst;
-          a.slot_first[slot] = ent.first_tile;
-          a.slot_done[slot] = 0u;
-          a.slot_status[slot] = 0u;
-          a.slot_seq[slot] = ent.seq;
+        constexpr int kRingBatch = 16;
+        static_assert(kRingBatch * kWords * 8 <= (int)sizeof(((ScanSmem *)0)->w), "ring batch fits the warp's buffer");
+        unsigned long long *buf = reinterpret_cast<unsigned long long *>(S0.w);
+        const int avail = (int)min(tail - consumed, (unsigned long long)kRingBatch);
+        const int total = avail * kWords;
+#pragma unroll 4
+        for (int idx = lane; idx < total; idx += 32) {
+          const int e = idx / kWords, w = idx - e * kWords;
+          const volatile unsigned long long *src =
+              reinterpret_cast<const volatile unsigned long long *>(a.h_ring + ((consumed + e) % a.rcap));
+          buf[idx] = src[w];
         }
-        const unsigned long long nt = serve_tickets(ent.inst);
-        for (unsigned long long i = lane; i < nt; i += 32) a.tile_slot[(ent.first_tile + i) % a.tile_cap] = slot;
-        __threadfence();
         __syncwarp();
-        if (lane == 0) *published = ent.first_tile + nt;
-        ++consumed;
+        for (int e = 0; e < avail; ++e) {
+          ServeEntry ent;
+          unsigned long long *dst = reinterpret_cast<unsigned long long *>(&ent);
+          for (int w = 0; w < kWords; ++w) dst[w] = buf[e * kWords + w];
+          const unsigned slot = ent.slot;
+          if (lane == 0) {
+            ent.inst.status = a.slot_status + slot;
+            a.slot_inst[slot] = ent.inst;
+            a.slot_first[slot] = ent.first_tile;
+            a.slot_done[slot] = 0u;
+            a.slot_status[slot] = 0u;
+            a.slot_seq[slot] = ent.seq;
+          }
+          const unsigned long long nt = serve_tickets(ent.inst);
+          for (unsigned long long i = lane; i < nt; i += 32) a.tile_slot[(ent.first_tile + i) % a.tile_cap] = slot;
+          __threadfence();
+          __syncwarp();
+          if (lane == 0) *published = ent.first_tile + nt;
+        }
+        consumed += (unsigned long long)avail;
         if (lane == 0) {
           *a.consumed = consumed;
           *a.h_consumed = consumed;
           __threadfence_system();
         }
+        __syncwarp();
         last_work = globaltimer_ns();
         sleep_ns = 64;
         continue;
