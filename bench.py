@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--only", default="", choices=["", "f64", "mixed", "mixed-refine", "batched", "variants",
-                                                   "schedule"],
+                                                   "schedule", "n1000", "noalloc"],
                     help="time one path only and print a short line (profiling runs)")
     ap.add_argument("--n", type=int, default=N_POINTS, help="knots = queries per instance (profiling runs)")
     ap.add_argument("--no-serving", action="store_true",
@@ -464,6 +464,34 @@ class Runner:
         return {"workload": "n = M = 1000, seed 0, natural and clamped (-1, 1) ends, one request at a time",
                 "requests_per_case": reps, **out}, (hx, hy)
 
+    def noalloc(self, sizes=(100_000, 1_000_000), reps=20):
+        """spl_fit_eval_noalloc (binary32 + one refinement step, fixed scratch inside the library,
+        no allocation) beside spl_submit with the same precision, one instance of n = M at a
+        time; device time from CUDA events around each call."""
+        torch, spl = self.torch, self.spl
+        out = {}
+        for n in sizes:
+            x, y = self.x[:n].contiguous(), self.y[:n].contiguous()
+            ypp = torch.empty(n, dtype=torch.float64, device=self.dev)
+            yq = torch.empty(n, dtype=torch.float64, device=self.dev)
+            plan = self.ctx.plan(n, spl.PREC_F32_REFINE, refine_steps=1)
+            t_na, t_sub = [], []
+            for r in range(self.W + reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(self.stream)
+                s, _ = spl.fit_eval_noalloc(x, y, spl.NATURAL, spl.NATURAL, n, ypp, yq, stream=self.stream,
+                                            want_status=False)
+                e1.record(self.stream)
+                assert s == spl.OK
+                e1.synchronize()
+                ms = self._timed_submit(plan, n, yq, x=x, y=y, ypp_out=ypp)
+                if r >= self.W:
+                    t_na.append(e0.elapsed_time(e1))
+                    t_sub.append(ms)
+            out["n=%d" % n] = {"noalloc_ms": dist_summary(t_na), "submit_ms": dist_summary(t_sub)}
+        return {"workload": "one instance of the n = 1e7 curve's first n points, M = n, binary32 + one refinement "
+                            "step: spl_fit_eval_noalloc (ring kernels, fixed scratch) and spl_submit", **out}
+
     def eval_variants(self, reps=None):
         """The three forms of section "Fast Interpolation" that the paper benchmarks (orig: one
         reciprocal then a multiply; noinv: a division at the end; vol: orig with the reciprocal
@@ -700,8 +728,9 @@ def run_ours(args, world, rank, local):
     r = Runner(args, world, rank, local)
     spl = r.spl
     if args.only:
-        if args.only in ("variants", "schedule"):
-            res = r.eval_variants()[0] if args.only == "variants" else r.n_schedule()
+        if args.only in ("variants", "schedule", "n1000", "noalloc"):
+            res = (r.eval_variants()[0] if args.only == "variants" else r.n_schedule() if args.only == "schedule"
+                   else r.config1()[0] if args.only == "n1000" else r.noalloc())
             if rank == 0:
                 print(json.dumps({"profile_run": True, "path": args.only, "result": res}))
             r.ctx.close()
@@ -729,6 +758,7 @@ def run_ours(args, world, rank, local):
     variants, vdata = r.eval_variants()
     schedule = r.n_schedule()
     small, c1data = r.config1()
+    noalloc = r.noalloc()
     if rank != 0:
         r.ctx.close()
         return
@@ -753,6 +783,7 @@ def run_ours(args, world, rank, local):
         "n_schedule": schedule,
         "newint_variants": variants,
         "n1000": small,
+        "noalloc": noalloc,
         "mixed_f32": path_entry(mixed0, "n=M=1e7 seed 1, binary32 solve + cubic, exact binary64 differences "
                                         "and query positions, no refinement", TOL["mixed"], "f32"),
         "mixed_f32_refine1": path_entry(mixed1, "same, plus one refinement step of y'' against a double-float "
@@ -921,6 +952,9 @@ def summary(line):
                         "wall_p50_ms": g(c1, k, "wall_ms", "median"), "wall_p99_ms": g(c1, k, "wall_ms", "p99")}
                     for k in ("f64/natural", "mixed_refine1/natural")}
     out["n1000"]["oracle_us_1core"] = g(c1, "cpu_baseline", "us_per_instance")
+    na = oc.get("noalloc") or {}
+    out["noalloc_p50_ms"] = {k: {"noalloc": g(na, k, "noalloc_ms", "median"), "submit": g(na, k, "submit_ms", "median")}
+                             for k in ("n=100000", "n=1000000")}
     v = oc.get("newint_variants") or {}
     out["eval_1e7_ms"] = {lab: {nm: g(v, lab, nm, "ms", "median") for nm in ("orig", "noinv", "vol", "noop")}
                           for lab in ("sorted", "unsorted")}

@@ -19,13 +19,14 @@ def bench():
 
 def test_committed_profiles_carry_hash_and_traffic(bench):
     """Every committed summary names the source hash it was taken on and the DRAM bytes of one
-    full-size launch (at least the algorithmic 32 B x 1e7 points)."""
+    full-size launch: at least the algorithmic reads (16 B x 1e7 points); up to the L2's 129 MB of
+    the 16 B x 1e7 output bytes can still sit in L2 when the kernel ends and go uncounted."""
     import re
     for which, (path, files) in bench.PROFILES.items():
         text = open(path).read()
         assert re.search(r"kernel_source_hash:\s*[0-9a-f]{16}", text), which
         m = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
-        assert m and float(m.group(1)) >= 3.2e8, which
+        assert m and float(m.group(1)) >= 1.6e8, which
 
 
 def _stamped(bench, which, tmp_path, name):
