@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
-    ap.add_argument("--only", default="", choices=["", "f64", "mixed", "mixed-refine", "batched", "variants",
+    ap.add_argument("--only", default="", choices=["", "f64", "mixed", "mixed-refine", "batched", "variants", "dfma",
                                                    "schedule", "n1000", "noalloc"],
                     help="time one path only and print a short line (profiling runs)")
     ap.add_argument("--n", type=int, default=N_POINTS, help="knots = queries per instance (profiling runs)")
@@ -492,6 +492,30 @@ class Runner:
         return {"workload": "one instance of the n = 1e7 curve's first n points, M = n, binary32 + one refinement "
                             "step: spl_fit_eval_noalloc (ring kernels, fixed scratch) and spl_submit", **out}
 
+    def dfma_probe(self, warps_per_sm=8, trips=6000, reps=5, clock_mhz=None):
+        """The FP64 pipe's rate on a pure DFMA stream (spl_selftest_dfma: one CTA of `warps_per_sm`
+        warps per SM, four independent chains per thread), timed with CUDA events: the measured
+        ceiling beside the unit-count peak of the FP64 roofline.  lanes/clk/SM uses the SM clock
+        sampled during the main timed region (the maximum clock when none was sampled)."""
+        torch, spl = self.torch, self.spl
+        sms = torch.cuda.get_device_properties(self.dev).multi_processor_count
+        sink = torch.empty(sms * warps_per_sm * 32, dtype=torch.float64, device=self.dev)
+        times, ops = [], 0
+        for r in range(self.W + reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            ops = spl.selftest_dfma(trips, warps_per_sm, sink, stream=self.stream)
+            e1.record(self.stream)
+            e1.synchronize()
+            if r >= self.W:
+                times.append(e0.elapsed_time(e1))
+        ms = float(np.median(times))
+        rate = ops / (ms * 1e-3)
+        mhz = clock_mhz or 2070.0
+        return {"lane_ops_per_s_T": rate / 1e12, "lanes_per_clk_per_sm": rate / (sms * mhz * 1e6),
+                "clock_mhz": mhz, "ms": ms, "lane_ops": ops, "warps_per_sm": warps_per_sm,
+                "what": "DFMA lane operations per second, %d SMs x %d warps x 4 independent chains" % (sms, warps_per_sm)}
+
     def eval_variants(self, reps=None):
         """The three forms of section "Fast Interpolation" that the paper benchmarks (orig: one
         reciprocal then a multiply; noinv: a division at the end; vol: orig with the reciprocal
@@ -728,9 +752,10 @@ def run_ours(args, world, rank, local):
     r = Runner(args, world, rank, local)
     spl = r.spl
     if args.only:
-        if args.only in ("variants", "schedule", "n1000", "noalloc"):
+        if args.only in ("variants", "schedule", "n1000", "noalloc", "dfma"):
             res = (r.eval_variants()[0] if args.only == "variants" else r.n_schedule() if args.only == "schedule"
-                   else r.config1()[0] if args.only == "n1000" else r.noalloc())
+                   else r.config1()[0] if args.only == "n1000" else r.dfma_probe() if args.only == "dfma"
+                   else r.noalloc())
             if rank == 0:
                 print(json.dumps({"profile_run": True, "path": args.only, "result": res}))
             r.ctx.close()
@@ -759,6 +784,7 @@ def run_ours(args, world, rank, local):
     schedule = r.n_schedule()
     small, c1data = r.config1()
     noalloc = r.noalloc()
+    dfma = r.dfma_probe(clock_mhz=(main.get("clocks") or {}).get("sm_mhz"))
     if rank != 0:
         r.ctx.close()
         return
@@ -831,6 +857,8 @@ def run_ours(args, world, rank, local):
                               "peak = 2 FP64 ops/clk/SM x 152 SMs x 2.07 GHz (one op per lane per clock)"
                               % FLOPS_PER_POINT),
                      "frac_of_fma_counted_peak": achieved / PEAK_FP64_TFLOPS,
+                     "dfma_stream_measured": dfma,
+                     "frac_of_dfma_stream": achieved / dfma["lane_ops_per_s_T"],
                      "fp64_pipe_active_ncu": profiled_fraction("f64", "fp64_pipe_active_pct"),
                      "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / hbm if hbm else None},
         "cpu_baseline": cpu,
@@ -923,7 +951,9 @@ def summary(line):
 
     oc = line.get("other_configs", {})
     out = {"f64_1e7": {"ms": g(line, "ms_per_step"), "inst_s": g(line, "value"),
-                       "alu_frac": g(line, "roofline", "frac"), "e2e_inst_s": g(line, "e2e", "value"),
+                       "alu_frac": g(line, "roofline", "frac"),
+                       "frac_of_dfma_stream": g(line, "roofline", "frac_of_dfma_stream"),
+                       "e2e_inst_s": g(line, "e2e", "value"),
                        "err_ypp": g(line, "error_vs_oracle", "ypp"), "err_yq": g(line, "error_vs_oracle", "yq"),
                        "oracle_inst_s_1core": g(line, "cpu_baseline", "value")}}
     for key, name in (("mixed_f32", "mixed_1e7"), ("mixed_f32_refine1", "mixed_refine1_1e7")):

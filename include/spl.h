@@ -346,6 +346,19 @@ void spl_serve_destroy(spl_server *srv);
 spl_status spl_selftest_div64(const double *num, const double *den, uint64_t count, double *q_fast, double *r_fast,
                               double *q_ieee, double *r_ieee, void *stream);
 
+/* Probe of the FP64 pipe's rate (no counterpart in the paper: it measures the ceiling of the
+ * SPL_PREC_F64 kernel, whose time is set by its FP64 instructions).  Launches one CTA of
+ * warps_per_sm warps on every SM of the current device; each thread runs 4 independent
+ * recurrences a <- fma(a, mul, add) for trips x 16 steps and writes the sum of its four values to
+ * sink[thread] (sink: caller-owned device array of at least sink_count >= SMs x warps_per_sm x 32
+ * doubles).  *lane_ops (host, may be NULL) receives the number of DFMA lane operations the launch
+ * performs; the caller times the launch on `stream` (NULL = legacy default stream) and divides.
+ * With |mul| < 1 the values converge to add / (1 - mul).  SPL_ERR_INVALID_ARG for warps_per_sm
+ * outside 1..32, trips above 2^40, or a missing or short sink; SPL_ERR_CUDA when the launch
+ * fails. */
+spl_status spl_selftest_dfma(uint64_t trips, int32_t warps_per_sm, double mul, double add, double *sink,
+                             uint64_t sink_count, uint64_t *lane_ops, void *stream);
+
 /* One instance without any allocation, for callers that cannot allocate device memory:
  * host applications that own all of the GPU's memory themselves (a simulation or game
  * engine, a database or plug-in host that hands out fixed pools), and code under a hard

@@ -52,6 +52,9 @@ __device__ __forceinline__ F2 dif2(double b, double a) {
   if (diff_f2(b, a, &v)) return v;
   return sub_f64_f2(b, a);
 }
+// the same out of line: the fallback of the same-binade and in-range routes, rare, kept out of
+// the refinement's unrolled rows (instruction-cache footprint)
+static __device__ __noinline__ F2 dif2_slow(double b, double a) { return dif2(b, a); }
 
 __device__ __forceinline__ float to_f32(double d) {
   const uint64_t u = bits64(d);

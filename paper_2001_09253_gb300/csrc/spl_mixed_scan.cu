@@ -164,14 +164,18 @@ __device__ __forceinline__ void fwd_step(const Inst &I, const EndsS &E, long lon
       if (kMode == 2) {
         // exact widths as double-floats (same binade: the integer ulp count), value differences
         // as the binary64 difference split in two (the rounding the binary64 slopes see too)
-        if (!diff_up_f2(xv[v + 1], xv[v], &h[v])) h[v] = dif2(xv[v + 1], xv[v]);
+        if (!diff_up_f2(xv[v + 1], xv[v], &h[v])) h[v] = dif2_slow(xv[v + 1], xv[v]);
         F2 dy;
-        if (!f64_to_f2(yv[v + 1] - yv[v], &dy)) dy = dif2(yv[v + 1], yv[v]);
+        if (!f64_to_f2(yv[v + 1] - yv[v], &dy)) dy = dif2_slow(yv[v + 1], yv[v]);
         s[v] = df_div(dy, h[v], rcp32(h[v].hi));
       } else {
         h[v].hi = dif32_up(xv[v + 1], xv[v]);
         s[v].hi = quot32(dy32(yv[v + 1], yv[v]), h[v].hi, rcp32(h[v].hi));
       }
+    } else if (kEdge && j == n - 1 && !nat1) {
+      // clamped last row: the interior row with a zero width above and the end slope in place
+      // of the slope above (a = h_{n-2}, b = 2 h_{n-2}, c = 0, d = 6 (y'_n - s_{n-2}))
+      s[v] = kMode == 2 ? E.ypnF : F2{E.ypn, 0.0f};
     }
     if (kMode != 2 && (!kEdge || j < f1)) bad |= row_check(xv[v], yv[v], hasn, xv[v + 1]);
   }
@@ -206,46 +210,14 @@ __device__ __forceinline__ void fwd_step(const Inst &I, const EndsS &E, long lon
       d[v] = 6.0f * (s[v].hi - sp.hi);
     }
     if (kEdge) {
+      // identity rows: natural ends (y'' = 0: the refinement's correction is -Z there) and the
+      // rows past the sweep; the clamped end rows are general rows (see above and the carry)
       const long long j = j0 + v;
-      if (j == 0) {
-        a[v] = 0.0f;
-        if (nat0) {
-          b[v] = 1.0f;
-          c[v] = 0.0f;
-          d[v] = kMode == 2 ? -zv[v] : 0.0f;  // natural first row: y''_0 = 0
-        } else {
-          b[v] = 2.0f * h[v].hi;
-          if (kMode == 2) {
-            const F2 dd = df_mul_f(df_add(s[v], df_neg(E.yp1F)), 6.0f);
-            const F2 res = df_add(dd, df_neg(df_add(df_mul_f(h[v], 2.0f * zv[v]), df_mul_f(h[v], zv[v + 1]))));
-            d[v] = res.hi + res.lo;
-          } else {
-            d[v] = 6.0f * (s[v].hi - E.yp1);
-          }
-        }
-      } else if (j == n - 1) {
-        c[v] = 0.0f;
-        if (nat1) {
-          a[v] = 0.0f;
-          b[v] = 1.0f;
-          d[v] = kMode == 2 ? -zv[v] : 0.0f;  // y''_{n-1} = 0
-        } else {
-          b[v] = 2.0f * hp.hi;
-          if (kMode == 2) {
-            const float zp = v ? zv[v - 1] : zm;
-            const F2 dd = df_mul_f(df_add(E.ypnF, df_neg(sp)), 6.0f);
-            const F2 res = df_add(dd, df_neg(df_add(df_mul_f(hp, zp), df_mul_f(hp, 2.0f * zv[v]))));
-            d[v] = res.hi + res.lo;
-          } else {
-            d[v] = 6.0f * (E.ypn - sp.hi);
-          }
-        }
-      }
-      if (j >= f1) {  // past the sweep: identity rows
+      if (j >= f1 || (j == 0 && nat0) || (j == n - 1 && nat1)) {
         a[v] = 0.0f;
         b[v] = 1.0f;
         c[v] = 0.0f;
-        d[v] = 0.0f;
+        d[v] = (kMode == 2 && j < f1) ? -zv[v] : 0.0f;
       }
     }
   }
@@ -336,9 +308,13 @@ __device__ void scan_tile(const Inst &I, long long tile, ScanSmem &S, int lane) 
   E.ypnF = (kMode == 2 && !E.nat1) ? f2_of(I.ypn) : F2{0.0f, 0.0f};
 
   // ---- forward sweep, rows f0 .. f1-1, one step of 128 rows at a time; loads one step ahead ----
+  // The carry into row f0: zero width below row 0 and, for a clamped first row, the end slope in
+  // place of the slope below, which makes row 0 the general row a = 0, b = 2 h_0, c = h_0,
+  // d = 6 (s_0 - y'_1) (section "Start and End Derivatives").
   CarryS C;
   C.c = C.d = C.z = 0.0f;
   C.h = C.s = F2{0.0f, 0.0f};
+  if (f0 == 0 && !E.nat0) C.s = kMode == 2 ? E.yp1F : F2{E.yp1, 0.0f};
   double xn[kVS + 1], yn[kVS + 1];
   float zn[kVS + 1];
   {
@@ -494,43 +470,32 @@ __device__ void scan_tile(const Inst &I, long long tile, ScanSmem &S, int lane) 
       const int imin = (int)(ilo - R), imax = (int)(ihi - R) - 1;
       const float4 *wst = S.w + st * kStepS;
       const float4 *wup = wst + kStepS;  // row R + 128 (the step above): right end of interval R + 127
-      // two independent queries per lane and round (k and k + 32), every lane through every
-      // shuffle; stores only for k < khi
-      for (long long kb = kb0; kb < khi; kb += 64) {
-        long long kk[2], kq[2];
-        double q[2];
-        int L[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          kk[u] = kb + 32 * u + lane;
-          q[u] = G.at(min(kk[u], khi - 1));
-          kq[u] = dkey(q[u]);
-          L[u] = 0;
-        }
+      // one query per lane and round, every lane through every shuffle; stores only for k < khi.
+      // (Two queries per lane and round measured slower: the longer loop body costs more in
+      // instruction fetch, with warps in different phases, than the second chain hides.)
+      for (long long kb = kb0; kb < khi; kb += 32) {
+        const long long kk = kb + lane;
+        const double q = G.at(min(kk, khi - 1));
+        const long long kq = dkey(q);
         // interval: largest i in [imin, imax] with x_{R+i} < q; first the lane among the
         // lanes' first knots, then the row among that lane's four
+        int L = 0;
 #pragma unroll
         for (int stp = 16; stp >= 1; stp >>= 1) {
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const long long kc = shfl_i64(K0, L[u] + stp);
-            if (kc < kq[u]) L[u] += stp;
-          }
+          const long long kc = shfl_i64(K0, L + stp);
+          if (kc < kq) L += stp;
         }
+        int i = 4 * L;
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          int i = 4 * L[u];
-#pragma unroll
-          for (int v = 1; v < kVS; ++v) i += (S.keys[v * 32 + L[u]] < kq[u]) ? 1 : 0;
-          i = max(min(i, imax), imin);
-          if (kk[u] < khi) {
-            const float4 wj = wst[wpos(i)];
-            const float4 wj1 = (i + 1 < kStepS) ? wst[wpos(i + 1)] : wup[0];
-            const double xj = key_to_double(S.keys[wpos(i)]);
-            const float xa = dif32_up(q[u], xj);
-            I.yq[kk[u]] = to_f64(newint32(xa, wj.z - xa, wj.w, wj1.w, wj.y, wj1.y, wj.z, wj.x));
-            if (I.jq) I.jq[kk[u]] = (int32_t)(R + i);
-          }
+        for (int v = 1; v < kVS; ++v) i += (S.keys[v * 32 + L] < kq) ? 1 : 0;
+        i = max(min(i, imax), imin);
+        if (kk < khi) {
+          const float4 wj = wst[wpos(i)];
+          const float4 wj1 = (i + 1 < kStepS) ? wst[wpos(i + 1)] : wup[0];
+          const double xj = key_to_double(S.keys[wpos(i)]);
+          const float xa = dif32_up(q, xj);
+          I.yq[kk] = to_f64(newint32(xa, wj.z - xa, wj.w, wj1.w, wj.y, wj1.y, wj.z, wj.x));
+          if (I.jq) I.jq[kk] = (int32_t)(R + i);
         }
       }
       khi = kb0;

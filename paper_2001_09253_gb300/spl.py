@@ -32,7 +32,7 @@ EXPORTS = [
     "spl_submit_batch", "spl_poll", "spl_wait", "spl_get_stats", "spl_batch_create", "spl_batch_launch",
     "spl_batch_wait", "spl_batch_destroy", "spl_generate_scratch_bytes", "spl_generate_curve",
     "spl_fit_eval_noalloc", "spl_serve_create", "spl_serve_submit", "spl_serve_poll", "spl_serve_wait",
-    "spl_serve_replay", "spl_serve_stats", "spl_serve_destroy", "spl_selftest_div64",
+    "spl_serve_replay", "spl_serve_stats", "spl_serve_destroy", "spl_selftest_div64", "spl_selftest_dfma",
 ]
 NOALLOC_MAX_N = 1048576
 
@@ -123,11 +123,12 @@ def load(path: str | None = None):
         L.spl_serve_destroy.argtypes = [vp]
         L.spl_serve_destroy.restype = None
         L.spl_selftest_div64.argtypes = [vp, vp, u64, vp, vp, vp, vp, vp]
+        L.spl_selftest_dfma.argtypes = [u64, i32, ctypes.c_double, ctypes.c_double, vp, u64, ctypes.POINTER(u64), vp]
         for name in ["spl_create", "spl_plan_create", "spl_submit", "spl_submit_batch", "spl_poll", "spl_wait",
                      "spl_get_stats", "spl_batch_create", "spl_batch_launch", "spl_batch_wait",
                      "spl_generate_curve", "spl_fit_eval_noalloc", "spl_serve_create", "spl_serve_submit",
                      "spl_serve_poll", "spl_serve_wait", "spl_serve_replay", "spl_serve_stats",
-                     "spl_selftest_div64"]:
+                     "spl_selftest_div64", "spl_selftest_dfma"]:
             getattr(L, name).restype = i32
         _lib = L
         return L
@@ -414,6 +415,18 @@ def selftest_div64(num, den, stream=None):
     _check(L.spl_selftest_div64(_ptr(num), _ptr(den), n, *[_ptr(o) for o in outs], st.cuda_stream),
            "spl_selftest_div64")
     return tuple(o[:n] for o in outs)
+
+
+def selftest_dfma(trips: int, warps_per_sm: int, sink, mul: float = 0.999999, add: float = 1e-6, stream=None):
+    """spl_selftest_dfma: enqueues the DFMA-stream probe on `stream` (sink: a float64 device tensor of
+    at least SMs x warps_per_sm x 32 elements) and returns the DFMA lane operations it performs."""
+    import torch
+    L = load()
+    ops = ctypes.c_uint64(0)
+    st = stream if stream is not None else torch.cuda.current_stream(sink.device)
+    _check(L.spl_selftest_dfma(int(trips), int(warps_per_sm), float(mul), float(add), _ptr(sink), int(sink.numel()),
+                               ctypes.byref(ops), st.cuda_stream), "spl_selftest_dfma")
+    return ops.value
 
 
 def generate_curve(seed: int, n: int, instance: int = 0, device: int = 0, stream=None):

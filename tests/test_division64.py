@@ -69,3 +69,21 @@ def test_quotients_bit_exact_and_reciprocals_faithful():
         assert int(d_ulp.max()) <= 1, name
         total += len(num)
     assert total >= 10_000_000
+
+
+@pytest.mark.gpu
+def test_dfma_probe_counts_and_converges():
+    """spl_selftest_dfma: the lane-operation count it reports is SMs x warps x 32 threads x trips x
+    16 steps x 4 chains, and every chain of a <- a/2 + 1/2 reaches the fixed point 1 exactly (the
+    sum of a thread's four chains is 4); a sink shorter than one value per thread is refused."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sink = torch.full((sms * 4 * 32,), float("nan"), dtype=torch.float64, device="cuda")
+    ops = spl.selftest_dfma(100, 4, sink, mul=0.5, add=0.5)
+    torch.cuda.synchronize()
+    assert ops == sms * 4 * 32 * 100 * 16 * 4
+    assert bool((sink == 4.0).all())
+    with pytest.raises(spl.SplError):
+        spl.selftest_dfma(1, 4, sink[:100])
+    with pytest.raises(spl.SplError):
+        spl.selftest_dfma(1, 0, sink)
