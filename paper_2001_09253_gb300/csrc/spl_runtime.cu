@@ -219,9 +219,11 @@ int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points, uint3
   return (int)L;
 }
 
-// Binary32 launches go to the warp-cooperative kernel when at least half of their points lie in
+// Binary32 batches go to the warp-cooperative kernel when at least half of their points lie in
 // instances of this many rows or more; to the ring kernel (one thread per tile) otherwise: many
-// small instances, of which one warp each would leave most lanes without rows.
+// small instances, of which one warp each would leave most lanes without rows.  A single instance
+// always takes the warp-cooperative kernel: below 1,024 rows its latency (a warp per 128-row
+// tile) is far below the ring kernel's (a thread per 16-row tile behind a 48-row halo).
 constexpr uint64_t kScanMinRows = 1024;
 
 struct Staged {
@@ -286,7 +288,7 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
     uint64_t big = 0;
     for (uint32_t i = 0; i < count; ++i)
       if (reqs[i].n >= kScanMinRows) big += reqs[i].n;
-    lp.scan_mixed = 2 * big >= total_points;
+    lp.scan_mixed = count == 1 || 2 * big >= total_points;
     if (lp.scan_mixed)  // tiles of whole 32-row chunks, no longer than the shared-memory scratch holds
       L = p->tile_rows > 0 ? std::min((p->tile_rows + 31) / 32 * 32, spl::scan_mixed_tile_max())
                            : spl::scan_mixed_tile_rows((long long)total_points, c->sm_count, (int)count);

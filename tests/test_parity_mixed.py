@@ -133,6 +133,36 @@ def test_refined_batch(ctx):
 
 
 @pytest.mark.parametrize("refine", [0, 1])
+def test_small_instance_batch(ctx, refine):
+    """A batch whose points lie mostly in instances below 1,024 knots (the one-thread-per-tile ring
+    kernel): sizes 3..1000, clamped and natural ends, against the oracle."""
+    import torch
+    plan = _plan(ctx, 0, refine)
+    rng = np.random.default_rng(40 + refine)
+    sizes = [3, 4, 5, 16, 17, 31, 33, 64, 127, 128, 129, 500, 999, 1000] + list(rng.integers(3, 1000, 50))
+    reqs, keep, refs = [], [], []
+    for i, n in enumerate(sizes):
+        n = int(n)
+        x, y = synth.curve(41, n, instance=i)
+        xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+        ypp = torch.full((n,), np.nan, dtype=torch.float64, device="cuda")
+        m = n + i % 3
+        yq = torch.full((m,), np.nan, dtype=torch.float64, device="cuda")
+        jq = torch.full((m,), -7, dtype=torch.int32, device="cuda")
+        bc = [(NAT, NAT), (-1.0, 2.0), (NAT, 0.5)][i % 3]
+        reqs.append(spl.make_request(xt, yt, bc[0], bc[1], m, ypp, yq, jq))
+        keep.append((xt, yt, ypp, yq, jq))
+        refs.append((x, y, bc, m))
+    for t, (x, y, bc, m), k in zip(ctx.submit_batch(plan, reqs, keep), refs, keep):
+        st, _ = ctx.wait(t)
+        assert st == 0
+        ref = oracle.fit_eval(x, y, bc[0], bc[1], m)
+        assert np.array_equal(k[4].cpu().numpy().astype(np.int64), ref["jq"])
+        assert ypp_error(k[2].cpu().numpy(), ref["ypp"]) <= (1e-8 if refine else TOL_MIXED)
+        assert yq_error(x, y, ref["ypp"], ref["jq"], k[3].cpu().numpy(), ref["yq"]) <= TOL_MIXED
+
+
+@pytest.mark.parametrize("refine", [0, 1])
 def test_full_size_n1e7(ctx, refine):
     """n = M = 10^7, seed 1, in the benchmark's launch configurations (no refinement, one
     refinement step); all outputs compared."""
