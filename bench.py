@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
-    ap.add_argument("--only", default="", choices=["", "f64", "mixed", "mixed-refine", "batched", "variants", "dfma",
+    ap.add_argument("--only", default="", choices=["", "f64", "mixed", "mixed-refine", "batched", "variants", "dfma", "serving",
                                                    "schedule", "n1000", "noalloc"],
                     help="time one path only and print a short line (profiling runs)")
     ap.add_argument("--n", type=int, default=N_POINTS, help="knots = queries per instance (profiling runs)")
@@ -276,8 +276,8 @@ class Runner:
         arena = (min(self.window, self.K) + 2) * (ring + 4 * self.n)
         if not args.no_e2e:
             arena += 10 * (32 * self.n + ring)  # host-buffer leg: staged inputs/outputs, 8 in flight
-        if not args.only or args.only == "batched":
-            arena += 2 << 30  # batched workload scratch
+        if not args.only or args.only in ("batched", "serving"):
+            arena += 2 << 30  # batched workload and serving scratch
         self.ctx = spl.Context(device=local, stream=self.stream, arena_bytes=int(arena), max_slots=8192)
         with torch.cuda.stream(self.stream):
             self.x, self.y = spl.generate_curve(SEED, self.n, instance=rank, device=local, stream=self.stream)
@@ -752,10 +752,10 @@ def run_ours(args, world, rank, local):
     r = Runner(args, world, rank, local)
     spl = r.spl
     if args.only:
-        if args.only in ("variants", "schedule", "n1000", "noalloc", "dfma"):
+        if args.only in ("variants", "schedule", "n1000", "noalloc", "dfma", "serving"):
             res = (r.eval_variants()[0] if args.only == "variants" else r.n_schedule() if args.only == "schedule"
                    else r.config1()[0] if args.only == "n1000" else r.dfma_probe() if args.only == "dfma"
-                   else r.noalloc())
+                   else serving(r)[0] if args.only == "serving" else r.noalloc())
             if rank == 0:
                 print(json.dumps({"profile_run": True, "path": args.only, "result": res}))
             r.ctx.close()

@@ -446,7 +446,9 @@ __device__ void scan_tile(const Inst &I, long long tile, ScanSmem &S, int lane) 
       const long long j = j0 + v;
       if (j >= s0 && j < e0) {
         if (kMode == 1) I.z[j] = val[v];
-        else if (I.ypp) I.ypp[j] = kMode == 2 ? to_f64(zc[v]) + to_f64(val[v]) : to_f64(val[v]);
+        // widened by the hardware conversion (exact): measured faster than the integer-pipe route
+        // here, whose code, repeated per row, weighs on the instruction cache in batched launches
+        else if (I.ypp) I.ypp[j] = kMode == 2 ? (double)zc[v] + (double)val[v] : (double)val[v];
       }
     }
     if (!evaluate) continue;
@@ -494,7 +496,7 @@ __device__ void scan_tile(const Inst &I, long long tile, ScanSmem &S, int lane) 
           const float4 wj1 = (i + 1 < kStepS) ? wst[wpos(i + 1)] : wup[0];
           const double xj = key_to_double(S.keys[wpos(i)]);
           const float xa = dif32_up(q, xj);
-          I.yq[kk] = to_f64(newint32(xa, wj.z - xa, wj.w, wj1.w, wj.y, wj1.y, wj.z, wj.x));
+          I.yq[kk] = (double)newint32(xa, wj.z - xa, wj.w, wj1.w, wj.y, wj1.y, wj.z, wj.x);
           if (I.jq) I.jq[kk] = (int32_t)(R + i);
         }
       }
