@@ -136,11 +136,18 @@ typedef struct spl_ctx_desc {
  *                 values are SPL_ERR_INVALID_ARG.
  *   tile_rows     knots per tile of the chunked solve; 0 picks it from the device and n.
  *                 Exposed so tests can force many small tiles; values below 16 are refused.
- *                 Binary32 launches whose points lie mostly in instances of 1,024 knots or
- *                 more run the warp-cooperative kernel, whose tiles are whole 32-row chunks:
- *                 there tile_rows is rounded up to a multiple of 32.
+ *                 Binary32 launches of one instance, or whose points lie mostly in instances
+ *                 of 1,024 knots or more, run the warp-cooperative kernel, whose tiles are
+ *                 whole 32-row chunks: there tile_rows is rounded up to a multiple of 32.
+ *                 With 0, an FP64 request of one instance of at most SMs x 4,096 knots runs
+ *                 on a cooperative grid of CTAs that exchange their partial solutions (the
+ *                 latency path; its device-side waits are bounded and a wait that runs out
+ *                 completes the request with SPL_ERR_TIMEOUT).
  *   query_mode    spl_query_mode.
- *   eval_variant  spl_eval_variant of the separate evaluation kernel. */
+ *   eval_variant  spl_eval_variant of the separate evaluation kernel.
+ *   fault_flags   failure-detection tests only (0 otherwise): bit 0 makes the last CTA of the
+ *                 multi-CTA FP64 kernel withhold its partial solutions, so that the other
+ *                 CTAs' bounded waits run out.  Other bits are SPL_ERR_INVALID_ARG. */
 typedef struct spl_plan_desc {
   uint64_t max_n;
   int32_t precision;
@@ -148,7 +155,7 @@ typedef struct spl_plan_desc {
   int32_t tile_rows;
   int32_t query_mode;
   int32_t eval_variant;
-  int32_t reserved;
+  uint32_t fault_flags;
 } spl_plan_desc;
 
 /* One instance.
@@ -241,7 +248,9 @@ spl_status spl_poll(spl_ctx *ctx, uint64_t ticket, spl_result *res);
 
 /* As spl_poll (completion of the fit and evaluation of sections "Generating Second Derivatives"
  * and "Fast Interpolation"), blocking up to timeout_ns (bounded; never forever);
- * SPL_ERR_TIMEOUT when it runs out (the ticket stays valid). */
+ * SPL_ERR_TIMEOUT when it runs out (res->status is then SPL_PENDING and the ticket stays valid).
+ * A request that completed because a device-side wait ran out also returns SPL_ERR_TIMEOUT, with
+ * res->status = SPL_ERR_TIMEOUT and the ticket released. */
 spl_status spl_wait(spl_ctx *ctx, uint64_t ticket, uint64_t timeout_ns, spl_result *res);
 
 spl_status spl_get_stats(spl_ctx *ctx, spl_stats *out);

@@ -9,7 +9,7 @@ namespace spl {
 
 // Status bits a tile ORs into its instance's status word (device memory).  kStBadTile: a tile
 // longer than the kernel's scratch holds (the host never launches one; the tile is skipped).
-enum : unsigned { kStNonFinite = 1u, kStNotIncreasing = 2u, kStBadTile = 4u };
+enum : unsigned { kStNonFinite = 1u, kStNotIncreasing = 2u, kStBadTile = 4u, kStWaitTimeout = 8u };
 
 // One instance as the kernels see it (built by the host runtime, lives in device memory
 // or in the kernel parameter block).

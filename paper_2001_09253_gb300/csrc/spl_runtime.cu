@@ -26,7 +26,10 @@ uint64_t round_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
 // Per-launch status block: one status word per instance, then two tile counters (one per
 // kernel of the launch), all zeroed before the launch.
 uint64_t status_words_bytes(uint64_t count) { return round_up(4 * count, 16); }
-uint64_t status_block_bytes(uint64_t count) { return status_words_bytes(count) + 16; }
+// (a single instance's block also holds the exchange area of the multi-CTA FP64 kernel)
+uint64_t status_block_bytes(uint64_t count) {
+  return status_words_bytes(count) + 16 + (count == 1 ? spl::mid_f64_exchange_bytes() : 0);
+}
 
 double now_ms() {
   using namespace std::chrono;
@@ -97,6 +100,7 @@ struct spl_plan {
   int tile_rows;
   int query_mode;
   int eval_variant;
+  unsigned fault_flags;
 };
 
 struct Job;
@@ -160,6 +164,7 @@ spl_status map_status_bits(unsigned bits) {
   if (bits & spl::kStBadTile) return SPL_ERR_INVALID_ARG;
   if (bits & spl::kStNonFinite) return SPL_ERR_NONFINITE;
   if (bits & spl::kStNotIncreasing) return SPL_ERR_NOT_INCREASING;
+  if (bits & spl::kStWaitTimeout) return SPL_ERR_TIMEOUT;
   return SPL_OK;
 }
 
@@ -243,6 +248,8 @@ struct LaunchPlan {
   uint64_t ring_bytes = 0;
   bool fit = true;             // run the fit kernel(s)
   bool small_f64 = false;      // FP64: every instance small enough for one CTA (latency path)
+  bool mid_f64 = false;        // FP64: one instance on a cooperative grid of CTAs (latency path)
+  unsigned fault_flags = 0;    // failure-detection tests (the plan's)
   bool scan_mixed = false;     // binary32: the warp-cooperative kernel (with refinement: two launches)
   bool separate_eval = false;  // evaluate with the separate kernel (explicit queries, stored y'')
   int eval_variant = 0;
@@ -298,9 +305,17 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
     L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, count);
   }
   lp.eval_variant = p->eval_variant;
+  lp.fault_flags = p->fault_flags;
   if (p->precision == SPL_PREC_F64 && p->tile_rows == 0 && lp.fit && !lp.separate_eval) {
-    lp.small_f64 = true;
-    for (uint32_t i = 0; i < count; ++i) lp.small_f64 = lp.small_f64 && reqs[i].n <= (uint64_t)spl::small_f64_max_rows();
+    // one instance up to SMs x 4,096 knots: the multi-CTA kernel (its latency is a piece's FP64
+    // chain); several instances of at most 4,096 knots: one CTA each
+    if (count == 1 && spl::mid_f64_cta_rows((long long)reqs[0].n, c->sm_count) > 0) {
+      lp.mid_f64 = true;
+    } else {
+      lp.small_f64 = true;
+      for (uint32_t i = 0; i < count; ++i)
+        lp.small_f64 = lp.small_f64 && reqs[i].n <= (uint64_t)spl::small_f64_max_rows();
+    }
   }
   lp.insts.resize(count);
   // Instances of 32 tiles or more of the FP64 kernel use the grouped geometry: their tiles
@@ -340,7 +355,9 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
   lp.total_tiles = tiles;
   lp.threads = threads_for(c, p->precision, tiles, lp.scan_mixed);
   lp.tile_rows = L;
-  lp.ring_bytes = (lp.fit && p->precision == SPL_PREC_F64 && !lp.small_f64) ? spl::ring_bytes_f64(lp.threads, L) : 0;
+  lp.ring_bytes = (lp.fit && p->precision == SPL_PREC_F64 && !lp.small_f64 && !lp.mid_f64)
+                      ? spl::ring_bytes_f64(lp.threads, L)
+                      : 0;
 
   // footprint check against the whole budget first
   uint64_t need = round_up(sizeof(Inst) * count, kAlign) + round_up(status_block_bytes(count), kAlign) +
@@ -437,6 +454,9 @@ cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, 
   cudaError_t e = cudaSuccess;
   if (!lp.fit) {
     // stored y'': evaluation only
+  } else if (lp.precision == SPL_PREC_F64 && lp.mid_f64) {
+    e = spl::launch_mid_f64(insts, lp.insts[0].n, counters + 2, c->sm_count, lp.fault_flags, st);
+    if (launches) *launches += 1;
   } else if (lp.precision == SPL_PREC_F64 && lp.small_f64) {
     e = spl::launch_small_f64(insts, count, st);
     if (launches) *launches += 1;
@@ -637,6 +657,7 @@ spl_status spl_plan_create(spl_ctx *c, const spl_plan_desc *d, spl_plan **out) {
   if (d->tile_rows != 0 && d->tile_rows < 16) return SPL_ERR_INVALID_ARG;
   if (d->query_mode != SPL_QUERY_UNIFORM && d->query_mode != SPL_QUERY_EXPLICIT) return SPL_ERR_INVALID_ARG;
   if (d->eval_variant < SPL_EVAL_ORIG || d->eval_variant > SPL_EVAL_NOOP) return SPL_ERR_INVALID_ARG;
+  if (d->fault_flags & ~1u) return SPL_ERR_INVALID_ARG;
   spl_plan *p = new (std::nothrow) spl_plan();
   if (!p) return SPL_ERR_CUDA;
   p->ctx = c;
@@ -646,6 +667,7 @@ spl_status spl_plan_create(spl_ctx *c, const spl_plan_desc *d, spl_plan **out) {
   p->tile_rows = d->tile_rows;
   p->query_mode = d->query_mode;
   p->eval_variant = d->eval_variant;
+  p->fault_flags = d->fault_flags;
   *out = p;
   return SPL_OK;
 }

@@ -45,7 +45,7 @@ class CtxDesc(ctypes.Structure):
 class PlanDesc(ctypes.Structure):
     _fields_ = [("max_n", ctypes.c_uint64), ("precision", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
                 ("tile_rows", ctypes.c_int32), ("query_mode", ctypes.c_int32), ("eval_variant", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("fault_flags", ctypes.c_uint32)]
 
 
 class Request(ctypes.Structure):
@@ -181,11 +181,11 @@ def make_request(x, y, yp1=NATURAL, ypn=NATURAL, m=None, ypp_out=None, yq_out=No
 
 class Plan:
     def __init__(self, ctx: "Context", max_n: int, precision: int = PREC_F64, refine_steps: int = 0,
-                 tile_rows: int = 0, query_mode: int = 0, eval_variant: int = 0):
+                 tile_rows: int = 0, query_mode: int = 0, eval_variant: int = 0, fault_flags: int = 0):
         self.ctx = ctx
         d = PlanDesc(max_n=int(max_n), precision=int(precision), refine_steps=int(refine_steps),
                      tile_rows=int(tile_rows), query_mode=int(query_mode), eval_variant=int(eval_variant),
-                     reserved=0)
+                     fault_flags=int(fault_flags))
         h = ctypes.c_void_p()
         _check(ctx.lib.spl_plan_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)), "spl_plan_create")
         self.handle = h
@@ -257,8 +257,8 @@ class Context:
         self._keep = {}
 
     def plan(self, max_n: int, precision: int = PREC_F64, refine_steps: int = 0, tile_rows: int = 0,
-             query_mode: int = 0, eval_variant: int = 0) -> Plan:
-        return Plan(self, max_n, precision, refine_steps, tile_rows, query_mode, eval_variant)
+             query_mode: int = 0, eval_variant: int = 0, fault_flags: int = 0) -> Plan:
+        return Plan(self, max_n, precision, refine_steps, tile_rows, query_mode, eval_variant, fault_flags)
 
     def submit(self, plan: Plan, x, y, yp1=NATURAL, ypn=NATURAL, m=None, ypp_out=None, yq_out=None,
                jq_out=None, xq=None, ypp_in=None) -> int:
@@ -287,7 +287,7 @@ class Context:
     def wait(self, ticket: int, timeout_s: float = 60.0):
         res = Result()
         s = self.lib.spl_wait(self.handle, int(ticket), int(timeout_s * 1e9), ctypes.byref(res))
-        if s not in (PENDING, ERR_TIMEOUT):
+        if s != PENDING and not (s == ERR_TIMEOUT and res.status == PENDING):  # completed
             self._keep.pop(int(ticket), None)
         return s, res
 

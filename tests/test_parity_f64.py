@@ -202,9 +202,9 @@ def test_full_size_n1e7(ctx):
 
 @pytest.mark.parametrize("n", [3, 4, 5, 127, 128, 129, 255, 256, 257, 1000, 2047, 4095, 4096, 4097])
 def test_small_instances_one_cta(ctx, n):
-    """Automatic tiling sends single FP64 instances of up to 4,096 knots to the one-CTA latency
-    kernel (pieces of ceil(n / 128) rows, block scans of the d' and y'' maps); 4,097 takes the
-    tiled kernel.  Every end-condition pair, query counts below, at and above n."""
+    """Automatic tiling sends single FP64 instances to the latency kernel: one CTA up to 512 knots
+    (pieces of ceil(n / 128) rows, block scans of the d' and y'' maps), several CTAs above
+    (test_parity_mid_f64.py).  Every end-condition pair, query counts below, at and above n."""
     x, y = synth.curve(4000 + n, n)
     plan = _plan(ctx, 0)
     for bc in ((NAT, NAT), (-1.0, 1.0), (NAT, 2.0), (-3.0, NAT)):
@@ -213,7 +213,7 @@ def test_small_instances_one_cta(ctx, n):
 
 
 def test_small_instances_adversarial_and_far_knots(ctx):
-    """The one-CTA kernel on 8-decade gaps and on knots near 5e6 with small gaps."""
+    """The latency kernels on 8-decade gaps and on knots near 5e6 with small gaps."""
     x, y = synth.curve_adversarial(7, 3000, decades=8)
     check_instance(ctx, _plan(ctx, 0), x, y, NAT, NAT, 4001)
     check_instance(ctx, _plan(ctx, 0), x, y, 0.5, -2.0, 2999)

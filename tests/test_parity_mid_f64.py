@@ -1,0 +1,113 @@
+"""GPU parity of the multi-CTA FP64 latency kernel (one instance of up to SMs x 4,096 knots on a
+cooperative grid of CTAs that exchange the affine maps of their partial d' and y'' solutions)
+against the oracle, through the C ABI; and its bounded device-side waits."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2001_09253_gb300 import spl, synth
+from parity_util import TOL_F64, check_instance, ypp_error, yq_error
+
+pytestmark = pytest.mark.gpu
+
+NAT = oracle.NATURAL
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = spl.Context(device=0, arena_bytes=2 << 30, max_slots=64)
+    yield c
+    c.close()
+
+
+def _plan(ctx, max_n=1 << 24, fault_flags=0):
+    return ctx.plan(max_n=max_n, precision=spl.PREC_F64, fault_flags=fault_flags)
+
+
+def _sm_count():
+    import torch
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+@pytest.mark.parametrize("n", [511, 512, 513, 1000, 2048, 2049, 4096, 4097, 5000, 6143, 20000, 65537])
+def test_mid_sizes_ends_and_query_counts(ctx, n):
+    """One CTA up to 512 knots, several from 513 up (pieces of 4 rows, 512 rows per CTA): CTA
+    boundaries on and off the piece grid, ragged last CTAs, every end-condition pair, query counts
+    below, at and above n."""
+    x, y = synth.curve(6000 + n, n)
+    plan = _plan(ctx)
+    for bc in ((NAT, NAT), (-1.0, 1.0), (NAT, 2.0), (-3.0, NAT)):
+        for m in sorted({1, 2, n, 2 * n + 1}):
+            check_instance(ctx, plan, x, y, bc[0], bc[1], m)
+    check_instance(ctx, plan, x, y, NAT, NAT, 0)
+
+
+@pytest.mark.parametrize("which", ["max", "beyond", "mid"])
+def test_mid_largest_instances(ctx, which):
+    """The largest instance the path takes (SMs x 4,096 knots, 32-row pieces on every SM), one
+    knot more (the tiled kernel), and 2e5 knots (11-row pieces)."""
+    n = {"max": _sm_count() * 4096, "beyond": _sm_count() * 4096 + 1, "mid": 200_000}[which]
+    x, y = synth.curve(77, n)
+    check_instance(ctx, _plan(ctx), x, y, NAT, NAT, n)
+    check_instance(ctx, _plan(ctx), x, y, -1.0, 0.5, n // 3)
+
+
+def test_mid_adversarial_gaps_and_far_knots(ctx):
+    """8-decade gaps (y'' spanning many orders across CTA boundaries), geometric gap runs, and
+    knots near 5e6 with small gaps."""
+    x, y = synth.curve_adversarial(11, 100_000, decades=8)
+    check_instance(ctx, _plan(ctx), x, y, NAT, NAT, 150_001)
+    check_instance(ctx, _plan(ctx), x, y, 0.5, -2.0, 99_999)
+    g = np.concatenate([0.7 ** np.arange(60), 0.7 ** np.arange(60)[::-1]] * 100)
+    xg = np.concatenate([[0.0], np.cumsum(g)])
+    for yg in (np.sin(7 * xg), np.random.default_rng(3).random(len(xg))):
+        check_instance(ctx, _plan(ctx), xg, yg, NAT, NAT, 2 * len(xg))
+        check_instance(ctx, _plan(ctx), xg, yg, 1.0, -1.0, len(xg))
+    x, y = synth.curve(12, 30_000)
+    check_instance(ctx, _plan(ctx), x + 5.0e6, y, -1.0, 1.0, 30_000)
+
+
+def test_mid_in_a_graph_batch(ctx):
+    """One instance as a reusable batch: the cooperative launch captured in a CUDA graph and
+    replayed; every replay equals the oracle."""
+    import torch
+    n = 30_000
+    x, y = synth.curve(13, n)
+    xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    ypp = torch.empty(n, dtype=torch.float64, device="cuda")
+    yq = torch.empty(n, dtype=torch.float64, device="cuda")
+    jq = torch.empty(n, dtype=torch.int32, device="cuda")
+    b = ctx.batch(_plan(ctx), [spl.make_request(xt, yt, -1.0, 1.0, n, ypp, yq, jq)], keep=(xt, yt, ypp, yq, jq))
+    ref = oracle.fit_eval(x, y, -1.0, 1.0, n)
+    for _ in range(3):
+        ypp.fill_(float("nan"))
+        b.launch()
+        assert (b.wait() == 0).all()
+        assert np.array_equal(jq.cpu().numpy().astype(np.int64), ref["jq"])
+        assert ypp_error(ypp.cpu().numpy(), ref["ypp"]) <= TOL_F64
+        assert yq_error(x, y, ref["ypp"], ref["jq"], yq.cpu().numpy(), ref["yq"]) <= TOL_F64
+    b.close()
+
+
+def test_mid_wait_timeout_reported_and_context_usable(ctx):
+    """Failure detection without a GPU fault: the last CTA withholds its maps (plan fault bit 0),
+    the other CTAs' bounded waits run out, the request completes with SPL_ERR_TIMEOUT within a
+    second, and the context serves the next request normally."""
+    import torch
+    n = 20_000
+    x, y = synth.curve(14, n)
+    xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    ypp = torch.empty(n, dtype=torch.float64, device="cuda")
+    yq = torch.empty(n, dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+    st, res = ctx.wait(ctx.submit(_plan(ctx, fault_flags=1), xt, yt, NAT, NAT, n, ypp, yq), 10.0)
+    assert st == spl.ERR_TIMEOUT and res.status == spl.ERR_TIMEOUT  # completed, not still pending
+    assert time.perf_counter() - t0 < 5.0
+    check_instance(ctx, _plan(ctx), x, y, NAT, NAT, n)
+
+
+def test_fault_flags_validated(ctx):
+    with pytest.raises(spl.SplError):
+        _plan(ctx, fault_flags=2)
