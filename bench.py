@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
-    ap.add_argument("--only", default="", choices=["", "f64", "mixed", "mixed-refine", "batched", "variants", "dfma", "serving",
+    ap.add_argument("--only", default="", choices=["", "f64", "mixed", "mixed-refine", "batched", "variants", "dfma", "serving", "latency",
                                                    "schedule", "n1000", "noalloc"],
                     help="time one path only and print a short line (profiling runs)")
     ap.add_argument("--n", type=int, default=N_POINTS, help="knots = queries per instance (profiling runs)")
@@ -464,6 +464,30 @@ class Runner:
         return {"workload": "n = M = 1000, seed 0, natural and clamped (-1, 1) ends, one request at a time",
                 "requests_per_case": reps, **out}, (hx, hy)
 
+    def latency_by_size(self, sizes=(1_000, 10_000, 100_000, 600_000, 1_000_000), reps=50):
+        """One request at a time through spl_submit + spl_wait for n = M from 1e3 to 1e6 (the
+        first n points of the benchmark curve, natural ends), FP64 and binary32 with one
+        refinement step: the latency paths (the multi-CTA FP64 kernel up to SMs x 4,096 knots,
+        the warp-cooperative binary32 kernel) and, past them, the tiled FP64 kernel.  Device time
+        per request from the library's events, as distributions."""
+        torch, spl = self.torch, self.spl
+        out = {}
+        for label, prec, refine in (("f64", spl.PREC_F64, 0), ("mixed_refine1", spl.PREC_F32_REFINE, 1)):
+            for n in sizes:
+                x, y = self.x[:n].contiguous(), self.y[:n].contiguous()
+                ypp = torch.empty(n, dtype=torch.float64, device=self.dev)
+                yq = torch.empty(n, dtype=torch.float64, device=self.dev)
+                plan = self.ctx.plan(n, prec, refine_steps=refine)
+                dev_ms = []
+                for r in range(self.W + reps):
+                    st, res = self.ctx.wait(self.ctx.submit(plan, x, y, spl.NATURAL, spl.NATURAL, n, ypp, yq), 60.0)
+                    assert st == spl.OK, spl.status_str(st)
+                    if r >= self.W:
+                        dev_ms.append(float(res.device_ms))
+                out["%s/n=%d" % (label, n)] = dist_summary(dev_ms)
+        return {"workload": "one request at a time, n = M, the first n points of the n = 1e7 curve, natural ends",
+                "unit": "ms (device, per request)", "requests_per_case": reps, **out}
+
     def noalloc(self, sizes=(100_000, 1_000_000), reps=20):
         """spl_fit_eval_noalloc (binary32 + one refinement step, fixed scratch inside the library,
         no allocation) beside spl_submit with the same precision, one instance of n = M at a
@@ -752,10 +776,11 @@ def run_ours(args, world, rank, local):
     r = Runner(args, world, rank, local)
     spl = r.spl
     if args.only:
-        if args.only in ("variants", "schedule", "n1000", "noalloc", "dfma", "serving"):
+        if args.only in ("variants", "schedule", "n1000", "noalloc", "dfma", "serving", "latency"):
             res = (r.eval_variants()[0] if args.only == "variants" else r.n_schedule() if args.only == "schedule"
                    else r.config1()[0] if args.only == "n1000" else r.dfma_probe() if args.only == "dfma"
-                   else serving(r)[0] if args.only == "serving" else r.noalloc())
+                   else serving(r)[0] if args.only == "serving" else r.latency_by_size() if args.only == "latency"
+                   else r.noalloc())
             if rank == 0:
                 print(json.dumps({"profile_run": True, "path": args.only, "result": res}))
             r.ctx.close()
@@ -784,6 +809,7 @@ def run_ours(args, world, rank, local):
     schedule = r.n_schedule()
     small, c1data = r.config1()
     noalloc = r.noalloc()
+    lat_sizes = r.latency_by_size()
     dfma = r.dfma_probe(clock_mhz=(main.get("clocks") or {}).get("sm_mhz"))
     if rank != 0:
         r.ctx.close()
@@ -809,6 +835,7 @@ def run_ours(args, world, rank, local):
         "n_schedule": schedule,
         "newint_variants": variants,
         "n1000": small,
+        "latency_by_size": lat_sizes,
         "noalloc": noalloc,
         "mixed_f32": path_entry(mixed0, "n=M=1e7 seed 1, binary32 solve + cubic, exact binary64 differences "
                                         "and query positions, no refinement", TOL["mixed"], "f32"),
@@ -985,6 +1012,8 @@ def summary(line):
     na = oc.get("noalloc") or {}
     out["noalloc_p50_ms"] = {k: {"noalloc": g(na, k, "noalloc_ms", "median"), "submit": g(na, k, "submit_ms", "median")}
                              for k in ("n=100000", "n=1000000")}
+    ls = oc.get("latency_by_size") or {}
+    out["latency_p50_ms"] = {k: g(ls, k, "median") for k in ls if "/n=" in k}
     v = oc.get("newint_variants") or {}
     out["eval_1e7_ms"] = {lab: {nm: g(v, lab, nm, "ms", "median") for nm in ("orig", "noinv", "vol", "noop")}
                           for lab in ("sorted", "unsorted")}
