@@ -43,7 +43,10 @@ constexpr int kHaloS = 64;             // forward rows before a tile
 constexpr int kOvS = 32;               // back-substitution start past a tile
 constexpr int kWarpsS = 20;            // warps per CTA (one CTA per SM; 12 / 16 / 20 measured: more is faster)
 constexpr int kThreadsS = 32 * kWarpsS;
-constexpr int kTileMaxS = 512;         // longest tile the shared-memory scratch holds
+// longest tile the shared-memory scratch holds: 544 + the 64-row halo + the 32-row overlap = 640
+// rows, five whole steps (512-row tiles used the same five steps for 608 rows: 6 % more steps per
+// point; batched launches 21 % slower)
+constexpr int kTileMaxS = 544;
 constexpr int kRowsCapS = (kTileMaxS + kHaloS + kOvS + kStepS - 1) / kStepS * kStepS;
 constexpr unsigned kFullS = 0xffffffffu;
 constexpr long long kKeyInf = 0x7FF0000000000000LL;  // key of +inf: above every finite knot
