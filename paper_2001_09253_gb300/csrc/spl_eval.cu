@@ -26,13 +26,42 @@ constexpr int kThreadsE = 256;
 // ran as a wave and a partial one: ~9 % slower on unsorted queries)
 constexpr int kBlocksPerSmE = 5;
 
-__device__ __forceinline__ long long bracket_bisect(const double *__restrict__ x, long long n, long long kq) {
+// count = the number of knots x_0..x_{n-2} whose key is below kq; the bracket is count - 1 (0 when
+// count is 0).  With a coarse table T[i] = key(x_{8i}) (built by coarse_keys_kernel for large
+// instances) the first levels run on T, which stays in L2: the entries below kq number
+// cc = ceil(count / 8), so count lies in [8(cc - 1) + 1, min(8 cc, n - 1)], a window of one
+// 64-byte run of knots that three probes of x finish.  The comparisons are the same key
+// comparisons, so the bracket is the same as the plain bisection's.
+__device__ __forceinline__ long long bracket_bisect(const double *__restrict__ x, long long n, long long kq,
+                                                    const long long *__restrict__ ktab) {
   long long lo = 0, hi = n - 1;  // knots x_0..x_{n-2} below q: a count in [lo, hi]
+  if (ktab) {
+    long long a = 0, b = coarse_key_entries(n);
+    while (a < b) {
+      const long long mid = a + ((b - a) >> 1);
+      if (ktab[mid] < kq) a = mid + 1; else b = mid;
+    }
+    if (a == 0) return 0;
+    lo = (long long)kCoarseKeys * (a - 1) + 1;
+    hi = min((long long)kCoarseKeys * a, n - 1);
+  }
   while (lo < hi) {
     const long long mid = lo + ((hi - lo) >> 1);
     if (dkey(x[mid]) < kq) lo = mid + 1; else hi = mid;
   }
   return lo > 0 ? lo - 1 : 0;
+}
+
+// The coarse key tables of the instances that have one (blockIdx.y strides the instances).
+__global__ void coarse_keys_kernel(const Inst *__restrict__ insts, int ninst) {
+  for (int i = blockIdx.y; i < ninst; i += gridDim.y) {
+    const Inst &I = insts[i];
+    if (!I.ktab) continue;
+    long long *t = const_cast<long long *>(I.ktab);
+    const long long nt = coarse_key_entries(I.n);
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nt; e += (long long)gridDim.x * blockDim.x)
+      t[e] = dkey(I.x[e * kCoarseKeys]);
+  }
 }
 
 // The one-division form, with ba = x_{j+1}-x_j, xa = x-x_j, bx = x_{j+1}-x:
@@ -186,7 +215,7 @@ __global__ void __launch_bounds__(kThreadsE, kBlocksPerSmE)
         if (far) gallop = false;
       } else {
         if (jprev >= 0) gallop = false;
-        j = bracket_bisect(x, n, kq);
+        j = bracket_bisect(x, n, kq, nullptr);
       }
       jprev = j;
       const double *__restrict__ y = I.y;
@@ -231,7 +260,7 @@ __global__ void __launch_bounds__(kThreadsE, kBlocksPerSmE)
       }
       q = G.at(k);
     }
-    const long long j = bracket_bisect(x, n, dkey(q));
+    const long long j = bracket_bisect(x, n, dkey(q), I.ktab);
     const double *__restrict__ y = I.y;
     const double *__restrict__ ypp = I.ypp;
     if (kVariant == 3)
@@ -244,8 +273,13 @@ __global__ void __launch_bounds__(kThreadsE, kBlocksPerSmE)
 }
 
 cudaError_t launch_eval(const Inst *d_insts, int ninst, long long total_q, int variant, bool f32, bool uniform,
-                        int sm_count, cudaStream_t stream) {
+                        long long max_coarse_entries, int sm_count, cudaStream_t stream) {
   if (total_q <= 0) return cudaSuccess;
+  if (!uniform && max_coarse_entries > 0) {  // coarse key tables first (instances that have one)
+    const long long bx = std::min<long long>((max_coarse_entries + kThreadsE - 1) / kThreadsE, 4LL * sm_count);
+    const dim3 g((unsigned)std::max<long long>(bx, 1), (unsigned)std::min(ninst, 65535));
+    coarse_keys_kernel<<<g, kThreadsE, 0, stream>>>(d_insts, ninst);
+  }
   // uniform grids (ascending by construction): runs of queries per lane with galloping brackets;
   // explicit positions (any order): one query per thread with bisection
   const long long per_block = uniform ? (long long)kThreadsE * kRunE : (long long)kThreadsE;

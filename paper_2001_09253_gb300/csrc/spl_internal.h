@@ -89,8 +89,10 @@ cudaError_t launch_scan_mixed(const Inst *d_insts, int ninst, long long total_ti
 // (Inst::xq) or on the uniform grid, with the y'' in Inst::ypp; variant = spl_eval_variant; f32:
 // the binary32 form of the mixed-precision plans.
 // uniform: no instance of the launch has explicit positions (the queries ascend).
+// max_coarse_entries: the largest coarse key table of the launch (Inst::ktab), 0 when none; the
+// tables are filled by a kernel launched first.
 cudaError_t launch_eval(const Inst *d_insts, int ninst, long long total_q, int variant, bool f32, bool uniform,
-                        int sm_count, cudaStream_t stream);
+                        long long max_coarse_entries, int sm_count, cudaStream_t stream);
 
 }  // namespace spl
 

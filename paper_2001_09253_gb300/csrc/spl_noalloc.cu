@@ -13,6 +13,7 @@ constexpr size_t kInstOff = 0;      // the instance descriptor
 constexpr size_t kStatusOff = 256;  // its status word and two tile counters (cleared by every call)
 constexpr size_t kZOff = 512;       // binary32 y'' of the first pass, kMaxN floats
 constexpr size_t kScratchBytes = kZOff + 4 * kMaxN;
+static_assert(sizeof(spl::Inst) <= kStatusOff, "the descriptor fits below the status words");
 
 // The scratch.  Every GPU that loads this library holds these 4 MiB + 512 B until the
 // process exits.  Host code must not use this name as an address: it is a host-side stand-in;

@@ -231,6 +231,10 @@ int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points, uint3
 // tile) is far below the ring kernel's (a thread per 16-row tile behind a 48-row halo).
 constexpr uint64_t kScanMinRows = 1024;
 
+// Instances from this many knots up get a coarse key table for the bisection of explicit query
+// positions (below it the whole knot array stays in L2 anyway).
+constexpr uint64_t kCoarseMinKnots = 1ull << 16;
+
 struct Staged {
   std::vector<Block> dev;
   Block pin;
@@ -379,6 +383,13 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
       need += round_up(8 * r.n, kAlign);
     }
   }
+  // explicit query positions on a large instance: the coarse key table of its bisection (scratch)
+  auto coarse_bytes = [&](const spl_request &r) -> uint64_t {
+    return (lp.separate_eval && r.xq && r.m > 0 && r.n >= kCoarseMinKnots)
+               ? 8ull * (uint64_t)spl::coarse_key_entries((long long)r.n)
+               : 0;
+  };
+  for (uint32_t i = 0; i < count; ++i) need += round_up(coarse_bytes(reqs[i]), kAlign);
   // refined mixed path: binary32 y'' of the first pass, one float per knot (scratch)
   const uint64_t z_bytes = lp.refine_steps > 0 ? 4 * total_points : 0;
   need += round_up(z_bytes, kAlign);
@@ -432,6 +443,13 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
       lp.hio.push_back(h);
     }
   }
+  for (uint32_t i = 0; ok && i < count; ++i) {
+    const uint64_t cb = coarse_bytes(reqs[i]);
+    if (!cb) continue;
+    uint64_t off = 0;
+    ok = dev_alloc(c, cb, dev_blocks, &off);
+    if (ok) lp.insts[i].ktab = reinterpret_cast<const long long *>(c->arena + off);
+  }
   uint64_t poff = 0;
   if (ok) ok = c->pin.alloc(pin_need, &poff);
   if (!ok) {
@@ -483,10 +501,14 @@ cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, 
   }
   if (e == cudaSuccess && lp.separate_eval && lp.total_queries > 0) {
     bool uniform = true;
-    for (const Inst &I : lp.insts) uniform = uniform && I.xq == nullptr;
+    long long coarse = 0;
+    for (const Inst &I : lp.insts) {
+      uniform = uniform && I.xq == nullptr;
+      if (I.ktab) coarse = std::max(coarse, spl::coarse_key_entries(I.n));
+    }
     e = spl::launch_eval(insts, count, lp.total_queries, lp.eval_variant, lp.precision != SPL_PREC_F64, uniform,
-                         c->sm_count, st);
-    if (launches) *launches += 1;
+                         coarse, c->sm_count, st);
+    if (launches) *launches += coarse > 0 ? 2 : 1;
   }
   return e;
 }

@@ -251,6 +251,48 @@ def test_explicit_large_sampled(ctx):
     assert e <= TOL_F64
 
 
+@pytest.mark.parametrize("n", [65535, 65536, 65537, 100003])
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_explicit_coarse_key_table(ctx, n, precision):
+    """Instances of 65,536 knots and more bisect explicit positions on a coarse table of every
+    8th knot's key first, then within one 8-knot window: brackets must equal the oracle's on the
+    hardest positions (every knot exactly, the binary64 neighbours on both sides of every knot,
+    both ends and beyond), here and in a batch beside an instance without a table."""
+    import torch
+    from paper_2001_09253_gb300 import spl
+    from parity_util import TOL_MIXED
+    rng = np.random.default_rng(n)
+    x, y = synth.curve(30, n)
+    q = np.concatenate([x, np.nextafter(x, -np.inf), np.nextafter(x, np.inf), _queries(x, n // 4, rng)])
+    rng.shuffle(q)
+    prec = spl.PREC_F64 if precision == "f64" else spl.PREC_F32_REFINE
+    tol = TOL_F64 if precision == "f64" else TOL_MIXED
+    plan = ctx.plan(n, prec, query_mode=spl.QUERY_EXPLICIT)
+    ref = oracle.fit_eval(x, y, NAT, NAT, 0)
+    st, ypp, yq, jq = _run(ctx, plan, x, y, q)
+    assert st == 0
+    jref = oracle.bracket_any(x, q)
+    assert np.array_equal(jq.astype(np.int64), jref)
+    pick = rng.choice(len(q), size=5000, replace=False)
+    yref = oracle.evaluate(x, y, ref["ypp"], q[pick], jref[pick])
+    assert yq_error(x, y, ref["ypp"], jref[pick], yq[pick], yref) <= tol
+    # the same positions in a batch beside a small instance (no table) with its own positions
+    dev = torch.device("cuda", ctx.device)
+    xs, ys = synth.curve(31, 1000)
+    qs = _queries(xs, 3000, rng)
+    big = [torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (x, y, q)]
+    small = [torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (xs, ys, qs)]
+    outs = [(torch.full((len(v[2]),), np.nan, dtype=torch.float64, device=dev),
+             torch.full((len(v[2]),), -7, dtype=torch.int32, device=dev)) for v in (small, big)]
+    reqs = [spl.make_request(v[0], v[1], NAT, NAT, len(v[2]), None, o[0], o[1], xq=v[2])
+            for v, o in zip((small, big), outs)]
+    for t in ctx.submit_batch(plan, reqs, (big, small, outs)):
+        st, _ = ctx.wait(t, 120.0)
+        assert st == 0
+    assert np.array_equal(outs[0][1].cpu().numpy().astype(np.int64), oracle.bracket_any(xs, qs))
+    assert np.array_equal(outs[1][1].cpu().numpy().astype(np.int64), jref)
+
+
 @pytest.mark.parametrize("refine", [0, 1])
 @pytest.mark.parametrize("variant", [0, 1, 2])
 def test_mixed_explicit_queries_and_stored_fit(ctx, refine, variant):
