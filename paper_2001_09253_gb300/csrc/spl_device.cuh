@@ -31,15 +31,8 @@ struct Inst {
   long long mq;         // separate evaluation: queries (the fused kernels see m = 0 then)
   long long q_begin;    // separate evaluation: global index of this instance's first query
   const long long *ktab;// separate evaluation of explicit positions: keys of every kCoarseKeys-th
-                        // knot (the coarse level of the bisection), or null for plain bisection
+                        // knot (spl_internal.h; the coarse level of the bisection), or null
 };
-
-// Knots per entry of the coarse key table of the explicit-position evaluation.
-constexpr int kCoarseKeys = 8;
-// Entries of an instance's coarse key table: knots 0, 8, 16, ... up to n - 2.
-__host__ __device__ __forceinline__ long long coarse_key_entries(long long n) {
-  return (n - 1 + kCoarseKeys - 1) / kCoarseKeys;
-}
 
 // Inst::pad bit of a served request with one refinement step (two passes over its tiles).
 constexpr int kServeRefined = 2;

@@ -27,11 +27,12 @@ constexpr int kThreadsE = 256;
 constexpr int kBlocksPerSmE = 5;
 
 // count = the number of knots x_0..x_{n-2} whose key is below kq; the bracket is count - 1 (0 when
-// count is 0).  With a coarse table T[i] = key(x_{8i}) (built by coarse_keys_kernel for large
+// count is 0).  With a coarse table T[i] = key(x_{16 i}) (built by coarse_keys_kernel for large
 // instances) the first levels run on T, which stays in L2: the entries below kq number
-// cc = ceil(count / 8), so count lies in [8(cc - 1) + 1, min(8 cc, n - 1)], a window of one
-// 64-byte run of knots that three probes of x finish.  The comparisons are the same key
-// comparisons, so the bracket is the same as the plain bisection's.
+// cc = ceil(count / 16), so count lies in [16 (cc - 1) + 1, min(16 cc, n - 1)], a window of one
+// 128-byte run of knots that four probes of x finish.  The comparisons are the same key
+// comparisons, so the bracket is the same as the plain bisection's.  (Every 4th, 8th, 16th or
+// 32nd knot measured at 1e7 unsorted queries: 0.81, 0.72, 0.70, 0.73 ms.)
 __device__ __forceinline__ long long bracket_bisect(const double *__restrict__ x, long long n, long long kq,
                                                     const long long *__restrict__ ktab) {
   long long lo = 0, hi = n - 1;  // knots x_0..x_{n-2} below q: a count in [lo, hi]

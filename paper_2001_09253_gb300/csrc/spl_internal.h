@@ -85,6 +85,13 @@ long long threads_scan_mixed(int sm_count, long long total_tiles);
 cudaError_t launch_scan_mixed(const Inst *d_insts, int ninst, long long total_tiles, int sm_count,
                               unsigned long long *counter, cudaStream_t stream, int mode);
 
+// Knots per entry of the coarse key table of the explicit-position evaluation (every 16th knot),
+// and the entries of an instance's table: knots 0, 16, 32, ... up to n - 2.
+constexpr int kCoarseKeys = 16;
+__host__ __device__ __forceinline__ long long coarse_key_entries(long long n) {
+  return (n - 1 + kCoarseKeys - 1) / kCoarseKeys;
+}
+
 // Separate evaluation (spl_eval.cu): queries q_begin .. q_begin+mq-1 of each instance, explicit
 // (Inst::xq) or on the uniform grid, with the y'' in Inst::ypp; variant = spl_eval_variant; f32:
 // the binary32 form of the mixed-precision plans.

@@ -255,7 +255,7 @@ def test_explicit_large_sampled(ctx):
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_explicit_coarse_key_table(ctx, n, precision):
     """Instances of 65,536 knots and more bisect explicit positions on a coarse table of every
-    8th knot's key first, then within one 8-knot window: brackets must equal the oracle's on the
+    16th knot's key first, then within one 16-knot window: brackets must equal the oracle's on the
     hardest positions (every knot exactly, the binary64 neighbours on both sides of every knot,
     both ends and beyond), here and in a batch beside an instance without a table."""
     import torch
