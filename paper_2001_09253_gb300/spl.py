@@ -180,6 +180,11 @@ def make_request(x, y, yp1=NATURAL, ypn=NATURAL, m=None, ypp_out=None, yq_out=No
 
 
 class Plan:
+    """spl_plan_create: options shared by the requests submitted with the plan (spl_plan_desc in
+    include/spl.h).  fault_flags is for failure-detection tests only: bit 0 makes the last CTA of
+    the multi-CTA FP64 kernel withhold its partial solutions, so that the request completes with
+    ERR_TIMEOUT."""
+
     def __init__(self, ctx: "Context", max_n: int, precision: int = PREC_F64, refine_steps: int = 0,
                  tile_rows: int = 0, query_mode: int = 0, eval_variant: int = 0, fault_flags: int = 0):
         self.ctx = ctx
