@@ -139,7 +139,7 @@ typedef struct spl_ctx_desc {
  *                 Binary32 launches of one instance, or whose points lie mostly in instances
  *                 of 1,024 knots or more, run the warp-cooperative kernel, whose tiles are
  *                 whole 32-row chunks: there tile_rows is rounded up to a multiple of 32.
- *                 With 0, an FP64 request of one instance of at most SMs x 4,096 knots runs
+ *                 With 0, an FP64 request of one instance of at most SMs x 9,600 knots runs
  *                 on a cooperative grid of CTAs that exchange their partial solutions (the
  *                 latency path; its device-side waits are bounded and a wait that runs out
  *                 completes the request with SPL_ERR_TIMEOUT).

@@ -38,7 +38,7 @@ cudaError_t launch_fused_f64(const Inst *d_insts, int ninst, long long total_til
 int small_f64_max_rows();
 cudaError_t launch_small_f64(const Inst *d_insts, int ninst, cudaStream_t stream);
 // FP64 fit + evaluation of one mid-size instance on a cooperative grid of CTAs (spl_mid_f64.cu):
-// mid_f64_cta_rows gives the rows per CTA for n points (0: beyond the path, n > SMs x 4096);
+// mid_f64_cta_rows gives the rows per CTA for n points (0: beyond the path, n > SMs x 9600);
 // `exchange` (mid_f64_exchange_bytes, zeroed before the launch) carries the CTAs' maps; fault bit
 // 0 makes the last CTA withhold its maps (failure-detection tests: the others' waits run out).
 uint64_t mid_f64_exchange_bytes();

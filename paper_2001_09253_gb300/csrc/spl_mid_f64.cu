@@ -7,7 +7,9 @@
 //
 // The one-CTA kernel (spl_small_f64.cu) spread over G CTAs of kThreadsMF threads: CTA b owns the
 // rows [b Lb, (b+1) Lb), its threads pieces of L = Lb / kThreadsMF rows, with L chosen so that
-// G <= the SM count (a cooperative launch: every CTA is resident at once).  On this part a warp's
+// G <= the SM count (a cooperative launch: every CTA is resident at once).  The CTA's c', d' and
+// sensitivities live in shared memory, and up to 4,096 rows per CTA also its x and y; up to
+// 9,600 rows the x and y are read from global memory instead.  On this part a warp's
 // FP64 instruction holds its sub-partition's FP64 unit for ~64 cycles, so the time is the FP64
 // chain of a piece; more CTAs give shorter pieces.  Every recurrence is split as in the one-CTA
 // kernel, plus one exchange between CTAs per direction:
@@ -33,7 +35,8 @@ namespace spl {
 
 constexpr int kThreadsMF = 128;   // one warp per sub-partition
 constexpr int kWarpsMF = kThreadsMF / 32;
-constexpr int kMaxRowsMF = 4096;  // rows of one CTA that the shared memory holds
+constexpr int kMaxRowsMF = 4096;  // rows of one CTA with x and y staged in shared memory
+constexpr int kMaxRowsBigMF = 9600;  // rows of one CTA without the staging (c', d', sensitivities only)
 constexpr int kWarmMF = 16;       // c'-only rows before a piece
 constexpr int kTargetRowsMF = 4;  // rows per thread while there are SMs to spare (4, 8, 16 measured: 4 best)
 constexpr int kMaxCtasMF = 256;   // exchange slots
@@ -48,11 +51,9 @@ struct MidExchange {
 };
 static_assert(sizeof(MidExchange) == 48, "exchange slot layout");
 
-constexpr int kStageMF = kMaxRowsMF + kWarmMF + 2;  // staged knots/values: warm-up rows, the CTA's, one past
-
+// Shared memory: this head, then c', d' and the sensitivities of the CTA's Lb rows and, when the
+// kernel stages them, x and y of rows [r_lo, r_hi) (warm-up rows, the CTA's, one past).
 struct MidSmem {
-  double cp[kMaxRowsMF], dp[kMaxRowsMF], mm[kMaxRowsMF];
-  double sx[kStageMF], sy[kStageMF];   // x, y of rows [r_lo, r_hi), loaded once, coalesced
   double wa[kWarpsMF], wb[kWarpsMF];   // per-warp totals of the block scans
   double ta, tb;                       // the CTA's total map of a block scan
   long long kfirst[kThreadsMF + 1];    // first query of each piece, and of the row past the CTA
@@ -60,6 +61,12 @@ struct MidSmem {
   double din, yend;                    // d' entering the CTA, y'' past its last row
   unsigned fail;
 };
+constexpr size_t kHeadMF = (sizeof(MidSmem) + 15) / 16 * 16;
+__host__ __device__ constexpr size_t mid_smem_bytes(long long Lb, bool stage) {
+  return kHeadMF + 8 * (size_t)(3 * Lb + (stage ? 2 * (Lb + kWarmMF + 2) : 0));
+}
+static_assert(mid_smem_bytes(kMaxRowsMF, true) <= 232448 && mid_smem_bytes(kMaxRowsBigMF, false) <= 232448,
+              "one CTA's shared memory");
 
 struct RowMF {
   double a, b, c, d;
@@ -209,17 +216,23 @@ __device__ long long first_above_mf(const Grid &G, double inv_step, double v) {
   return k + 1;
 }
 
+// kStage: x and y of the CTA's rows staged in shared memory (Lb <= kMaxRowsMF); otherwise read from
+// global memory (Lb <= kMaxRowsBigMF: larger instances, whose rows no longer fit beside them).
+template <bool kStage>
 __global__ void __launch_bounds__(kThreadsMF, 1)
     mid_f64_kernel(const Inst *__restrict__ inst, MidExchange *__restrict__ ex, long long Lb, unsigned fault) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   MidSmem &S = *reinterpret_cast<MidSmem *>(smem_raw);
+  double *const cpS = reinterpret_cast<double *>(smem_raw + kHeadMF);
+  double *const dpS = cpS + Lb;
+  double *const mmS = dpS + Lb;
   const Inst I = *inst;
   const long long n = I.n, m = I.m;
   const double *__restrict__ x = I.x;
   const double *__restrict__ y = I.y;
   const int t = threadIdx.x, b = blockIdx.x, G = gridDim.x;
   const bool nat0 = is_natural(I.yp1), nat1 = is_natural(I.ypn);
-  if (Lb > kMaxRowsMF || Lb % kThreadsMF != 0 || G > kMaxCtasMF) {  // never launched by the host
+  if (Lb > (kStage ? kMaxRowsMF : kMaxRowsBigMF) || Lb % kThreadsMF != 0 || G > kMaxCtasMF) {  // never launched by the host
     if (t == 0) atomicOr(I.status, kStBadTile);
     return;
   }
@@ -230,16 +243,22 @@ __global__ void __launch_bounds__(kThreadsMF, 1)
   const bool withhold = (fault & 1u) && b == G - 1;  // failure-detection tests: the others time out
   if (t == 0) S.fail = 0u;
   unsigned bad = 0;
-  // every x and y the CTA reads (the warm-up rows before it, its rows, one past) into shared
-  // memory in one coalesced pass: the row loops below then wait on no global load
-  const long long r_lo = max(c0 - kWarmMF - 1, 0LL), r_hi = min(c1 + 1, n);
-  for (long long r = r_lo + t; r < r_hi; r += kThreadsMF) {
-    S.sx[r - r_lo] = x[r];
-    S.sy[r - r_lo] = y[r];
+  // kStage: every x and y the CTA reads (the warm-up rows before it, its rows, one past) into
+  // shared memory in one coalesced pass, so the row loops below wait on no global load
+  const double *__restrict__ XS = x;  // XS[j] = x_j (from shared memory for j in [r_lo, r_hi))
+  const double *__restrict__ YS = y;
+  if (kStage) {
+    double *const sx = mmS + Lb;
+    double *const sy = sx + (Lb + kWarmMF + 2);
+    const long long r_lo = max(c0 - kWarmMF - 1, 0LL), r_hi = min(c1 + 1, n);
+    for (long long r = r_lo + t; r < r_hi; r += kThreadsMF) {
+      sx[r - r_lo] = x[r];
+      sy[r - r_lo] = y[r];
+    }
+    __syncthreads();
+    XS = sx - r_lo;
+    YS = sy - r_lo;
   }
-  __syncthreads();
-  const double *__restrict__ XS = S.sx - r_lo;  // XS[j] = x_j for j in [r_lo, r_hi)
-  const double *__restrict__ YS = S.sy - r_lo;
 
   // ---- forward: c' warm-up, then the piece's rows from the guess d'_{s0-1} = 0 ----
   double cp = 0.0, dp = 0.0, M = 1.0, hm = 0.0, sm = 0.0;
@@ -279,9 +298,9 @@ __global__ void __launch_bounds__(kThreadsMF, 1)
     cp = r.c * iden;
     dp = (r.d - r.a * dp) * iden;
     M *= -r.a * iden;
-    S.cp[j - c0] = cp;
-    S.dp[j - c0] = dp;
-    S.mm[j - c0] = M;
+    cpS[j - c0] = cp;
+    dpS[j - c0] = dp;
+    mmS[j - c0] = M;
     hm = h;
     sm = sl;
   }
@@ -299,11 +318,11 @@ __global__ void __launch_bounds__(kThreadsMF, 1)
   }
   __syncthreads();
   const double delta = fma(EB, S.din, EA);
-  for (long long j = s0; j < e0; ++j) S.dp[j - c0] = fma(S.mm[j - c0], delta, S.dp[j - c0]);
+  for (long long j = s0; j < e0; ++j) dpS[j - c0] = fma(mmS[j - c0], delta, dpS[j - c0]);
   // ---- back substitution: each piece's map of the y'' above it, block scan, the CTAs above ----
   double P = 0.0, Q = 1.0;
   for (long long j = e0 - 1; j >= s0; --j) {
-    const double c = S.cp[j - c0], d = S.dp[j - c0];
+    const double c = cpS[j - c0], d = dpS[j - c0];
     P = fma(-c, P, d);
     Q *= -c;
   }
@@ -321,8 +340,8 @@ __global__ void __launch_bounds__(kThreadsMF, 1)
   __syncthreads();
   double Y = fma(FB, S.yend, FA);  // y'' of row e0
   for (long long j = e0 - 1; j >= s0; --j) {
-    Y = S.dp[j - c0] - S.cp[j - c0] * Y;
-    S.dp[j - c0] = Y;
+    Y = dpS[j - c0] - cpS[j - c0] * Y;
+    dpS[j - c0] = Y;
     if (I.ypp) I.ypp[j] = Y;
   }
   if (t == 0 && S.fail) bad |= kStWaitTimeout;
@@ -363,8 +382,8 @@ __global__ void __launch_bounds__(kThreadsMF, 1)
       ih = rcp64(xj1 - xj);
     }
     const double ba = xj1 - xj, xa = q - xj, bx = xj1 - q;
-    const double ppj = S.dp[j - c0];
-    const double ppj1 = (j + 1 < c1) ? S.dp[j + 1 - c0] : S.yend;  // past the CTA: the next CTA's first row
+    const double ppj = dpS[j - c0];
+    const double ppj1 = (j + 1 < c1) ? dpS[j + 1 - c0] : S.yend;  // past the CTA: the next CTA's first row
     const double lower = xa * YS[j + 1] + bx * YS[j];
     const double C = (xa * xa - ba * ba) * xa * ppj1;
     const double D = (bx * bx - ba * ba) * bx * ppj;
@@ -381,13 +400,14 @@ std::atomic<unsigned> g_mid_ok[kMaxDevMF];
 uint64_t mid_f64_exchange_bytes() { return (uint64_t)kMaxCtasMF * sizeof(MidExchange); }
 
 // Rows per CTA for n points on sm_count SMs: kTargetRowsMF rows per thread while that needs no
-// more CTAs than SMs, else as few more as fit one CTA per SM; 0 when n is beyond the path.
+// more CTAs than SMs, else as few more as fit one CTA per SM; 0 when n is beyond the path
+// (SMs x kMaxRowsBigMF knots).
 long long mid_f64_cta_rows(long long n, int sm_count) {
   const int ctas = std::min(sm_count, kMaxCtasMF);
   long long L = std::max<long long>(kTargetRowsMF, (n + (long long)ctas * kThreadsMF - 1) / ((long long)ctas * kThreadsMF));
   const long long G1 = (n + (long long)kThreadsMF * kTargetRowsMF - 1) / ((long long)kThreadsMF * kTargetRowsMF);
   if (G1 <= 1) L = (n + kThreadsMF - 1) / kThreadsMF;  // one CTA: the shortest pieces
-  if (L * kThreadsMF > kMaxRowsMF) return 0;
+  if (L * kThreadsMF > kMaxRowsBigMF) return 0;
   return L * kThreadsMF;
 }
 
@@ -396,11 +416,16 @@ cudaError_t launch_mid_f64(const Inst *d_inst, long long n, void *exchange, int 
   const long long Lb = mid_f64_cta_rows(n, sm_count);
   if (Lb <= 0) return cudaErrorInvalidValue;
   const unsigned G = (unsigned)((n + Lb - 1) / Lb);
+  const bool stage = Lb <= kMaxRowsMF;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (!(dev >= 0 && dev < kMaxDevMF && g_mid_ok[dev].load(std::memory_order_acquire))) {
-    e = cudaFuncSetAttribute(mid_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MidSmem));
+    e = cudaFuncSetAttribute(mid_f64_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)mid_smem_bytes(kMaxRowsMF, true));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(mid_f64_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)mid_smem_bytes(kMaxRowsBigMF, false));
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < kMaxDevMF) g_mid_ok[dev].store(1u, std::memory_order_release);
   }
@@ -408,14 +433,16 @@ cudaError_t launch_mid_f64(const Inst *d_inst, long long n, void *exchange, int 
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(G);
   cfg.blockDim = dim3(kThreadsMF);
-  cfg.dynamicSmemBytes = sizeof(MidSmem);
+  cfg.dynamicSmemBytes = mid_smem_bytes(Lb, stage);
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, mid_f64_kernel, d_inst, reinterpret_cast<MidExchange *>(exchange), Lb, fault);
+  MidExchange *ex = reinterpret_cast<MidExchange *>(exchange);
+  return stage ? cudaLaunchKernelEx(&cfg, mid_f64_kernel<true>, d_inst, ex, Lb, fault)
+               : cudaLaunchKernelEx(&cfg, mid_f64_kernel<false>, d_inst, ex, Lb, fault);
 }
 
 }  // namespace spl

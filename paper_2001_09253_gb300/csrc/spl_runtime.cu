@@ -311,7 +311,7 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
   lp.eval_variant = p->eval_variant;
   lp.fault_flags = p->fault_flags;
   if (p->precision == SPL_PREC_F64 && p->tile_rows == 0 && lp.fit && !lp.separate_eval) {
-    // one instance up to SMs x 4,096 knots: the multi-CTA kernel (its latency is a piece's FP64
+    // one instance up to SMs x 9,600 knots: the multi-CTA kernel (its latency is a piece's FP64
     // chain); several instances of at most 4,096 knots: one CTA each
     if (count == 1 && spl::mid_f64_cta_rows((long long)reqs[0].n, c->sm_count) > 0) {
       lp.mid_f64 = true;

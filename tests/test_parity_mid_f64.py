@@ -1,4 +1,4 @@
-"""GPU parity of the multi-CTA FP64 latency kernel (one instance of up to SMs x 4,096 knots on a
+"""GPU parity of the multi-CTA FP64 latency kernel (one instance of up to SMs x 9,600 knots on a
 cooperative grid of CTAs that exchange the affine maps of their partial d' and y'' solutions)
 against the oracle, through the C ABI; and its bounded device-side waits."""
 import time
@@ -44,11 +44,15 @@ def test_mid_sizes_ends_and_query_counts(ctx, n):
     check_instance(ctx, plan, x, y, NAT, NAT, 0)
 
 
-@pytest.mark.parametrize("which", ["max", "beyond", "mid"])
+@pytest.mark.parametrize("which", ["staged_max", "unstaged_min", "max", "beyond", "mid"])
 def test_mid_largest_instances(ctx, which):
-    """The largest instance the path takes (SMs x 4,096 knots, 32-row pieces on every SM), one
-    knot more (the tiled kernel), and 2e5 knots (11-row pieces)."""
-    n = {"max": _sm_count() * 4096, "beyond": _sm_count() * 4096 + 1, "mid": 200_000}[which]
+    """The largest instance with x and y staged in shared memory (SMs x 4,096 knots, 32-row
+    pieces), one knot more (33-row pieces, x and y read from global memory), the largest the path
+    takes (SMs x 9,600 knots, 75-row pieces), one knot more (the tiled kernel), and 2e5 knots
+    (11-row pieces)."""
+    sms = _sm_count()
+    n = {"staged_max": sms * 4096, "unstaged_min": sms * 4096 + 1, "max": sms * 9600, "beyond": sms * 9600 + 1,
+         "mid": 200_000}[which]
     x, y = synth.curve(77, n)
     check_instance(ctx, _plan(ctx), x, y, NAT, NAT, n)
     check_instance(ctx, _plan(ctx), x, y, -1.0, 0.5, n // 3)
