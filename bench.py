@@ -514,7 +514,7 @@ class Runner:
                     t_sub.append(ms)
             out["n=%d" % n] = {"noalloc_ms": dist_summary(t_na), "submit_ms": dist_summary(t_sub)}
         return {"workload": "one instance of the n = 1e7 curve's first n points, M = n, binary32 + one refinement "
-                            "step: spl_fit_eval_noalloc (ring kernels, fixed scratch) and spl_submit", **out}
+                            "step: spl_fit_eval_noalloc (warp-cooperative kernels, fixed scratch) and spl_submit", **out}
 
     def dfma_probe(self, warps_per_sm=8, trips=6000, reps=5, clock_mhz=None):
         """The FP64 pipe's rate on a pure DFMA stream (spl_selftest_dfma: one CTA of `warps_per_sm`

@@ -118,7 +118,8 @@ extern "C" spl_status spl_fit_eval_noalloc(const double *x, const double *y, uin
   I.x = x; I.y = y; I.ypp = ypp_out; I.yq = yq_out; I.jq = nullptr;
   I.n = (long long)n; I.m = (long long)m;
   I.yp1 = yp1; I.ypn = ypn;
-  const long long L = spl::mixed_ring_tile_rows(sms, n);  // the runtime's rule for one instance
+  // the warp-cooperative kernel and the runtime's tile rule for one binary32 instance
+  const long long L = spl::scan_mixed_tile_rows((long long)n, sms, 1);
   I.tile_rows = (int)L;
   I.ntiles = ((long long)n + L - 1) / L;
   I.tile_begin = 0;
@@ -129,8 +130,8 @@ extern "C" spl_status spl_fit_eval_noalloc(const double *x, const double *y, uin
   unsigned long long *counters = reinterpret_cast<unsigned long long *>(base + kStatusOff + 16);
   noalloc_prepare<<<1, 1, 0, st>>>(I, d_inst, I.status, counters);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = spl::launch_fused_mixed(d_inst, 1, I.ntiles, sms, counters, st, true);
-  if (e == cudaSuccess) e = spl::launch_refine_mixed(d_inst, 1, I.ntiles, sms, counters + 1, st);
+  if (e == cudaSuccess) e = spl::launch_scan_mixed(d_inst, 1, I.ntiles, sms, counters, st, 1);
+  if (e == cudaSuccess) e = spl::launch_scan_mixed(d_inst, 1, I.ntiles, sms, counters + 1, st, 2);
   if (e != cudaSuccess) return SPL_ERR_CUDA;
   if (status_out) {
     unsigned bits = 0;
