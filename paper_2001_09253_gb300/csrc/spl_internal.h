@@ -46,27 +46,6 @@ long long mid_f64_cta_rows(long long n, int sm_count);
 cudaError_t launch_mid_f64(const Inst *d_inst, long long n, void *exchange, int sm_count, unsigned fault,
                            cudaStream_t stream);
 
-// Mixed-precision fused fit + evaluation (spl_fused_mixed.cu).
-long long threads_mixed(int sm_count, long long total_tiles);
-int mixed_threads_per_sm();  // threads of one ring-kernel CTA (one CTA per SM)
-// Tile length of the ring kernel for ONE instance of n points: 16-row tiles while n is too small
-// to keep every SM busy with long tiles (one tile's serial chain is then the time; measured on
-// GB300 for n = 1e3..1e6, 16 rows ran the binary32 fit ~3x faster than 128), else the length
-// that gives every thread of one wave one tile, at least 128 rows.
-inline int mixed_ring_tile_rows(int sm_count, unsigned long long n) {
-  if (n <= (unsigned long long)sm_count * 13000ull) return 16;
-  const unsigned long long target = (unsigned long long)sm_count * (unsigned long long)mixed_threads_per_sm();
-  unsigned long long L = (n + target - 1) / target;
-  L = L < 128 ? 128 : (L > (1u << 20) ? (1u << 20) : L);
-  return (int)L;
-}
-// fit_only: first pass of the refined path (y'' in binary32 to each Inst::z, no queries).
-cudaError_t launch_fused_mixed(const Inst *d_insts, int ninst, long long total_tiles, int sm_count,
-                               unsigned long long *counter, cudaStream_t stream, bool fit_only);
-// Second pass of the refined path: one refinement step of y'' and the evaluation.
-cudaError_t launch_refine_mixed(const Inst *d_insts, int ninst, long long total_tiles, int sm_count,
-                                unsigned long long *counter, cudaStream_t stream);
-
 // Persistent serving loop (spl_mixed_scan.cu): a cooperative launch of one CTA per SM; its
 // workers solve tiles of serve_tile_rows(tile_rows) rows (at most serve_tile_max()) with the
 // warp-cooperative kernel's solver, each in its own shared memory.

@@ -1,6 +1,6 @@
 // Warp-cooperative binary32 fit + evaluation ("scan" form of the mixed-precision path).
 //
-// The system and arithmetic are those of the binary32 ring kernel (spl_fused_mixed.cu): the
+// The binary32 path of every mixed-precision launch: the
 // tridiagonal system of eq. (init_val) with the end rows of "Start and End Derivatives", the
 // Thomas recurrences of "Implementation", and the one-division form of "Fast Interpolation" on
 // the grid of "Curve Interpolation", in binary32 arithmetic on exact, once-rounded differences of

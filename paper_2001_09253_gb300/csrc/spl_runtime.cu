@@ -188,29 +188,28 @@ spl_status check_request(const spl_plan *plan, const spl_request *r) {
 
 // Launch geometry: persistent CTAs, tiles fetched dynamically.  The FP64 kernel runs 448
 // threads per SM, one tile per thread (its measured best between FP64-pipe latency hiding and
-// the per-tile work more tiles bring); the binary32 ring kernel 512, one tile per thread; the
-// warp-cooperative binary32 kernel 1024, one tile per warp.
-long long threads_for(const spl_ctx *c, int precision, long long total_tiles, bool scan_mixed) {
+// the per-tile work more tiles bring); the warp-cooperative binary32 kernel 640, one tile per
+// warp.
+long long threads_for(const spl_ctx *c, int precision, long long total_tiles) {
   return precision == SPL_PREC_F64 ? spl::threads_f64(c->sm_count, total_tiles)
-         : scan_mixed              ? spl::threads_scan_mixed(c->sm_count, total_tiles)
-                                   : spl::threads_mixed(c->sm_count, total_tiles);
+                                   : spl::threads_scan_mixed(c->sm_count, total_tiles);
 }
 
-// Tile length (one tile per thread) for the FP64 and binary32 ring kernels, so that one instance
-// of total_points fills every thread of one wave; never shorter than a few halos.  FP64 tiles
-// come in warp groups of 32L - overhang - lane0_short rows, so L is chosen for the group count to
+// Tile length (one tile per thread) for the tiled FP64 kernel, so that one instance of
+// total_points fills every thread of one wave; never shorter than a few halos.  FP64 tiles come
+// in warp groups of 32L - overhang - lane0_short rows, so L is chosen for the group count to
 // match the warps.
-int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points, uint32_t count) {
+int auto_tile_rows(const spl_ctx *c, uint64_t total_points, uint32_t count) {
   // several instances: short tiles, fetched dynamically, balance instances of uneven sizes
   // (one wave of long tiles waits on the longest; 4,096 log-uniform instances run ~1.4x faster)
   if (count > 1) return 128;
-  // One instance too small to keep the GPU's FP64 (or binary32) pipes busy with long tiles:
+  // One instance too small to keep the GPU's FP64 pipes busy with long tiles (an explicit tile
+  // length or a stored fit keeps it on this kernel; otherwise it takes the multi-CTA kernel):
   // its time is then one tile's serial dependency chain (halo, tile, back-substitution start,
   // one thread), so short tiles spread it over more warps.  Measured on GB300 for n = 1e3..1e5:
-  // 16-row tiles halve the FP64 time (0.36-0.41 -> 0.17 ms) and cut the binary32 time 3x; past
-  // a few 1e5 points (FP64) the halo work that every short tile repeats outweighs the shorter
-  // chain, and from ~1e6 the grouped long tiles below win.
-  if (precision != SPL_PREC_F64) return spl::mixed_ring_tile_rows(c->sm_count, total_points);
+  // 16-row tiles halve the time (0.36-0.41 -> 0.17 ms); past a few 1e5 points the halo work that
+  // every short tile repeats outweighs the shorter chain, and from ~1e6 the grouped long tiles
+  // below win.
   const uint64_t upto16 = (uint64_t)c->sm_count * 2000ull;
   const uint64_t upto32 = (uint64_t)c->sm_count * 8000ull;
   if (total_points <= upto16) return 16;
@@ -223,13 +222,6 @@ int auto_tile_rows(const spl_ctx *c, int precision, uint64_t total_points, uint3
   L = std::min<long long>(L, 1 << 20);
   return (int)L;
 }
-
-// Binary32 batches go to the warp-cooperative kernel when at least half of their points lie in
-// instances of this many rows or more; to the ring kernel (one thread per tile) otherwise: many
-// small instances, of which one warp each would leave most lanes without rows.  A single instance
-// always takes the warp-cooperative kernel: below 1,024 rows its latency (a warp per 128-row
-// tile) is far below the ring kernel's (a thread per 16-row tile behind a 48-row halo).
-constexpr uint64_t kScanMinRows = 1024;
 
 // Instances from this many knots up get a coarse key table for the bisection of explicit query
 // positions (below it the whole knot array stays in L2 anyway).
@@ -254,7 +246,6 @@ struct LaunchPlan {
   bool small_f64 = false;      // FP64: every instance small enough for one CTA (latency path)
   bool mid_f64 = false;        // FP64: one instance on a cooperative grid of CTAs (latency path)
   unsigned fault_flags = 0;    // failure-detection tests (the plan's)
-  bool scan_mixed = false;     // binary32: the warp-cooperative kernel (with refinement: two launches)
   bool separate_eval = false;  // evaluate with the separate kernel (explicit queries, stored y'')
   int eval_variant = 0;
   long long total_queries = 0;
@@ -293,20 +284,15 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
   lp.refine_steps = p->precision == SPL_PREC_F64 ? 0 : p->refine_steps;
   lp.fit = reqs[0].ypp_in == nullptr;
   lp.separate_eval = p->query_mode == SPL_QUERY_EXPLICIT || !lp.fit;
-  lp.scan_mixed = false;
   int L;
   if (p->precision == SPL_PREC_F32_REFINE) {
-    uint64_t big = 0;
-    for (uint32_t i = 0; i < count; ++i)
-      if (reqs[i].n >= kScanMinRows) big += reqs[i].n;
-    lp.scan_mixed = count == 1 || 2 * big >= total_points;
-    if (lp.scan_mixed)  // tiles of whole 32-row chunks, no longer than the shared-memory scratch holds
-      L = p->tile_rows > 0 ? std::min((p->tile_rows + 31) / 32 * 32, spl::scan_mixed_tile_max())
-                           : spl::scan_mixed_tile_rows((long long)total_points, c->sm_count, (int)count);
-    else
-      L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, count);
+    // the warp-cooperative kernel for every binary32 launch (one thread per tile was 2-6x slower
+    // even on batches of instances of a few hundred knots): tiles of whole 32-row chunks, no
+    // longer than its shared memory holds
+    L = p->tile_rows > 0 ? std::min((p->tile_rows + 31) / 32 * 32, spl::scan_mixed_tile_max())
+                         : spl::scan_mixed_tile_rows((long long)total_points, c->sm_count, (int)count);
   } else {
-    L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, p->precision, total_points, count);
+    L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, total_points, count);
   }
   lp.eval_variant = p->eval_variant;
   lp.fault_flags = p->fault_flags;
@@ -357,7 +343,7 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
     }
   }
   lp.total_tiles = tiles;
-  lp.threads = threads_for(c, p->precision, tiles, lp.scan_mixed);
+  lp.threads = threads_for(c, p->precision, tiles);
   lp.tile_rows = L;
   lp.ring_bytes = (lp.fit && p->precision == SPL_PREC_F64 && !lp.small_f64 && !lp.mid_f64)
                       ? spl::ring_bytes_f64(lp.threads, L)
@@ -482,21 +468,12 @@ cudaError_t launch_path(spl_ctx *c, const LaunchPlan &lp, uint64_t d_insts_off, 
     e = spl::launch_fused_f64(insts, count, lp.total_tiles, reinterpret_cast<double *>(c->arena + d_ring_off),
                               lp.tile_rows, c->sm_count, counters, st);
     if (launches) *launches += 1;
-  } else if (lp.scan_mixed) {
-    if (lp.refine_steps == 0) {
-      e = spl::launch_scan_mixed(insts, count, lp.total_tiles, c->sm_count, counters, st, 0);
-      if (launches) *launches += 1;
-    } else {
-      e = spl::launch_scan_mixed(insts, count, lp.total_tiles, c->sm_count, counters, st, 1);
-      if (e == cudaSuccess) e = spl::launch_scan_mixed(insts, count, lp.total_tiles, c->sm_count, counters + 1, st, 2);
-      if (launches) *launches += 2;
-    }
   } else if (lp.refine_steps == 0) {
-    e = spl::launch_fused_mixed(insts, count, lp.total_tiles, c->sm_count, counters, st, false);
+    e = spl::launch_scan_mixed(insts, count, lp.total_tiles, c->sm_count, counters, st, 0);
     if (launches) *launches += 1;
   } else {
-    e = spl::launch_fused_mixed(insts, count, lp.total_tiles, c->sm_count, counters, st, true);
-    if (e == cudaSuccess) e = spl::launch_refine_mixed(insts, count, lp.total_tiles, c->sm_count, counters + 1, st);
+    e = spl::launch_scan_mixed(insts, count, lp.total_tiles, c->sm_count, counters, st, 1);
+    if (e == cudaSuccess) e = spl::launch_scan_mixed(insts, count, lp.total_tiles, c->sm_count, counters + 1, st, 2);
     if (launches) *launches += 2;
   }
   if (e == cudaSuccess && lp.separate_eval && lp.total_queries > 0) {

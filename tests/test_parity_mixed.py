@@ -134,8 +134,8 @@ def test_refined_batch(ctx):
 
 @pytest.mark.parametrize("refine", [0, 1])
 def test_small_instance_batch(ctx, refine):
-    """A batch whose points lie mostly in instances below 1,024 knots (the one-thread-per-tile ring
-    kernel): sizes 3..1000, clamped and natural ends, against the oracle."""
+    """A batch of mostly small instances (sizes 3..1000, one or two tiles each, a warp per tile):
+    clamped and natural ends, against the oracle."""
     import torch
     plan = _plan(ctx, 0, refine)
     rng = np.random.default_rng(40 + refine)
