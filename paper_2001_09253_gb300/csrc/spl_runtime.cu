@@ -298,11 +298,13 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
   lp.fault_flags = p->fault_flags;
   if (p->precision == SPL_PREC_F64 && p->tile_rows == 0 && lp.fit && !lp.separate_eval) {
     // one instance up to SMs x 9,600 knots: the multi-CTA kernel (its latency is a piece's FP64
-    // chain); several instances of at most 4,096 knots: one CTA each
+    // chain); up to two waves of instances of at most 4,096 knots (two CTAs fit an SM): one CTA
+    // each.  More instances go to the tiled kernel, whose throughput then wins (4,096 instances of
+    // 3..4,096 knots: 0.98 ms against 1.24 ms; 512 of 1,000..4,096: 0.43 ms against 0.27 ms).
     if (count == 1 && spl::mid_f64_cta_rows((long long)reqs[0].n, c->sm_count) > 0) {
       lp.mid_f64 = true;
     } else {
-      lp.small_f64 = true;
+      lp.small_f64 = count <= 4u * (uint32_t)c->sm_count;
       for (uint32_t i = 0; i < count; ++i)
         lp.small_f64 = lp.small_f64 && reqs[i].n <= (uint64_t)spl::small_f64_max_rows();
     }

@@ -221,6 +221,35 @@ def test_small_instances_adversarial_and_far_knots(ctx):
     check_instance(ctx, _plan(ctx, 0), x + 5.0e6, y, -1.0, 1.0, 2500)
 
 
+def test_many_small_instances_take_the_tiled_kernel(ctx):
+    """More than two waves of small FP64 instances (700 > 4 x SMs on GB300) run the tiled kernel:
+    a sample of them against the oracle, with clamped and natural ends."""
+    import torch
+    plan = _plan(ctx, 0)
+    rng = np.random.default_rng(60)
+    sizes = rng.integers(3, 2001, 700)
+    reqs, keep, refs = [], [], []
+    for i, n in enumerate(sizes):
+        n = int(n)
+        x, y = synth.curve(61, n, instance=i)
+        xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+        ypp = torch.empty(n, dtype=torch.float64, device="cuda")
+        yq = torch.empty(n, dtype=torch.float64, device="cuda")
+        bc = (NAT, NAT) if i % 2 else (-1.0, 0.5)
+        reqs.append(spl.make_request(xt, yt, bc[0], bc[1], n, ypp, yq))
+        keep.append((xt, yt, ypp, yq))
+        refs.append((x, y, bc))
+    tickets = ctx.submit_batch(plan, reqs, keep)
+    for t in tickets:
+        st, _ = ctx.wait(t)
+        assert st == 0
+    for i in rng.choice(len(sizes), size=60, replace=False):
+        x, y, bc = refs[i]
+        ref = oracle.fit_eval(x, y, bc[0], bc[1], len(x))
+        assert ypp_error(keep[i][2].cpu().numpy(), ref["ypp"]) <= TOL_F64
+        assert yq_error(x, y, ref["ypp"], ref["jq"], keep[i][3].cpu().numpy(), ref["yq"]) <= TOL_F64
+
+
 def test_small_instances_batched_and_errors(ctx):
     """Several small FP64 instances in one launch (one CTA each) with one bad instance."""
     import torch
