@@ -39,12 +39,15 @@ int small_f64_max_rows();
 cudaError_t launch_small_f64(const Inst *d_insts, int ninst, cudaStream_t stream);
 // FP64 fit + evaluation of one mid-size instance on a cooperative grid of CTAs (spl_mid_f64.cu):
 // mid_f64_cta_rows gives the rows per CTA for n points (0: beyond the path, n > SMs x 9600);
-// `exchange` (mid_f64_exchange_bytes, zeroed before the launch) carries the CTAs' maps; fault bit
-// 0 makes the last CTA withhold its maps (failure-detection tests: the others' waits run out).
+// the descriptor is *d_inst in device memory or, with d_inst null, *h_inst passed by value;
+// `exchange` (mid_f64_exchange_bytes) carries the CTAs' maps: zeroed before the launch with
+// launch = 0, else an area reserved for such launches and given a new launch number > 0 each time
+// (never cleared); fault bit 0 makes the last CTA withhold its maps (failure-detection tests: the
+// others' waits run out).
 uint64_t mid_f64_exchange_bytes();
 long long mid_f64_cta_rows(long long n, int sm_count);
-cudaError_t launch_mid_f64(const Inst *d_inst, long long n, void *exchange, int sm_count, unsigned fault,
-                           cudaStream_t stream);
+cudaError_t launch_mid_f64(const Inst *d_inst, const Inst *h_inst, long long n, void *exchange,
+                           unsigned long long launch, int sm_count, unsigned fault, cudaStream_t stream);
 
 // Persistent serving loop (spl_mixed_scan.cu): a cooperative launch of one CTA per SM; its
 // workers solve tiles of serve_tile_rows(tile_rows) rows (at most serve_tile_max()) with the
@@ -56,12 +59,14 @@ int serve_tile_max();
 // Warp-cooperative binary32 fit + evaluation (spl_mixed_scan.cu): one warp per tile of
 // scan_mixed_tile_rows rows (a multiple of 32, at most scan_mixed_tile_max()), its scratch in
 // shared memory.  mode 0: fit + eval; 1: fit only into Inst::z (binary32), the refined path's
-// first pass; 2: refinement of Inst::z + eval.  `counter` must be zero when the kernel starts.
+// first pass; 2: refinement of Inst::z + eval.  The descriptors are d_insts in device memory or,
+// with d_insts null, the one instance *h_one passed by value.  Warps fetch tiles from `counter`,
+// which must be zero when the kernel starts; the kernel leaves it at zero when it ends.
 int scan_mixed_threads_per_sm();
 int scan_mixed_tile_max();
 int scan_mixed_tile_rows(long long total_points, int sm_count, int count);
 long long threads_scan_mixed(int sm_count, long long total_tiles);
-cudaError_t launch_scan_mixed(const Inst *d_insts, int ninst, long long total_tiles, int sm_count,
+cudaError_t launch_scan_mixed(const Inst *d_insts, const Inst *h_one, int ninst, long long total_tiles, int sm_count,
                               unsigned long long *counter, cudaStream_t stream, int mode);
 
 // Knots per entry of the coarse key table of the explicit-position evaluation (every 16th knot),

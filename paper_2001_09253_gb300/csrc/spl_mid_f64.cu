@@ -38,16 +38,18 @@ constexpr int kWarpsMF = kThreadsMF / 32;
 constexpr int kMaxRowsMF = 4096;  // rows of one CTA with x and y staged in shared memory
 constexpr int kMaxRowsBigMF = 9600;  // rows of one CTA without the staging (c', d', sensitivities only)
 constexpr int kWarmMF = 16;       // c'-only rows before a piece
-constexpr int kTargetRowsMF = 4;  // rows per thread while there are SMs to spare (4, 8, 16 measured: 4 best)
+constexpr int kTargetRowsMF = 1;  // rows per thread while there are SMs to spare (1, 2, 4, 8, 16 measured: 1 best)
+constexpr int kOneCtaMaxMF = 512; // up to this many rows one CTA (up to 4 rows per thread) beats the exchange
 constexpr int kMaxCtasMF = 256;   // exchange slots
 constexpr unsigned long long kWaitNsMF = 200000000ull;
 
-// One CTA's maps in the per-launch exchange area (zeroed before the launch).
+// One CTA's maps in the exchange area.  A map is published when its flag holds the launch's tag:
+// 1 in an area zeroed before the launch, else the launch's own number (an area that outlives
+// launches then holds only older numbers, so it needs no clearing).
 struct MidExchange {
   double fa, fb;     // d' at the CTA's last row = fa + fb * (d' at the row before its first)
   double ba, bb;     // y'' at the CTA's first row = ba + bb * (y'' at the row past its last)
-  unsigned fflag, bflag;
-  unsigned pad[2];
+  unsigned long long fflag, bflag;
 };
 static_assert(sizeof(MidExchange) == 48, "exchange slot layout");
 
@@ -155,8 +157,9 @@ __device__ __forceinline__ unsigned long long gtimer_mf() {
 
 // Warp 0: the composition of the published maps of the `count` CTAs k0, k0 + dir, ..., in that
 // order (the first one is a constant map): returns its constant term.  Waits (bounded) for each
-// map's flag; *fail is set on every lane when any wait ran out.
-__device__ double compose_published(const MidExchange *ex, int k0, int count, int dir, bool fwd, unsigned *fail) {
+// map's flag to hold `tag`; *fail is set on every lane when any wait ran out.
+__device__ double compose_published(const MidExchange *ex, int k0, int count, int dir, bool fwd,
+                                    unsigned long long tag, unsigned *fail) {
   const int lane = threadIdx.x & 31;
   unsigned late = 0u;
   double PA = 0.0, PB = 1.0;
@@ -165,10 +168,10 @@ __device__ double compose_published(const MidExchange *ex, int k0, int count, in
     double A = 0.0, B = 1.0;
     if (i < count) {
       const MidExchange *e = ex + (k0 + dir * i);
-      const volatile unsigned *flag = fwd ? &e->fflag : &e->bflag;
+      const volatile unsigned long long *flag = fwd ? &e->fflag : &e->bflag;
       const unsigned long long t0 = gtimer_mf();
       unsigned sleep_ns = 32;
-      while (*flag == 0u) {
+      while (*flag != tag) {
         if (gtimer_mf() - t0 > kWaitNsMF) {
           late = 1u;
           break;
@@ -192,7 +195,7 @@ __device__ double compose_published(const MidExchange *ex, int k0, int count, in
   return PA;
 }
 
-__device__ void publish_mf(MidExchange *e, double A, double B, bool fwd) {
+__device__ void publish_mf(MidExchange *e, double A, double B, bool fwd, unsigned long long tag) {
   if (fwd) {
     e->fa = A;
     e->fb = B;
@@ -201,7 +204,7 @@ __device__ void publish_mf(MidExchange *e, double A, double B, bool fwd) {
     e->bb = B;
   }
   __threadfence();
-  atomicExch(fwd ? &e->fflag : &e->bflag, 1u);
+  atomicExch(fwd ? &e->fflag : &e->bflag, tag);
 }
 
 // Least k in [0, m] with x_k > v on the grid (binary64 estimate, checked on its two neighbours).
@@ -218,15 +221,19 @@ __device__ long long first_above_mf(const Grid &G, double inv_step, double v) {
 
 // kStage: x and y of the CTA's rows staged in shared memory (Lb <= kMaxRowsMF); otherwise read from
 // global memory (Lb <= kMaxRowsBigMF: larger instances, whose rows no longer fit beside them).
+// The descriptor is *inst, or `one` (a kernel parameter) when inst is null; `launch` is the
+// launch's number for an exchange area that is not cleared before it, 0 for a zeroed one.
 template <bool kStage>
 __global__ void __launch_bounds__(kThreadsMF, 1)
-    mid_f64_kernel(const Inst *__restrict__ inst, MidExchange *__restrict__ ex, long long Lb, unsigned fault) {
+    mid_f64_kernel(const Inst *__restrict__ inst, const Inst one, MidExchange *__restrict__ ex,
+                   long long Lb, unsigned fault, unsigned long long launch) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   MidSmem &S = *reinterpret_cast<MidSmem *>(smem_raw);
   double *const cpS = reinterpret_cast<double *>(smem_raw + kHeadMF);
   double *const dpS = cpS + Lb;
   double *const mmS = dpS + Lb;
-  const Inst I = *inst;
+  const Inst I = inst ? *inst : one;
+  const unsigned long long tag = launch ? launch : 1ull;
   const long long n = I.n, m = I.m;
   const double *__restrict__ x = I.x;
   const double *__restrict__ y = I.y;
@@ -307,10 +314,10 @@ __global__ void __launch_bounds__(kThreadsMF, 1)
   // ---- d' entering each piece: block scan, then the maps of the CTAs below ----
   double EA, EB;
   scan_up_mf(has ? dp : 0.0, has ? M : 1.0, S, EA, EB);
-  if (t == 0 && !withhold) publish_mf(ex + b, S.ta, S.tb, true);
+  if (t == 0 && !withhold) publish_mf(ex + b, S.ta, S.tb, true, tag);
   if (t < 32) {
     unsigned fail = 0u;
-    const double din = (b > 0) ? compose_published(ex, 0, b, 1, true, &fail) : 0.0;
+    const double din = (b > 0) ? compose_published(ex, 0, b, 1, true, tag, &fail) : 0.0;
     if (t == 0) {
       S.din = din;
       if (fail) S.fail = 1u;
@@ -328,10 +335,10 @@ __global__ void __launch_bounds__(kThreadsMF, 1)
   }
   double FA, FB;
   scan_down_mf(has ? P : 0.0, has ? Q : 1.0, S, FA, FB);
-  if (t == 0 && !withhold) publish_mf(ex + b, S.ta, S.tb, false);
+  if (t == 0 && !withhold) publish_mf(ex + b, S.ta, S.tb, false, tag);
   if (t < 32) {
     unsigned fail = 0u;
-    const double yend = (b < G - 1) ? compose_published(ex, G - 1, G - 1 - b, -1, false, &fail) : 0.0;
+    const double yend = (b < G - 1) ? compose_published(ex, G - 1, G - 1 - b, -1, false, tag, &fail) : 0.0;
     if (t == 0) {
       S.yend = yend;
       if (fail) S.fail = 1u;
@@ -399,20 +406,22 @@ std::atomic<unsigned> g_mid_ok[kMaxDevMF];
 
 uint64_t mid_f64_exchange_bytes() { return (uint64_t)kMaxCtasMF * sizeof(MidExchange); }
 
-// Rows per CTA for n points on sm_count SMs: kTargetRowsMF rows per thread while that needs no
-// more CTAs than SMs, else as few more as fit one CTA per SM; 0 when n is beyond the path
-// (SMs x kMaxRowsBigMF knots).
+// Rows per CTA for n points on sm_count SMs: one CTA up to kOneCtaMaxMF rows; beyond, kTargetRowsMF
+// rows per thread while that needs no more CTAs than SMs, else as few more as fit one CTA per SM;
+// 0 when n is beyond the path (SMs x kMaxRowsBigMF knots).  Measured on GB300 (one request, device
+// time): n = 1,000 in 0.028 ms with 1-row pieces on 8 CTAs against 0.037 ms with 4-row pieces on 2;
+// n = 300 in 0.025 ms on one CTA against 0.028 ms on 3.
 long long mid_f64_cta_rows(long long n, int sm_count) {
   const int ctas = std::min(sm_count, kMaxCtasMF);
   long long L = std::max<long long>(kTargetRowsMF, (n + (long long)ctas * kThreadsMF - 1) / ((long long)ctas * kThreadsMF));
-  const long long G1 = (n + (long long)kThreadsMF * kTargetRowsMF - 1) / ((long long)kThreadsMF * kTargetRowsMF);
-  if (G1 <= 1) L = (n + kThreadsMF - 1) / kThreadsMF;  // one CTA: the shortest pieces
+  if (n <= kOneCtaMaxMF) L = (n + kThreadsMF - 1) / kThreadsMF;  // one CTA: the shortest pieces
   if (L * kThreadsMF > kMaxRowsBigMF) return 0;
   return L * kThreadsMF;
 }
 
-cudaError_t launch_mid_f64(const Inst *d_inst, long long n, void *exchange, int sm_count, unsigned fault,
-                           cudaStream_t stream) {
+cudaError_t launch_mid_f64(const Inst *d_inst, const Inst *h_inst, long long n, void *exchange,
+                           unsigned long long launch, int sm_count, unsigned fault, cudaStream_t stream) {
+  if (!d_inst && !h_inst) return cudaErrorInvalidValue;
   const long long Lb = mid_f64_cta_rows(n, sm_count);
   if (Lb <= 0) return cudaErrorInvalidValue;
   const unsigned G = (unsigned)((n + Lb - 1) / Lb);
@@ -441,8 +450,10 @@ cudaError_t launch_mid_f64(const Inst *d_inst, long long n, void *exchange, int 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   MidExchange *ex = reinterpret_cast<MidExchange *>(exchange);
-  return stage ? cudaLaunchKernelEx(&cfg, mid_f64_kernel<true>, d_inst, ex, Lb, fault)
-               : cudaLaunchKernelEx(&cfg, mid_f64_kernel<false>, d_inst, ex, Lb, fault);
+  Inst one{};
+  if (!d_inst) one = *h_inst;
+  return stage ? cudaLaunchKernelEx(&cfg, mid_f64_kernel<true>, d_inst, one, ex, Lb, fault, launch)
+               : cudaLaunchKernelEx(&cfg, mid_f64_kernel<false>, d_inst, one, ex, Lb, fault, launch);
 }
 
 }  // namespace spl

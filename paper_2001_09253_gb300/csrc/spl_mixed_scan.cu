@@ -513,17 +513,22 @@ __device__ void scan_tile(const Inst &I, long long tile, ScanSmem &S, int lane) 
 template <int kMode>
 __global__ void __launch_bounds__(kThreadsS, 1)
     mixed_scan_kernel(const Inst *__restrict__ insts, int ninst, long long total_tiles,
-                      unsigned long long *__restrict__ counter) {
+                      unsigned long long *__restrict__ counter, const Inst one) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   ScanSmem &S = reinterpret_cast<ScanSmem *>(smem_raw)[threadIdx.x >> 5];
+  const unsigned long long last_claim = (unsigned long long)total_tiles + gridDim.x * (blockDim.x >> 5) - 1;
   for (;;) {
     unsigned long long t = 0;
-    if (lane == 0) t = atomicAdd(counter, 1ull);
+    if (lane == 0) {
+      t = atomicAdd(counter, 1ull);
+      // every warp ends with one claim past the tiles, so the claim numbered last_claim is the
+      // launch's final operation on the counter: it leaves the counter at zero for the next launch
+      if (t == last_claim) atomicExch(counter, 0ull);
+    }
     t = __shfl_sync(kFullS, t, 0);
     if ((long long)t >= total_tiles) break;
-    const int i = find_inst(insts, ninst, (long long)t);
-    const Inst I = insts[i];
+    const Inst I = insts ? insts[find_inst(insts, ninst, (long long)t)] : one;
     scan_tile<kMode>(I, (long long)t - I.tile_begin, S, lane);
     __syncwarp();
   }
@@ -774,17 +779,21 @@ long long threads_scan_mixed(int sm_count, long long total_tiles) {
   return (long long)blocks * bt;
 }
 
-cudaError_t launch_scan_mixed(const Inst *d_insts, int ninst, long long total_tiles, int sm_count,
+cudaError_t launch_scan_mixed(const Inst *d_insts, const Inst *h_one, int ninst, long long total_tiles, int sm_count,
                               unsigned long long *counter, cudaStream_t stream, int mode) {
+  if ((!d_insts && (!h_one || ninst != 1)) || !counter) return cudaErrorInvalidValue;
   const cudaError_t attr = allow_smem();
   if (attr != cudaSuccess) return attr;
   int blocks, bt;
   spread_grid(sm_count, total_tiles * 32, kThreadsS, &blocks, &bt);
   const size_t smem = kSmemPerWarpS * (size_t)(bt / 32);
+  Inst one{};
+  if (!d_insts) one = *h_one;
+  const dim3 g((unsigned)blocks), b((unsigned)bt);
   switch (mode) {
-    case 1: mixed_scan_kernel<1><<<(unsigned)blocks, (unsigned)bt, smem, stream>>>(d_insts, ninst, total_tiles, counter); break;
-    case 2: mixed_scan_kernel<2><<<(unsigned)blocks, (unsigned)bt, smem, stream>>>(d_insts, ninst, total_tiles, counter); break;
-    default: mixed_scan_kernel<0><<<(unsigned)blocks, (unsigned)bt, smem, stream>>>(d_insts, ninst, total_tiles, counter); break;
+    case 1: mixed_scan_kernel<1><<<g, b, smem, stream>>>(d_insts, ninst, total_tiles, counter, one); break;
+    case 2: mixed_scan_kernel<2><<<g, b, smem, stream>>>(d_insts, ninst, total_tiles, counter, one); break;
+    default: mixed_scan_kernel<0><<<g, b, smem, stream>>>(d_insts, ninst, total_tiles, counter, one); break;
   }
   return cudaGetLastError();
 }

@@ -130,8 +130,8 @@ extern "C" spl_status spl_fit_eval_noalloc(const double *x, const double *y, uin
   unsigned long long *counters = reinterpret_cast<unsigned long long *>(base + kStatusOff + 16);
   noalloc_prepare<<<1, 1, 0, st>>>(I, d_inst, I.status, counters);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = spl::launch_scan_mixed(d_inst, 1, I.ntiles, sms, counters, st, 1);
-  if (e == cudaSuccess) e = spl::launch_scan_mixed(d_inst, 1, I.ntiles, sms, counters + 1, st, 2);
+  if (e == cudaSuccess) e = spl::launch_scan_mixed(d_inst, nullptr, 1, I.ntiles, sms, counters, st, 1);
+  if (e == cudaSuccess) e = spl::launch_scan_mixed(d_inst, nullptr, 1, I.ntiles, sms, counters + 1, st, 2);
   if (e != cudaSuccess) return SPL_ERR_CUDA;
   if (status_out) {
     unsigned bits = 0;

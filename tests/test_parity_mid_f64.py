@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_2001_09253_gb300 import spl, synth
-from parity_util import TOL_F64, check_instance, ypp_error, yq_error
+from parity_util import TOL_F64, check_instance, run_gpu, ypp_error, yq_error
 
 pytestmark = pytest.mark.gpu
 
@@ -33,9 +33,9 @@ def _sm_count():
 
 @pytest.mark.parametrize("n", [511, 512, 513, 1000, 2048, 2049, 4096, 4097, 5000, 6143, 20000, 65537])
 def test_mid_sizes_ends_and_query_counts(ctx, n):
-    """One CTA up to 512 knots, several from 513 up (pieces of 4 rows, 512 rows per CTA): CTA
-    boundaries on and off the piece grid, ragged last CTAs, every end-condition pair, query counts
-    below, at and above n."""
+    """One CTA up to 512 knots (pieces of up to 4 rows), several from 513 up (1-row pieces, 128
+    rows per CTA, up to SMs x 128 knots; longer pieces beyond): ragged last CTAs and pieces,
+    every end-condition pair, query counts below, at and above n."""
     x, y = synth.curve(6000 + n, n)
     plan = _plan(ctx)
     for bc in ((NAT, NAT), (-1.0, 1.0), (NAT, 2.0), (-3.0, NAT)):
@@ -71,6 +71,38 @@ def test_mid_adversarial_gaps_and_far_knots(ctx):
         check_instance(ctx, _plan(ctx), xg, yg, 1.0, -1.0, len(xg))
     x, y = synth.curve(12, 30_000)
     check_instance(ctx, _plan(ctx), x + 5.0e6, y, -1.0, 1.0, 30_000)
+
+
+def test_mid_consecutive_requests_reuse_the_exchange_area(ctx):
+    """A single request in device memory launches the multi-CTA kernel without clearing its exchange
+    area: each launch waits for flags that hold its own launch number.  Grids that shrink and grow
+    between consecutive requests (the area still holding flags of earlier, larger grids) all equal
+    the oracle."""
+    plan = _plan(ctx)
+    for i, n in enumerate([20_000, 1_000, 65_537, 600, 5_000, 20_000, 130, 65_537, 2_049]):
+        x, y = synth.curve(900 + i, n)
+        check_instance(ctx, plan, x, y, NAT, NAT, n)
+        check_instance(ctx, plan, x, y, -1.0, 0.5, n // 2 + 1)
+
+
+def test_mid_validation_errors_reported(ctx):
+    """Input errors found on the device reach the request's status (the kernel ORs its status bits
+    into the job's pinned status word); the context keeps working."""
+    x, y = synth.curve(16, 5000)
+    plan = _plan(ctx)
+    bad = x.copy()
+    bad[2500] = bad[2499]
+    st, *_ = run_gpu(ctx, plan, bad, y, NAT, NAT, 100)
+    assert st == spl.ERR_NOT_INCREASING
+    bad = y.copy()
+    bad[4999] = np.nan
+    st, *_ = run_gpu(ctx, plan, x, bad, NAT, NAT, 100)
+    assert st == spl.ERR_NONFINITE
+    bad = x.copy()
+    bad[0] = -np.inf
+    st, *_ = run_gpu(ctx, plan, bad, y, -1.0, 1.0, 100)
+    assert st == spl.ERR_NONFINITE
+    check_instance(ctx, plan, x, y, NAT, NAT, 5000)
 
 
 def test_mid_in_a_graph_batch(ctx):

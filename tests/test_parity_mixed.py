@@ -132,6 +132,17 @@ def test_refined_batch(ctx):
         assert yq_error(x, y, ref["ypp"], ref["jq"], k[3].cpu().numpy(), ref["yq"]) <= TOL_MIXED
 
 
+def test_consecutive_single_requests_reuse_the_tile_counter(ctx):
+    """A single request in device memory launches the binary32 kernel(s) with a tile counter that
+    no memset clears: the kernel's last tile claim leaves it at zero for the next launch.  Requests
+    whose tile counts change from one launch to the next, with and without the refinement step,
+    all equal the oracle (a counter left non-zero would skip tiles, leaving the NaN fill)."""
+    for i, n in enumerate([100_000, 1_000, 1_000_000, 3, 50_000, 129, 300_001]):
+        x, y = synth.curve(950 + i, n)
+        check_instance(ctx, _plan(ctx, refine=i % 2), x, y, NAT, NAT, n, tol=TOL_MIXED)
+        check_instance(ctx, _plan(ctx, refine=1 - i % 2), x, y, -1.0, 1.0, n // 3 + 1, tol=TOL_MIXED)
+
+
 @pytest.mark.parametrize("refine", [0, 1])
 def test_small_instance_batch(ctx, refine):
     """A batch of mostly small instances (sizes 3..1000, one or two tiles each, a warp per tile):
