@@ -435,9 +435,11 @@ class Runner:
     def config1(self, reps=200):
         """The smallest configuration: n = M = 1,000 (seed 0), natural and clamped (-1, 1) ends,
         one request at a time through spl_submit + spl_wait, FP64 and binary32 with one refinement
-        step.  Latency per request: device (the library's CUDA events from the descriptor copy to
-        the status copy back) and wall (host clock around the Python submit and wait), as
-        distributions over `reps` requests after warm-up."""
+        step.  Latency per request: device (the library's CUDA events around the request's stream
+        work: for one instance in device memory the kernel(s) alone, the descriptor passed as a
+        kernel parameter and the status written by the kernel into pinned host memory) and wall
+        (host clock around the Python submit and wait), as distributions over `reps` requests after
+        warm-up."""
         torch, spl = self.torch, self.spl
         from paper_2001_09253_gb300 import synth
         n = 1000
@@ -467,7 +469,7 @@ class Runner:
     def latency_by_size(self, sizes=(1_000, 10_000, 100_000, 600_000, 1_000_000), reps=50):
         """One request at a time through spl_submit + spl_wait for n = M from 1e3 to 1e6 (the
         first n points of the benchmark curve, natural ends), FP64 and binary32 with one
-        refinement step: the latency paths (the multi-CTA FP64 kernel up to SMs x 4,096 knots,
+        refinement step: the latency paths (the multi-CTA FP64 kernel up to SMs x 9,600 knots,
         the warp-cooperative binary32 kernel) and, past them, the tiled FP64 kernel.  Device time
         per request from the library's events, as distributions."""
         torch, spl = self.torch, self.spl
@@ -639,9 +641,11 @@ class Runner:
                             "points, shuffled; %d seeded draws (n from %d to %d), one new curve per draw, "
                             "routines in shuffled order" % (draws, int(sizes.min()), nmax),
                 "unit": "ns per point",
-                "timing": "device: the library's CUDA events around one request (descriptor copy, status "
-                          "reset, kernels, status copy back); wall: host clock around the Python submit and "
-                          "wait (includes the binding's marshalling and the completion poll)",
+                "timing": "device: the library's CUDA events around one request (fit + evaluation: the "
+                          "kernel alone, the descriptor a kernel parameter and the status written into pinned "
+                          "host memory; evaluation from a stored fit: status reset, descriptor copy, kernel, "
+                          "status copy back); wall: host clock around the Python submit and wait (includes "
+                          "the binding's marshalling and the completion poll)",
                 "routines": out, "wall": out_wall}
 
 

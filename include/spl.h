@@ -213,7 +213,8 @@ const char *spl_status_str(int32_t status);
 /* Creates a context (device, stream, arena) for the fit and evaluation of section "Fast
  * Interpolation" / "Generating Second Derivatives"; SPL_ERR_INVALID_ARG for a null or malformed
  * descriptor (max_slots < 1, arena_bytes < 1 MiB, an arena not 256-byte aligned), SPL_ERR_CUDA when
- * the device is absent or an allocation fails.  *out is NULL on failure. */
+ * the device is absent or an allocation fails.  *out is NULL on failure.  The context keeps ~12 KB
+ * of the arena for its single-instance launches (spl_submit) from creation on. */
 spl_status spl_create(spl_ctx **out, const spl_ctx_desc *desc);
 void spl_destroy(spl_ctx *ctx);  /* waits for the context's work; NULL is a no-op.  Destroy the
                                     context's servers first: they use its arena. */
@@ -233,7 +234,11 @@ void spl_plan_destroy(spl_plan *plan);
  * SPL_ERR_INVALID_ARG (n < 3 or > max_n, null arrays, a NaN or -inf end slope), SPL_ERR_BUDGET
  * (footprint above the arena) or SPL_ERR_QUEUE_FULL (no slot or memory now).  The paper's input
  * asserts (strictly increasing knots) and finite values are checked on the device and reported at
- * completion (NOT_INCREASING, NONFINITE). */
+ * completion (NOT_INCREASING, NONFINITE).  One instance in device memory that is fitted and
+ * evaluated in one pass (no ypp_in, uniform queries, automatic tile length for SPL_PREC_F64 up to
+ * SMs x 9,600 knots, any binary32 plan) is enqueued as its kernel launch(es) alone where the device
+ * has native atomics on host memory: the descriptor goes as a kernel parameter and the kernel writes
+ * the status into the context's pinned memory, with no copy or memset around it. */
 spl_status spl_submit(spl_ctx *ctx, spl_plan *plan, const spl_request *req, uint64_t *ticket);
 
 /* Many instances in one launch; tickets[i] names req[i].  All requests must use the same

@@ -311,7 +311,8 @@ __global__ void __launch_bounds__(kThreadsMF, 1)
     hm = h;
     sm = sl;
   }
-  // ---- d' entering each piece: block scan, then the maps of the CTAs below ----
+  // ---- d' entering each piece: block scan, then the maps of the CTAs below (warp 0), while
+  // warp 1 forms the query grid's step (off the critical path: the other warps wait anyway) ----
   double EA, EB;
   scan_up_mf(has ? dp : 0.0, has ? M : 1.0, S, EA, EB);
   if (t == 0 && !withhold) publish_mf(ex + b, S.ta, S.tb, true, tag);
@@ -322,8 +323,17 @@ __global__ void __launch_bounds__(kThreadsMF, 1)
       S.din = din;
       if (fail) S.fail = 1u;
     }
+  } else if (t == 32 && m > 0) {
+    const Grid G0 = make_grid(x, n, m);
+    S.step = G0.step;
+    S.inv_step = (m >= 2) ? rcp64(G0.step) : 0.0;
   }
   __syncthreads();
+  Grid Gd;
+  Gd.x0 = x[0];
+  Gd.xl = x[n - 1];
+  Gd.m = m;
+  Gd.step = S.step;
   const double delta = fma(EB, S.din, EA);
   for (long long j = s0; j < e0; ++j) dpS[j - c0] = fma(mmS[j - c0], delta, dpS[j - c0]);
   // ---- back substitution: each piece's map of the y'' above it, block scan, the CTAs above ----
@@ -343,6 +353,13 @@ __global__ void __launch_bounds__(kThreadsMF, 1)
       S.yend = yend;
       if (fail) S.fail = 1u;
     }
+  } else if (m > 0) {
+    // meanwhile warps 1..3: the first query of every piece (threads without rows: s0 = c1, the
+    // row past the CTA) and of the row past the CTA
+    for (int i = t - 32; i <= kThreadsMF; i += kThreadsMF - 32) {
+      const long long si = min(c0 + (long long)i * L, c1);
+      S.kfirst[i] = (si == 0) ? 0 : (si > n - 2 ? m : first_above_mf(Gd, S.inv_step, XS[si]));
+    }
   }
   __syncthreads();
   double Y = fma(FB, S.yend, FA);  // y'' of row e0
@@ -354,22 +371,7 @@ __global__ void __launch_bounds__(kThreadsMF, 1)
   if (t == 0 && S.fail) bad |= kStWaitTimeout;
   if (bad) atomicOr(I.status, bad);
   if (m == 0) return;
-  // ---- evaluation: the grid (once per CTA), each piece's first query, then its queries ----
-  if (t == 0) {
-    Grid G0 = make_grid(x, n, m);
-    S.step = G0.step;
-    S.inv_step = (m >= 2) ? rcp64(G0.step) : 0.0;
-  }
-  __syncthreads();
-  Grid Gd;
-  Gd.x0 = x[0];
-  Gd.xl = x[n - 1];
-  Gd.m = m;
-  Gd.step = S.step;
-  // first query of row s0 (threads without rows: s0 = c1, the row past the CTA)
-  S.kfirst[t] = (s0 == 0) ? 0 : (s0 > n - 2 ? m : first_above_mf(Gd, S.inv_step, XS[s0]));
-  if (t == 0) S.kfirst[kThreadsMF] = (c1 > n - 2) ? m : first_above_mf(Gd, S.inv_step, XS[c1]);
-  __syncthreads();
+  // ---- evaluation of the piece's queries (the grid step and the first queries from above) ----
   if (!has || s0 > n - 2) return;
   long long k = S.kfirst[t];
   const long long khi = (e0 <= n - 2) ? S.kfirst[t + 1] : m;  // the next piece's first query
