@@ -308,6 +308,26 @@ __device__ void tile_correct(const FwdOut &o, double delta, const Scratch64 &S) 
   for (int k = 0; k < o.K; ++k) S.at(k, 1) = fma(S.m(k), delta, S.at(k, 1));
 }
 
+// First query whose bracket index is >= s (first_query's result): the estimate
+// floor((x_s - x_0) / step) from binary64 arithmetic (within one of the answer: the grid points
+// are rounded sums) checked on the two grid points around it by their keys, with the bisection
+// for a miss or non-finite operands.  Four grid points instead of ~2 log2(m).
+__device__ __forceinline__ long long first_query_est(const Grid &G, double inv_step, const double *x, long long s) {
+  if (s == 0 || G.m == 0) return 0;
+  if (G.m >= 2) {
+    const double v = x[s];
+    const double e = (v - G.x0) * inv_step;
+    if (finite64(v) && e > -2.0 && e < 9.0e15) {  // false for NaN
+      const long long kv = dkey(v);
+      long long k = max(min((long long)e, G.m - 1), -1LL);  // ~ the last grid point at or below v
+      const bool lo_ok = k < 0 || dkey(G.at(k)) <= kv;
+      const bool hi_ok = k + 1 >= G.m || dkey(G.at(k + 1)) > kv;
+      if (lo_ok && hi_ok) return k + 1;
+    }
+  }
+  return first_query(G, x, s);
+}
+
 // Back substitution from rlast (y''_{rlast} := d'_{rlast}, exact when rlast == n-1), fused
 // with the evaluation: row t's y'' completes interval t, whose queries are evaluated right
 // away, walking the grid downwards.  With T.succ the rows past the tile come from the next
@@ -355,8 +375,9 @@ __device__ void tile_backward_eval(const Inst &I, const TileRows &T, long long r
   // queries over their intervals.
   const bool evaluate = (m > 0 && s0 <= n - 2);
   const Grid G = make_grid(x, n, m);
-  const long long klo = evaluate ? first_query(G, x, s0) : 0;
-  long long k = evaluate ? ((e0 <= n - 2) ? first_query(G, x, e0) - 1 : m - 1) : -1;
+  const double inv_step = (evaluate && m >= 2) ? rcp64(G.step) : 0.0;
+  const long long klo = evaluate ? first_query_est(G, inv_step, x, s0) : 0;
+  long long k = evaluate ? ((e0 <= n - 2) ? first_query_est(G, inv_step, x, e0) - 1 : m - 1) : -1;
   if (t < 0) return;  // a one-row tile at the end of the instance
   // current row t: y''_t (Yt), y''_{t+1} (Yt1), its knot, value, 1/h and width; the next row
   // down is loaded one step ahead
