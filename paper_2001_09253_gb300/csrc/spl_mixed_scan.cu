@@ -43,6 +43,11 @@ constexpr int kHaloS = 64;             // forward rows before a tile
 constexpr int kOvS = 32;               // back-substitution start past a tile
 constexpr int kWarpsS = 20;            // warps per CTA (one CTA per SM; 12 / 16 / 20 measured: more is faster)
 constexpr int kThreadsS = 32 * kWarpsS;
+// The serving loop, which carries the scheduler and all three tile modes, runs 16 warps per SM: at
+// 20 (96 registers) it spilled 408 bytes per thread; at 16 (128 registers) 124, with served
+// latency p50 0.051 -> 0.043 ms and saturation 289k -> 336k requests/s on GB300 (12 warps: p50
+// 0.041 ms, saturation 301k)
+constexpr int kServeThreadsS = 32 * 16;
 // longest tile the shared-memory scratch holds: 544 + the 64-row halo + the 32-row overlap = 640
 // rows, five whole steps (512-row tiles used the same five steps for 608 rows: 6 % more steps per
 // point; batched launches 21 % slower)
@@ -558,7 +563,7 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-__global__ void __launch_bounds__(kThreadsS, 1) serve_kernel(ServeArgs a) {
+__global__ void __launch_bounds__(kServeThreadsS, 1) serve_kernel(ServeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const bool scheduler = (blockIdx.x == 0 && threadIdx.x < 32);
@@ -637,7 +642,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) serve_kernel(ServeArgs a) {
   }
 
   // workers: one ticket per warp; lane 0 waits for it (bounded) and the warp solves the tile.
-  // SM 0 runs the scheduler alone: beside 19 busy worker warps its installs slowed down exactly
+  // SM 0 runs the scheduler alone: beside busy worker warps its installs slowed down exactly
   // when the workers were loaded (saturation 272k -> 288k requests/s without them)
   if (blockIdx.x == 0) return;
   ScanSmem &S = reinterpret_cast<ScanSmem *>(smem_raw)[threadIdx.x >> 5];
@@ -752,8 +757,8 @@ cudaError_t launch_serve(const ServeArgs &args, int sm_count, cudaStream_t strea
   if (attr != cudaSuccess) return attr;
   ServeArgs copy = args;
   void *params[] = {&copy};
-  return cudaLaunchCooperativeKernel((const void *)serve_kernel, dim3((unsigned)sm_count), dim3(kThreadsS), params,
-                                     kSmemPerWarpS * kWarpsS, stream);
+  return cudaLaunchCooperativeKernel((const void *)serve_kernel, dim3((unsigned)sm_count), dim3(kServeThreadsS), params,
+                                     kSmemPerWarpS * (kServeThreadsS / 32), stream);
 }
 
 int serve_tile_rows(int tile_rows) {
