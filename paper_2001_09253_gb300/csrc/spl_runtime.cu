@@ -24,7 +24,8 @@ constexpr uint64_t kAlign = 256;
 uint64_t round_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
 
 // Per-launch status block: one status word per instance, then two tile counters (one per
-// kernel of the launch), all zeroed before the launch.
+// kernel of the launch), all zeroed before the launch.  Direct launches (LaunchPlan::direct) use
+// none: their status word is pinned host memory and their counter and exchange area the context's.
 uint64_t status_words_bytes(uint64_t count) { return round_up(4 * count, 16); }
 // (a single instance's block also holds the exchange area of the multi-CTA FP64 kernel)
 uint64_t status_block_bytes(uint64_t count) {
