@@ -769,10 +769,14 @@ int serve_tile_max() { return kTileMaxS; }
 int scan_mixed_threads_per_sm() { return kThreadsS; }
 int scan_mixed_tile_max() { return kTileMaxS; }
 
-// rows of one tile: a multiple of 32, about two tiles per resident warp for one instance, at most
-// the shared-memory capacity
+// rows of one tile: a multiple of 32, at most the shared-memory capacity.  One instance of at most
+// 32 rows per resident warp: 32-row tiles, one wave of tiles of a single 128-row step each (with
+// the halo and the overlap; latency of one refined request up to 3e4 knots 0.030 -> 0.022 ms on
+// GB300); larger ones about two tiles per resident warp, of at least 128 rows (shorter tiles
+// there need a second wave: 0.037 -> 0.055 ms at 3e5 knots).
 int scan_mixed_tile_rows(long long total_points, int sm_count, int count) {
   const long long warps = (long long)sm_count * kWarpsS;
+  if (count == 1 && total_points <= 32 * warps) return 32;
   long long L = count > 1 ? kTileMaxS : (total_points + 2 * warps - 1) / (2 * warps);
   L = (L + 31) / 32 * 32;
   return (int)std::max<long long>(std::min<long long>(L, kTileMaxS), 128);
