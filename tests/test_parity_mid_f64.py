@@ -147,3 +147,35 @@ def test_mid_wait_timeout_reported_and_context_usable(ctx):
 def test_fault_flags_validated(ctx):
     with pytest.raises(spl.SplError):
         _plan(ctx, fault_flags=2)
+
+
+def test_direct_requests_in_flight_together(ctx):
+    """Single requests in device memory queued back to back without waiting (each launched as its
+    kernel alone, on the context's one stream): multi-CTA FP64 requests of changing grids and
+    binary32 requests with and without the refinement step share the context's exchange area and
+    tile counter in stream order.  Every result equals the oracle."""
+    import torch
+    f64 = _plan(ctx)
+    f32 = ctx.plan(max_n=1 << 22, precision=spl.PREC_F32_REFINE, refine_steps=0)
+    f32r = ctx.plan(max_n=1 << 22, precision=spl.PREC_F32_REFINE, refine_steps=1)
+    # (plan, n, S tolerance, y'' tolerance): the refined y'' to 1e-8, as for refined batches
+    F64, F32, F32R = (f64, TOL_F64, TOL_F64), (f32, 1e-5, 1e-5), (f32r, 1e-5, 1e-8)
+    cases = [(F64, 20_000), (F32R, 5_000), (F64, 1_000), (F32, 300_000), (F64, 65_537), (F32R, 129),
+             (F64, 600), (F32, 97_280), (F64, 3_001), (F32R, 200_000)]
+    runs = []
+    for i, ((plan, tol, tol_ypp), n) in enumerate(cases):
+        x, y = synth.curve(970 + i, n)
+        bc = (NAT, NAT) if i % 2 == 0 else (-1.0, 0.5)
+        xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+        ypp = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+        yq = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+        jq = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+        t = ctx.submit(plan, xt, yt, bc[0], bc[1], n, ypp, yq, jq)
+        runs.append((t, x, y, bc, n, tol, tol_ypp, (xt, yt, ypp, yq, jq)))
+    for t, x, y, bc, n, tol, tol_ypp, (xt, yt, ypp, yq, jq) in runs:
+        st, _ = ctx.wait(t, 60.0)
+        assert st == spl.OK
+        ref = oracle.fit_eval(x, y, bc[0], bc[1], n)
+        assert np.array_equal(jq.cpu().numpy().astype(np.int64), ref["jq"])
+        assert ypp_error(ypp.cpu().numpy(), ref["ypp"]) <= tol_ypp
+        assert yq_error(x, y, ref["ypp"], ref["jq"], yq.cpu().numpy(), ref["yq"]) <= tol
