@@ -260,6 +260,33 @@ spl_status spl_wait(spl_ctx *ctx, uint64_t ticket, uint64_t timeout_ns, spl_resu
 
 spl_status spl_get_stats(spl_ctx *ctx, spl_stats *out);
 
+/* Launch geometry (introspection; the paper has no counterpart: this is the GPU decomposition of
+ * the fit of section "Implementation").  Which kernel fits a submission of `count` instances of
+ * n[0..count-1] knots under the plan options *plan on a device of sm_count SMs, and with what
+ * tiling: the decision spl_submit / spl_submit_batch take, as a pure function of these arguments
+ * (no device, no context, no allocation).  mem: where the requests' arrays live (spl_mem);
+ * stored_fit: nonzero when the requests carry ypp_in (evaluation only).  SPL_ERR_INVALID_ARG for
+ * a null pointer, count 0, an n below 3, sm_count < 1, an unknown mem, or plan options that
+ * spl_plan_create rejects. */
+typedef enum spl_kernel {
+  SPL_KERNEL_NONE = 0,        /* no fit (stored y''): the evaluation kernel alone */
+  SPL_KERNEL_FUSED_F64 = 1,   /* FP64, one thread per tile of tile_rows knots, persistent CTAs */
+  SPL_KERNEL_SMALL_F64 = 2,   /* FP64, one CTA per instance (batches of small instances) */
+  SPL_KERNEL_MID_F64 = 3,     /* FP64, one instance on a cooperative grid of ctas CTAs */
+  SPL_KERNEL_SCAN_MIXED = 4   /* binary32 (+ refinement), one warp per tile of tile_rows knots */
+} spl_kernel;
+typedef struct spl_geometry {
+  int32_t fit_kernel;     /* spl_kernel */
+  int32_t separate_eval;  /* 1: the queries are evaluated by the separate evaluation kernel */
+  int32_t tile_rows;      /* knots per tile in the instance descriptors */
+  int32_t direct;         /* 1: enqueued as its kernel launch(es) alone where the device has native
+                             atomics on host memory (see spl_submit) */
+  int64_t cta_rows;       /* SPL_KERNEL_MID_F64: knots per CTA (a multiple of 128); else 0 */
+  int64_t ctas;           /* SPL_KERNEL_MID_F64: CTAs of the cooperative grid; else 0 */
+} spl_geometry;
+spl_status spl_launch_geometry(const spl_plan_desc *plan, const uint64_t *n, uint32_t count, int32_t mem,
+                               int32_t stored_fit, int32_t sm_count, spl_geometry *out);
+
 /* Reusable batch: the descriptors of count device-memory requests are uploaded once and
  * the launch is captured in a CUDA graph; every spl_batch_launch replays it on the
  * context's stream (one persistent kernel over all tiles of all instances; two, the fit and

@@ -179,6 +179,19 @@ spl_status map_status_bits(unsigned bits) {
 
 bool slope_ok(double s) { return !std::isnan(s) && !(std::isinf(s) && s < 0); }
 
+// Plan options that spl_plan_create accepts.
+bool plan_desc_ok(const spl_plan_desc *d) {
+  if (d->max_n < 3) return false;
+  if (d->precision != SPL_PREC_F64 && d->precision != SPL_PREC_F32_REFINE) return false;
+  if (d->refine_steps < 0 || d->refine_steps > 1) return false;
+  if (d->precision == SPL_PREC_F64 && d->refine_steps != 0) return false;
+  if (d->tile_rows != 0 && d->tile_rows < 16) return false;
+  if (d->query_mode != SPL_QUERY_UNIFORM && d->query_mode != SPL_QUERY_EXPLICIT) return false;
+  if (d->eval_variant < SPL_EVAL_ORIG || d->eval_variant > SPL_EVAL_NOOP) return false;
+  if (d->fault_flags & ~1u) return false;
+  return true;
+}
+
 spl_status check_request(const spl_plan *plan, const spl_request *r) {
   if (!r) return SPL_ERR_INVALID_ARG;
   if (r->n < 3 || r->n > plan->max_n) return SPL_ERR_INVALID_ARG;
@@ -208,7 +221,7 @@ long long threads_for(const spl_ctx *c, int precision, long long total_tiles) {
 // total_points fills every thread of one wave; never shorter than a few halos.  FP64 tiles come
 // in warp groups of 32L - overhang - lane0_short rows, so L is chosen for the group count to
 // match the warps.
-int auto_tile_rows(const spl_ctx *c, uint64_t total_points, uint32_t count) {
+int auto_tile_rows(int sm_count, uint64_t total_points, uint32_t count) {
   // several instances: short tiles, fetched dynamically, balance instances of uneven sizes
   // (one wave of long tiles waits on the longest; 4,096 log-uniform instances run ~1.4x faster)
   if (count > 1) return 128;
@@ -219,17 +232,70 @@ int auto_tile_rows(const spl_ctx *c, uint64_t total_points, uint32_t count) {
   // 16-row tiles halve the time (0.36-0.41 -> 0.17 ms); past a few 1e5 points the halo work that
   // every short tile repeats outweighs the shorter chain, and from ~1e6 the grouped long tiles
   // below win.
-  const uint64_t upto16 = (uint64_t)c->sm_count * 2000ull;
-  const uint64_t upto32 = (uint64_t)c->sm_count * 8000ull;
+  const uint64_t upto16 = (uint64_t)sm_count * 2000ull;
+  const uint64_t upto32 = (uint64_t)sm_count * 8000ull;
   if (total_points <= upto16) return 16;
   if (total_points <= upto32) return 32;
-  const long long target = (long long)c->sm_count * spl::f64_threads_per_sm();
+  const long long target = (long long)sm_count * spl::f64_threads_per_sm();
   const long long warps = std::max<long long>(target / 32, 1);
   const long long per_warp = (long long)((total_points + warps - 1) / warps);
   long long L = (per_warp + spl::overhang_rows_f64() + spl::lane0_short_rows_f64() + 31) / 32;
   L = std::max<long long>(L, 128);
   L = std::min<long long>(L, 1 << 20);
   return (int)L;
+}
+
+// The launch shape of a submission: which kernel fits it and with what tiling, as a pure function
+// of the plan's options, the instances' sizes, where their arrays live and the SM count (no
+// device state).  prepare() builds the launch from it; spl_launch_geometry reports it.
+struct PathChoice {
+  int fit_kernel = SPL_KERNEL_NONE;  // spl_kernel
+  bool separate_eval = false;        // explicit queries or a stored fit: the evaluation kernel
+  int tile_rows = 0;                 // knots per tile in the descriptors
+  long long cta_rows = 0, ctas = 0;  // the multi-CTA FP64 kernel's grid
+  bool direct = false;               // a direct launch where the device allows it (LaunchPlan::direct)
+};
+
+PathChoice choose_path(int precision, int plan_tile_rows, int query_mode, bool fit, bool device_mem,
+                       const uint64_t *ns, uint32_t count, int sm_count) {
+  PathChoice pc;
+  uint64_t total_points = 0;
+  for (uint32_t i = 0; i < count; ++i) total_points += ns[i];
+  pc.separate_eval = query_mode == SPL_QUERY_EXPLICIT || !fit;
+  if (precision == SPL_PREC_F32_REFINE) {
+    // the warp-cooperative kernel for every binary32 launch (one thread per tile was 2-6x slower
+    // even on batches of instances of a few hundred knots): tiles of whole 32-row chunks, no
+    // longer than its shared memory holds
+    pc.tile_rows = plan_tile_rows > 0 ? std::min((plan_tile_rows + 31) / 32 * 32, spl::scan_mixed_tile_max())
+                                      : spl::scan_mixed_tile_rows((long long)total_points, sm_count, (int)count);
+  } else {
+    pc.tile_rows = plan_tile_rows > 0 ? plan_tile_rows : auto_tile_rows(sm_count, total_points, count);
+  }
+  if (!fit) return pc;
+  if (precision == SPL_PREC_F32_REFINE) {
+    pc.fit_kernel = SPL_KERNEL_SCAN_MIXED;
+  } else {
+    pc.fit_kernel = SPL_KERNEL_FUSED_F64;
+    if (plan_tile_rows == 0 && !pc.separate_eval) {
+      // one instance up to SMs x 9,600 knots: the multi-CTA kernel (its latency is a piece's FP64
+      // chain); up to two waves of instances of at most 4,096 knots (two CTAs fit an SM): one CTA
+      // each.  More instances go to the tiled kernel, whose throughput then wins (4,096 instances
+      // of 3..4,096 knots: 0.98 ms against 1.24 ms; 512 of 1,000..4,096: 0.43 ms against 0.27 ms).
+      const long long cr = count == 1 ? spl::mid_f64_cta_rows((long long)ns[0], sm_count) : 0;
+      if (cr > 0) {
+        pc.fit_kernel = SPL_KERNEL_MID_F64;
+        pc.cta_rows = cr;
+        pc.ctas = ((long long)ns[0] + cr - 1) / cr;
+      } else {
+        bool small = count <= 4u * (uint32_t)sm_count;
+        for (uint32_t i = 0; i < count; ++i) small = small && ns[i] <= (uint64_t)spl::small_f64_max_rows();
+        if (small) pc.fit_kernel = SPL_KERNEL_SMALL_F64;
+      }
+    }
+  }
+  pc.direct = count == 1 && device_mem && !pc.separate_eval &&
+              (pc.fit_kernel == SPL_KERNEL_MID_F64 || pc.fit_kernel == SPL_KERNEL_SCAN_MIXED);
+  return pc;
 }
 
 // Instances from this many knots up get a coarse key table for the bisection of explicit query
@@ -294,38 +360,23 @@ spl_status prepare(spl_ctx *c, spl_plan *p, const spl_request *reqs, uint32_t co
                    std::vector<Block> &dev_blocks, Block &pin_block, uint64_t *d_insts_off,
                    uint64_t *d_status_off, uint64_t *d_ring_off, bool allow_direct) {
   uint64_t total_points = 0;
-  for (uint32_t i = 0; i < count; ++i) total_points += reqs[i].n;
+  std::vector<uint64_t> ns(count);
+  for (uint32_t i = 0; i < count; ++i) {
+    ns[i] = reqs[i].n;
+    total_points += reqs[i].n;
+  }
   lp.precision = p->precision;
   lp.refine_steps = p->precision == SPL_PREC_F64 ? 0 : p->refine_steps;
   lp.fit = reqs[0].ypp_in == nullptr;
-  lp.separate_eval = p->query_mode == SPL_QUERY_EXPLICIT || !lp.fit;
-  int L;
-  if (p->precision == SPL_PREC_F32_REFINE) {
-    // the warp-cooperative kernel for every binary32 launch (one thread per tile was 2-6x slower
-    // even on batches of instances of a few hundred knots): tiles of whole 32-row chunks, no
-    // longer than its shared memory holds
-    L = p->tile_rows > 0 ? std::min((p->tile_rows + 31) / 32 * 32, spl::scan_mixed_tile_max())
-                         : spl::scan_mixed_tile_rows((long long)total_points, c->sm_count, (int)count);
-  } else {
-    L = p->tile_rows > 0 ? p->tile_rows : auto_tile_rows(c, total_points, count);
-  }
+  const PathChoice pc = choose_path(p->precision, p->tile_rows, p->query_mode, lp.fit,
+                                    reqs[0].mem == SPL_MEM_DEVICE, ns.data(), count, c->sm_count);
+  lp.separate_eval = pc.separate_eval;
+  const int L = pc.tile_rows;
   lp.eval_variant = p->eval_variant;
   lp.fault_flags = p->fault_flags;
-  if (p->precision == SPL_PREC_F64 && p->tile_rows == 0 && lp.fit && !lp.separate_eval) {
-    // one instance up to SMs x 9,600 knots: the multi-CTA kernel (its latency is a piece's FP64
-    // chain); up to two waves of instances of at most 4,096 knots (two CTAs fit an SM): one CTA
-    // each.  More instances go to the tiled kernel, whose throughput then wins (4,096 instances of
-    // 3..4,096 knots: 0.98 ms against 1.24 ms; 512 of 1,000..4,096: 0.43 ms against 0.27 ms).
-    if (count == 1 && spl::mid_f64_cta_rows((long long)reqs[0].n, c->sm_count) > 0) {
-      lp.mid_f64 = true;
-    } else {
-      lp.small_f64 = count <= 4u * (uint32_t)c->sm_count;
-      for (uint32_t i = 0; i < count; ++i)
-        lp.small_f64 = lp.small_f64 && reqs[i].n <= (uint64_t)spl::small_f64_max_rows();
-    }
-  }
-  lp.direct = allow_direct && c->direct_ok && count == 1 && reqs[0].mem == SPL_MEM_DEVICE && lp.fit &&
-              !lp.separate_eval && (lp.mid_f64 || p->precision == SPL_PREC_F32_REFINE);
+  lp.mid_f64 = pc.fit_kernel == SPL_KERNEL_MID_F64;
+  lp.small_f64 = pc.fit_kernel == SPL_KERNEL_SMALL_F64;
+  lp.direct = allow_direct && c->direct_ok && pc.direct;
   lp.insts.resize(count);
   // Instances of 32 tiles or more of the FP64 kernel use the grouped geometry: their tiles
   // start on a warp boundary, and each warp's 32 tiles cover 32L - overhang - lane0_short rows
@@ -709,14 +760,7 @@ void spl_destroy(spl_ctx *c) {
 spl_status spl_plan_create(spl_ctx *c, const spl_plan_desc *d, spl_plan **out) {
   if (!c || !d || !out) return SPL_ERR_INVALID_ARG;
   *out = nullptr;
-  if (d->max_n < 3) return SPL_ERR_INVALID_ARG;
-  if (d->precision != SPL_PREC_F64 && d->precision != SPL_PREC_F32_REFINE) return SPL_ERR_INVALID_ARG;
-  if (d->refine_steps < 0 || d->refine_steps > 1) return SPL_ERR_INVALID_ARG;
-  if (d->precision == SPL_PREC_F64 && d->refine_steps != 0) return SPL_ERR_INVALID_ARG;
-  if (d->tile_rows != 0 && d->tile_rows < 16) return SPL_ERR_INVALID_ARG;
-  if (d->query_mode != SPL_QUERY_UNIFORM && d->query_mode != SPL_QUERY_EXPLICIT) return SPL_ERR_INVALID_ARG;
-  if (d->eval_variant < SPL_EVAL_ORIG || d->eval_variant > SPL_EVAL_NOOP) return SPL_ERR_INVALID_ARG;
-  if (d->fault_flags & ~1u) return SPL_ERR_INVALID_ARG;
+  if (!plan_desc_ok(d)) return SPL_ERR_INVALID_ARG;
   spl_plan *p = new (std::nothrow) spl_plan();
   if (!p) return SPL_ERR_CUDA;
   p->ctx = c;
@@ -834,6 +878,23 @@ spl_status spl_wait(spl_ctx *c, uint64_t ticket, uint64_t timeout_ns, spl_result
     if (waited > 2.0) std::this_thread::sleep_for(std::chrono::microseconds(20));
     else std::this_thread::yield();
   }
+}
+
+spl_status spl_launch_geometry(const spl_plan_desc *plan, const uint64_t *n, uint32_t count, int32_t mem,
+                               int32_t stored_fit, int32_t sm_count, spl_geometry *out) {
+  if (!plan || !n || !out || count == 0 || sm_count < 1 || !plan_desc_ok(plan)) return SPL_ERR_INVALID_ARG;
+  if (mem != SPL_MEM_DEVICE && mem != SPL_MEM_HOST) return SPL_ERR_INVALID_ARG;
+  for (uint32_t i = 0; i < count; ++i)
+    if (n[i] < 3 || n[i] > plan->max_n || n[i] > (1ull << 40)) return SPL_ERR_INVALID_ARG;
+  const PathChoice pc = choose_path(plan->precision, plan->tile_rows, plan->query_mode, stored_fit == 0,
+                                    mem == SPL_MEM_DEVICE, n, count, sm_count);
+  out->fit_kernel = pc.fit_kernel;
+  out->separate_eval = pc.separate_eval ? 1 : 0;
+  out->tile_rows = pc.tile_rows;
+  out->direct = pc.direct ? 1 : 0;
+  out->cta_rows = pc.cta_rows;
+  out->ctas = pc.ctas;
+  return SPL_OK;
 }
 
 spl_status spl_get_stats(spl_ctx *c, spl_stats *out) {

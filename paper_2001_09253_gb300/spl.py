@@ -25,6 +25,7 @@ PREC_F64, PREC_F32_REFINE = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 QUERY_UNIFORM, QUERY_EXPLICIT = 0, 1
 EVAL_ORIG, EVAL_NOINV, EVAL_VOL, EVAL_NOOP = 0, 1, 2, 3
+KERNEL_NONE, KERNEL_FUSED_F64, KERNEL_SMALL_F64, KERNEL_MID_F64, KERNEL_SCAN_MIXED = 0, 1, 2, 3, 4
 NATURAL = 1e32
 
 EXPORTS = [
@@ -33,6 +34,7 @@ EXPORTS = [
     "spl_batch_wait", "spl_batch_destroy", "spl_generate_scratch_bytes", "spl_generate_curve",
     "spl_fit_eval_noalloc", "spl_serve_create", "spl_serve_submit", "spl_serve_poll", "spl_serve_wait",
     "spl_serve_replay", "spl_serve_stats", "spl_serve_destroy", "spl_selftest_div64", "spl_selftest_dfma",
+    "spl_launch_geometry",
 ]
 NOALLOC_MAX_N = 1048576
 
@@ -46,6 +48,11 @@ class PlanDesc(ctypes.Structure):
     _fields_ = [("max_n", ctypes.c_uint64), ("precision", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
                 ("tile_rows", ctypes.c_int32), ("query_mode", ctypes.c_int32), ("eval_variant", ctypes.c_int32),
                 ("fault_flags", ctypes.c_uint32)]
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("fit_kernel", ctypes.c_int32), ("separate_eval", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
+                ("direct", ctypes.c_int32), ("cta_rows", ctypes.c_int64), ("ctas", ctypes.c_int64)]
 
 
 class Request(ctypes.Structure):
@@ -103,6 +110,8 @@ def load(path: str | None = None):
         L.spl_poll.argtypes = [vp, u64, ctypes.POINTER(Result)]
         L.spl_wait.argtypes = [vp, u64, u64, ctypes.POINTER(Result)]
         L.spl_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        L.spl_launch_geometry.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(u64), u32, i32, i32, i32,
+                                          ctypes.POINTER(Geometry)]
         L.spl_batch_create.argtypes = [vp, vp, ctypes.POINTER(Request), u32, ctypes.POINTER(vp)]
         L.spl_batch_launch.argtypes = [vp]
         L.spl_batch_wait.argtypes = [vp, u64, ctypes.POINTER(i32)]
@@ -391,6 +400,26 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def launch_geometry(sizes, sm_count: int, precision: int = PREC_F64, refine_steps: int = 0, tile_rows: int = 0,
+                    query_mode: int = QUERY_UNIFORM, max_n: int | None = None, mem: int = MEM_DEVICE,
+                    stored_fit: bool = False):
+    """spl_launch_geometry: the kernel and tiling a submission of instances of `sizes` knots would
+    take on a device of sm_count SMs (a pure function; no GPU needed).  Returns a dict, or raises
+    SplError for arguments the library rejects."""
+    L = load()
+    ns = [int(v) for v in sizes]
+    arr = (ctypes.c_uint64 * len(ns))(*ns)
+    d = PlanDesc(max_n=int(max_n if max_n is not None else max(ns + [3])), precision=precision,
+                 refine_steps=refine_steps, tile_rows=tile_rows, query_mode=query_mode, eval_variant=EVAL_ORIG,
+                 fault_flags=0)
+    g = Geometry()
+    s = L.spl_launch_geometry(ctypes.byref(d), arr, len(ns), mem, 1 if stored_fit else 0, sm_count, ctypes.byref(g))
+    if s != OK:
+        raise SplError(s)
+    return {"fit_kernel": g.fit_kernel, "separate_eval": bool(g.separate_eval), "tile_rows": g.tile_rows,
+            "direct": bool(g.direct), "cta_rows": g.cta_rows, "ctas": g.ctas}
 
 
 def fit_eval_noalloc(x, y, yp1=NATURAL, ypn=NATURAL, m=None, ypp_out=None, yq_out=None, stream=None,
